@@ -1,0 +1,179 @@
+/*
+ * ffc_gb300.h -- C ABI of the GB300 (sm_103a) tensor-representation library.
+ *
+ * The library evaluates element tensors of bilinear variational forms on affine
+ * simplices by the tensor representation A^K_i = A0_{i alpha} G_K^alpha
+ * (Kirby & Logg, "A Compiler for Variational Forms", Section 3.2, eq.
+ * (tensorproduct)) and adds them into a global CSR matrix through the
+ * local-to-global dof map (Section 2.2, Algorithm 2).
+ *
+ * Conventions shared by every entry point
+ *  - Return value: FFC_OK (0) or a negative ffc_status. Argument checks happen
+ *    before any launch; a call that returns an error launched nothing.
+ *  - Pointers marked "device" are caller-owned CUDA device memory on the current
+ *    device, contiguous, row-major, 16-byte aligned. Pointers marked "host" are
+ *    caller-owned host memory. The library never frees caller memory.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *    Device work is asynchronous on that stream.
+ *  - Local dof order on a simplex with vertices 0..d: for m = 0..d, for each
+ *    vertex subset S of size m+1 in lexicographic order, the lattice points with
+ *    support exactly S in descending lexicographic order of their barycentric
+ *    multi-index (vertices, then edges 01,02,03,12,13,23, faces, interior).
+ *    Vector spaces are component blocked: i = c*n_scalar + s.
+ *  - Element tensor layout: A_K[e][i1][i2], i1 = test (row), i2 = trial (column),
+ *    the dense row-major block of Section 5.5 ("block[]").
+ *  - Geometry: J = [x_1 - x_0, ..., x_d - x_0] from the cell's vertices in the
+ *    given order; G_K uses |det J| (negatively oriented cells are allowed).
+ *  - Device-side problems (a degenerate cell, a CSR slot out of range) do not
+ *    stop a launch: they set bits in a library-owned device status word that
+ *    ffc_status_poll() returns and clears.
+ */
+#ifndef FFC_GB300_H
+#define FFC_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ffc_form ffc_form;   /* opaque; owns the reference tensor (host and device copies) */
+typedef struct ffc_batch ffc_batch; /* opaque; a heterogeneous work list for one persistent launch */
+
+typedef enum {
+  FFC_OK = 0,
+  FFC_EINVAL = -1,        /* null pointer, bad size, bad enum value */
+  FFC_ENOMEM = -2,        /* host or device allocation failed */
+  FFC_ECUDA = -3,         /* a CUDA runtime call failed (message via ffc_last_error) */
+  FFC_EDEGENERATE = -4,   /* status word: at least one cell had |det J| <= 1e-14 h_max^d */
+  FFC_EUNSUPPORTED = -5,  /* (form, cell, degree, precision) combination not built */
+  FFC_EBOUNDS = -6,       /* status word: an index (slot, dof, vertex) was out of range */
+  FFC_ETIMEOUT = -7       /* status word: a bounded device wait gave up */
+} ffc_status;
+
+/* Forms of Section 3.3 of the paper. */
+typedef enum {
+  FFC_MASS = 0,           /* int v u dx                         (test case 1) */
+  FFC_POISSON = 1,        /* int grad v . grad u dx             (test case 2) */
+  FFC_NS_CONVECTION = 2,  /* int v . (w . grad) u dx, w given   (test case 3) */
+  FFC_ELASTICITY = 3      /* int 2 mu eps(v):eps(u) + lambda div v div u dx (test case 4) */
+} ffc_form_kind;
+
+typedef enum { FFC_TRIANGLE = 2, FFC_TETRAHEDRON = 3 } ffc_cell; /* value = spatial dimension d */
+
+/* Arithmetic of the contraction A0 : G. Geometry (J, det J, J^{-1}, G) is always
+ * computed in FP64; FP64 is also the CSR accumulation type of ffc_assemble. */
+typedef enum {
+  FFC_FP64 = 0,   /* FP64 contraction, A_K stored as double */
+  FFC_FP32 = 1,   /* FP32 G and A0, FP32 accumulation on CUDA cores, A_K stored as float */
+  FFC_TF32 = 2,   /* tcgen05 kind::tf32, one product, FP32 accumulation in TMEM, float out */
+  FFC_TF32X3 = 3  /* tcgen05 kind::tf32 with hi/lo splits of G and A0 (three products), float out */
+} ffc_precision;
+
+/* Device status bits returned by ffc_status_poll. */
+#define FFC_FLAG_DEGENERATE 0x1u
+#define FFC_FLAG_BOUNDS 0x2u
+#define FFC_FLAG_TIMEOUT 0x4u
+
+/*
+ * ffc_form_create -- compile a form: build the reference tensor
+ *   A0[i1*n + i2][alpha] = int_{K0} prod dPhi/dX dX        (Section 3.2, A0 equation)
+ * once, in FP64, by collapsed Gauss-Jacobi quadrature on the reference simplex
+ * (Section 5.3 and Section 6), exact for the integrand degree.
+ *   form   ffc_form_kind; cell ffc_cell; degree q of the Lagrange space (1..4;
+ *          the convection form takes 1..2, elasticity 1..3, vector forms need tets).
+ *   mu, lambda  elasticity parameters (ignored by the other forms).
+ *   out    receives a new handle; release with ffc_form_destroy.
+ * Returns FFC_EINVAL / FFC_EUNSUPPORTED / FFC_ENOMEM. Host-only: no device memory
+ * is touched until a launch needs the reference tensor on a device.
+ */
+int ffc_form_create(int form, int cell, int degree, double mu, double lambda, ffc_form** out);
+
+/* n_local = n (local dofs per cell), n_alpha = |alpha| (entries of G_K),
+ * n_coeff = per-cell coefficients the form reads (30 for vector-P2 convection, else 0). */
+int ffc_form_info(const ffc_form* f, int* n_local, int* n_alpha, int* n_coeff);
+
+/* Raw reference tensor (the "raw format" output of Section 5.4):
+ * host_out double [n*n][n_alpha], row-major. */
+int ffc_form_reference_tensor(const ffc_form* f, double* host_out);
+
+/* Frees host data and any device copies of the reference tensor. NULL is ignored. */
+void ffc_form_destroy(ffc_form* f);
+
+/*
+ * ffc_tabulate -- element tensors A^K = A0 : G_K for n_elem cells (Section 3.2,
+ * eq. (tensorproduct); the per-cell evaluation the generated eval() of Section 5.5
+ * performs).
+ *   cells     device int32 [n_elem][d+1] vertex ids (local vertex order as given)
+ *   vertices  device double [n_vert][d]
+ *   coeffs    device double [n_elem][n_coeff] (convection: w on each cell, component
+ *             blocked like the basis), NULL when n_coeff == 0
+ *   A_K       device [n_elem][n][n], double for FFC_FP64, float otherwise
+ *   precision ffc_precision
+ * n_elem == 0 launches nothing and returns FFC_OK. A vertex id outside
+ * [0, n_vert) is replaced by 0 and sets FFC_FLAG_BOUNDS (never read out of range).
+ */
+int ffc_tabulate(const ffc_form* f, int64_t n_elem, const int32_t* cells, const double* vertices,
+                 int64_t n_vert, const double* coeffs, void* A_K, int precision, void* stream);
+
+/*
+ * ffc_csr_pattern -- sparsity pattern of the assembled matrix (host, setup).
+ * The pattern holds every (row, col) pair of dofs that share a cell (Algorithm 2
+ * touches exactly those entries), columns sorted ascending within each row.
+ *   dofmap  host int32 [n_elem][n_local], global ids in [0, n_dof)
+ *   row_ptr host int64 [n_dof + 1] (always written)
+ *   nnz     receives the number of stored entries
+ *   col     host int32 [nnz] or NULL; written only when col_capacity >= nnz
+ *   slot    host int32 [n_elem][n_local][n_local] or NULL: position in `col` of
+ *           (dofmap[e][i1], dofmap[e][i2]); written together with col
+ * Call once with col = NULL to learn nnz, then again with buffers.
+ * Uses all host threads of the process affinity mask. FFC_EBOUNDS if a dof id
+ * is out of range; FFC_EINVAL if nnz would exceed INT32_MAX (slots are int32).
+ */
+int ffc_csr_pattern(int64_t n_elem, int n_local, const int32_t* dofmap, int64_t n_dof,
+                    int64_t* row_ptr, int64_t* nnz, int32_t* col, int64_t col_capacity, int32_t* slot);
+
+/*
+ * ffc_assemble -- Algorithm 2 fused on the device: for every cell compute A^K
+ * (as ffc_tabulate, never written to memory) and add it into the CSR values,
+ *   csr_val[slot[e][i1][i2]] += A^K[i1][i2]     (FP64 atomic adds).
+ *   slot     device int32 [n_elem][n][n] from ffc_csr_pattern
+ *   csr_val  device double [nnz], accumulated into (zero it first for a fresh matrix)
+ * Slots >= nnz are skipped and set FFC_FLAG_BOUNDS. Summation order of the atomic
+ * adds is not deterministic (results agree to rounding).
+ */
+int ffc_assemble(const ffc_form* f, int64_t n_elem, const int32_t* cells, const double* vertices,
+                 int64_t n_vert, const double* coeffs, const int32_t* slot, double* csr_val, int64_t nnz,
+                 int precision, void* stream);
+
+/*
+ * ffc_tabulate_adjoint -- reverse mode of ffc_tabulate with respect to the vertex
+ * coordinates (chain rule through G_K(J) of the Poisson form, Section 3.3 test
+ * case 2, and J = [x_1 - x_0, ...]):
+ *   dG[alpha]   = sum_i A0[i][alpha] * dA_K[e][i]
+ *   dJ          from dG through G = |det J| K K^T, K = J^{-1}
+ *   dvertices[cells[e][j]] += dJ contributions   (FP64 atomic adds)
+ *   dA_K       device double [n_elem][n][n], the upstream gradient dL/dA_K
+ *   dvertices  device double [n_vert][d], accumulated into
+ * Poisson forms only (FFC_EUNSUPPORTED otherwise).
+ */
+int ffc_tabulate_adjoint(const ffc_form* f, int64_t n_elem, const int32_t* cells, const double* vertices,
+                         int64_t n_vert, const double* dA_K, double* dvertices, void* stream);
+
+/*
+ * ffc_status_poll -- synchronise `stream`, return the device status bits
+ * (FFC_FLAG_*) accumulated by earlier launches on the current device, and clear them.
+ */
+int ffc_status_poll(void* stream, uint32_t* flags);
+
+/* Human-readable name of a status code (static string). */
+const char* ffc_status_string(int status);
+
+/* Text of the last FFC_ECUDA / validation failure on this host thread (static per thread). */
+const char* ffc_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FFC_GB300_H */

@@ -90,24 +90,24 @@ def element_tensors(form: int, verts: np.ndarray, q: int, coeffs: np.ndarray | N
         v = verts[s:s + chunk]
         grad_lam, vol = barycentric_geometry(v)
         if form == MASS:
-            local = np.einsum("q,qi,qj->ij", w, phi, phi)
+            local = np.einsum("q,qi,qj->ij", w, phi, phi, optimize=True)
             out[s:s + chunk] = vol[:, None, None] * local[None]
             continue
         grad = np.einsum("qij,ejb->eqib", dphi, grad_lam)  # [e, q, ns, d]
         if form == POISSON:
-            out[s:s + chunk] = vol[:, None, None] * np.einsum("q,eqib,eqjb->eij", w, grad, grad)
+            out[s:s + chunk] = vol[:, None, None] * np.einsum("q,eqib,eqjb->eij", w, grad, grad, optimize=True)
         elif form == NS_CONVECTION:
             Phi, G = _vectorise(d, phi, grad)
             c = np.asarray(coeffs[s:s + chunk], dtype=np.float64)  # [e, n]
-            wq = np.einsum("et,qtc->eqc", c, Phi)  # w(x_q)
-            conv = np.einsum("eqb,eqjcb->eqjc", wq, G)  # (w . grad) phi_j
-            out[s:s + chunk] = vol[:, None, None] * np.einsum("q,qic,eqjc->eij", w, Phi, conv)
+            wq = np.einsum("et,qtc->eqc", c, Phi, optimize=True)  # w(x_q)
+            conv = np.einsum("eqb,eqjcb->eqjc", wq, G, optimize=True)  # (w . grad) phi_j
+            out[s:s + chunk] = vol[:, None, None] * np.einsum("q,qic,eqjc->eij", w, Phi, conv, optimize=True)
         elif form == ELASTICITY:
             _, G = _vectorise(d, phi, grad)
             eps = 0.5 * (G + np.swapaxes(G, -1, -2))
             div = np.trace(G, axis1=-2, axis2=-1)
-            a = 2.0 * mu * np.einsum("q,eqirs,eqjrs->eij", w, eps, eps)
-            a += lmbda * np.einsum("q,eqi,eqj->eij", w, div, div)
+            a = 2.0 * mu * np.einsum("q,eqirs,eqjrs->eij", w, eps, eps, optimize=True)
+            a += lmbda * np.einsum("q,eqi,eqj->eij", w, div, div, optimize=True)
             out[s:s + chunk] = vol[:, None, None] * a
         else:
             raise ValueError(form)

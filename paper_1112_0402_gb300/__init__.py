@@ -1,0 +1,10 @@
+"""GB300 (sm_103a) tensor representation of variational forms: batched element
+tensors A^K = A0 : G_K and their fused insertion into a global CSR matrix
+(Kirby & Logg, "A Compiler for Variational Forms", Sections 2.2 and 3.2).
+
+The compute path is the C-ABI library ``libffc_gb300.so`` (include/ffc_gb300.h);
+this package only marshals arguments to it.
+"""
+from .api import (ELASTICITY, FLAG_BOUNDS, FLAG_DEGENERATE, FLAG_TIMEOUT, FP32, FP64, MASS, NS_CONVECTION,  # noqa
+                  POISSON, TETRAHEDRON, TF32, TF32X3, TRIANGLE, FFCError, Form, assemble, csr_pattern,
+                  status_poll, tabulate, tabulate_adjoint)

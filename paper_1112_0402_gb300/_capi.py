@@ -1,0 +1,55 @@
+"""ctypes declarations of the C ABI in include/ffc_gb300.h.
+
+Loading fails loudly when the library has not been built: there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libffc_gb300.so")
+
+c_i32p = ctypes.POINTER(ctypes.c_int32)
+c_i64p = ctypes.POINTER(ctypes.c_int64)
+c_u32p = ctypes.POINTER(ctypes.c_uint32)
+c_dblp = ctypes.POINTER(ctypes.c_double)
+c_vp = ctypes.c_void_p
+
+# name -> (restype, argtypes); every entry point declared in ffc_gb300.h
+SIGNATURES = {
+    "ffc_form_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                       ctypes.POINTER(c_vp)]),
+    "ffc_form_info": (ctypes.c_int, [c_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                     ctypes.POINTER(ctypes.c_int)]),
+    "ffc_form_reference_tensor": (ctypes.c_int, [c_vp, c_vp]),
+    "ffc_form_destroy": (None, [c_vp]),
+    "ffc_tabulate": (ctypes.c_int, [c_vp, ctypes.c_int64, c_vp, c_vp, ctypes.c_int64, c_vp, c_vp, ctypes.c_int,
+                                    c_vp]),
+    "ffc_csr_pattern": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int, c_vp, ctypes.c_int64, c_vp, c_i64p, c_vp,
+                                       ctypes.c_int64, c_vp]),
+    "ffc_assemble": (ctypes.c_int, [c_vp, ctypes.c_int64, c_vp, c_vp, ctypes.c_int64, c_vp, c_vp, c_vp,
+                                    ctypes.c_int64, ctypes.c_int, c_vp]),
+    "ffc_tabulate_adjoint": (ctypes.c_int, [c_vp, ctypes.c_int64, c_vp, c_vp, ctypes.c_int64, c_vp, c_vp, c_vp]),
+    "ffc_status_poll": (ctypes.c_int, [c_vp, c_u32p]),
+    "ffc_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "ffc_last_error": (ctypes.c_char_p, []),
+}
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(
+                f"{LIB_PATH} is missing: build it with paper_1112_0402_gb300.build.build() "
+                "(nvcc, sm_103a). There is no CPU fallback.")
+        h = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(h, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = h
+    return _lib

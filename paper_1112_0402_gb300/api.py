@@ -1,0 +1,176 @@
+"""Python binding of the C ABI (argument marshalling only: every step runs in the
+library's CUDA kernels). PyTorch provides device memory and streams.
+
+    form = Form(POISSON, TETRAHEDRON, 2)
+    A_K = tabulate(form, cells, vertices)                 # [n_elem, n, n] on the GPU
+    row_ptr, col, slot = csr_pattern(dofmap, n_dof)       # host, setup
+    assemble(form, cells, vertices, slot_dev, csr_val)    # csr_val[slot] += A^K
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from ._capi import lib
+
+MASS, POISSON, NS_CONVECTION, ELASTICITY = 0, 1, 2, 3
+TRIANGLE, TETRAHEDRON = 2, 3
+FP64, FP32, TF32, TF32X3 = 0, 1, 2, 3
+PRECISIONS = {"fp64": FP64, "fp32": FP32, "tf32": TF32, "tf32x3": TF32X3}
+FLAG_DEGENERATE, FLAG_BOUNDS, FLAG_TIMEOUT = 1, 2, 4
+
+
+class FFCError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        L = lib()
+        msg = L.ffc_status_string(code).decode()
+        detail = L.ffc_last_error().decode()
+        super().__init__(f"{where}: {msg}" + (f" ({detail})" if detail else ""))
+        self.code = code
+
+
+def _check(code: int, where: str) -> None:
+    if code != 0:
+        raise FFCError(code, where)
+
+
+def _prec(p) -> int:
+    return PRECISIONS[p] if isinstance(p, str) else int(p)
+
+
+def _stream(stream):
+    import torch
+
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dev_ptr(t, dtype, name, shape=None):
+    import torch
+
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Form:
+    """A compiled form: the reference tensor A0 of (kind, cell, degree)."""
+
+    def __init__(self, kind: int, cell: int, degree: int, mu: float = 1.0, lmbda: float = 1.25):
+        h = ctypes.c_void_p()
+        _check(lib().ffc_form_create(kind, cell, degree, mu, lmbda, ctypes.byref(h)), "ffc_form_create")
+        self._h = h
+        self.kind, self.cell, self.degree = kind, cell, degree
+        n, na, nc = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(lib().ffc_form_info(h, ctypes.byref(n), ctypes.byref(na), ctypes.byref(nc)), "ffc_form_info")
+        self.n_local, self.n_alpha, self.n_coeff = n.value, na.value, nc.value
+
+    @property
+    def handle(self):
+        return self._h
+
+    @property
+    def dim(self) -> int:
+        return self.cell
+
+    def reference_tensor(self) -> np.ndarray:
+        out = np.empty((self.n_local * self.n_local, self.n_alpha), dtype=np.float64)
+        _check(lib().ffc_form_reference_tensor(self._h, out.ctypes.data_as(ctypes.c_void_p)),
+               "ffc_form_reference_tensor")
+        return out
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            lib().ffc_form_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def tabulate(form: Form, cells, vertices, coeffs=None, precision="fp64", out=None, stream=None):
+    """Element tensors [n_elem, n, n] (float64 for fp64, float32 otherwise)."""
+    import torch
+
+    p = _prec(precision)
+    n_elem = cells.shape[0]
+    n = form.n_local
+    dt = torch.float64 if p == FP64 else torch.float32
+    if out is None:
+        out = torch.empty((n_elem, n, n), dtype=dt, device=vertices.device)
+    c = _dev_ptr(cells, torch.int32, "cells", (n_elem, form.dim + 1))
+    v = _dev_ptr(vertices, torch.float64, "vertices")
+    w = _dev_ptr(coeffs, torch.float64, "coeffs", (n_elem, form.n_coeff)) if form.n_coeff else None
+    o = _dev_ptr(out, dt, "out", (n_elem, n, n))
+    _check(lib().ffc_tabulate(form.handle, n_elem, c, v, vertices.shape[0], w, o, p, _stream(stream)),
+           "ffc_tabulate")
+    return out
+
+
+def csr_pattern(dofmap: np.ndarray, n_dof: int, with_slots: bool = True):
+    """Sorted-column CSR pattern (row_ptr int64, col int32) and slots int32 [n_elem, n, n]."""
+    dm = np.ascontiguousarray(dofmap, dtype=np.int32)
+    n_elem, n = dm.shape
+    row_ptr = np.empty(n_dof + 1, dtype=np.int64)
+    nnz = ctypes.c_int64()
+    L = lib()
+    vp = lambda a: a.ctypes.data_as(ctypes.c_void_p)  # noqa: E731
+    _check(L.ffc_csr_pattern(n_elem, n, vp(dm), n_dof, vp(row_ptr), ctypes.byref(nnz), None, 0, None),
+           "ffc_csr_pattern")
+    col = np.empty(nnz.value, dtype=np.int32)
+    slot = np.empty((n_elem, n, n), dtype=np.int32) if with_slots else None
+    _check(L.ffc_csr_pattern(n_elem, n, vp(dm), n_dof, vp(row_ptr), ctypes.byref(nnz), vp(col), col.size,
+                             vp(slot) if slot is not None else None), "ffc_csr_pattern")
+    return row_ptr, col, slot
+
+
+def assemble(form: Form, cells, vertices, slot, csr_val, coeffs=None, precision="fp64", stream=None):
+    """csr_val[slot[e, i1, i2]] += A^K[e, i1, i2] for all cells (accumulates)."""
+    import torch
+
+    p = _prec(precision)
+    n_elem = cells.shape[0]
+    n = form.n_local
+    c = _dev_ptr(cells, torch.int32, "cells", (n_elem, form.dim + 1))
+    v = _dev_ptr(vertices, torch.float64, "vertices")
+    w = _dev_ptr(coeffs, torch.float64, "coeffs", (n_elem, form.n_coeff)) if form.n_coeff else None
+    s = _dev_ptr(slot, torch.int32, "slot", (n_elem, n, n))
+    val = _dev_ptr(csr_val, torch.float64, "csr_val")
+    _check(lib().ffc_assemble(form.handle, n_elem, c, v, vertices.shape[0], w, s, val, csr_val.numel(), p,
+                              _stream(stream)), "ffc_assemble")
+    return csr_val
+
+
+def tabulate_adjoint(form: Form, cells, vertices, dA_K, dvertices=None, stream=None):
+    """dL/dvertices (accumulated into ``dvertices``) for the upstream gradient dA_K."""
+    import torch
+
+    n_elem = cells.shape[0]
+    n = form.n_local
+    if dvertices is None:
+        dvertices = torch.zeros_like(vertices)
+    c = _dev_ptr(cells, torch.int32, "cells", (n_elem, form.dim + 1))
+    v = _dev_ptr(vertices, torch.float64, "vertices")
+    g = _dev_ptr(dA_K, torch.float64, "dA_K", (n_elem, n, n))
+    dv = _dev_ptr(dvertices, torch.float64, "dvertices", tuple(vertices.shape))
+    _check(lib().ffc_tabulate_adjoint(form.handle, n_elem, c, v, vertices.shape[0], g, dv, _stream(stream)),
+           "ffc_tabulate_adjoint")
+    return dvertices
+
+
+def status_poll(stream=None) -> int:
+    flags = ctypes.c_uint32()
+    _check(lib().ffc_status_poll(_stream(stream), ctypes.byref(flags)), "ffc_status_poll")
+    return flags.value

@@ -1,0 +1,183 @@
+// Device entry points of the C ABI: argument checks, lazy upload of the reference
+// tensor, the library-owned status word, and dispatch to the kernels.
+#include <cuda_runtime.h>
+
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "ffc_internal.h"
+
+namespace ffc {
+
+namespace {
+std::mutex g_status_lock;
+uint32_t* g_status[64] = {nullptr};
+
+int cuda_fail(cudaError_t e, const char* what) {
+  set_error(std::string(what) + ": " + cudaGetErrorString(e));
+  return FFC_ECUDA;
+}
+
+template <typename T>
+int upload(T** dst, const std::vector<T>& src) {
+  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(dst), src.size() * sizeof(T));
+  if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? FFC_ENOMEM : cuda_fail(e, "cudaMalloc");
+  e = cudaMemcpy(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice);
+  return e == cudaSuccess ? FFC_OK : cuda_fail(e, "cudaMemcpy");
+}
+}  // namespace
+
+uint32_t* status_word() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  std::lock_guard<std::mutex> g(g_status_lock);
+  if (!g_status[dev]) {
+    uint32_t* p = nullptr;
+    if (cudaMalloc(reinterpret_cast<void**>(&p), sizeof(uint32_t)) != cudaSuccess) return nullptr;
+    if (cudaMemset(p, 0, sizeof(uint32_t)) != cudaSuccess) return nullptr;
+    g_status[dev] = p;
+  }
+  return g_status[dev];
+}
+
+int ensure_device_tensors(ffc_form* f, DeviceTensors** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  std::lock_guard<std::mutex> g(f->lock);
+  auto it = f->dev.find(dev);
+  if (it != f->dev.end()) {
+    *out = &it->second;
+    return FFC_OK;
+  }
+  const size_t nn = size_t(f->n) * f->n, na = f->na;
+  std::vector<double> rows(f->A0), cols(nn * na);
+  for (size_t i = 0; i < nn; ++i)
+    for (size_t a = 0; a < na; ++a) cols[a * nn + i] = rows[i * na + a];
+  std::vector<float> rows32(rows.begin(), rows.end()), cols32(cols.begin(), cols.end());
+  DeviceTensors t;
+  int rc;
+  if ((rc = upload(&t.a0_f64, rows)) || (rc = upload(&t.a0t_f64, cols)) || (rc = upload(&t.a0_f32, rows32)) ||
+      (rc = upload(&t.a0t_f32, cols32))) {
+    cudaFree(t.a0_f64);
+    cudaFree(t.a0t_f64);
+    cudaFree(t.a0_f32);
+    cudaFree(t.a0t_f32);
+    return rc;
+  }
+  auto res = f->dev.emplace(dev, t);
+  *out = &res.first->second;
+  return FFC_OK;
+}
+
+void release_device_tensors(ffc_form* f) {
+  std::lock_guard<std::mutex> g(f->lock);
+  int cur = 0;
+  cudaGetDevice(&cur);
+  for (auto& kv : f->dev) {
+    cudaSetDevice(kv.first);
+    DeviceTensors& t = kv.second;
+    cudaFree(t.a0_f64);
+    cudaFree(t.a0t_f64);
+    cudaFree(t.a0_f32);
+    cudaFree(t.a0t_f32);
+    cudaFree(t.b_hi);
+    cudaFree(t.b_lo);
+  }
+  f->dev.clear();
+  cudaSetDevice(cur);
+}
+
+static int dispatch(const LaunchArgs& a, int precision, bool assemble) {
+  int rc = FFC_EUNSUPPORTED;
+  if (precision == FFC_FP64 || precision == FFC_FP32) {
+    rc = launch_simt_tri(a, precision, assemble);
+    if (rc == FFC_EUNSUPPORTED) rc = launch_simt_tet_mass(a, precision, assemble);
+    if (rc == FFC_EUNSUPPORTED) rc = launch_simt_tet_poisson(a, precision, assemble);
+    if (rc == FFC_EUNSUPPORTED) rc = launch_simt_vector(a, precision, assemble);
+  } else if (precision == FFC_TF32 || precision == FFC_TF32X3) {
+    rc = launch_tc(a, precision, assemble);
+  }
+  if (rc == FFC_ECUDA) set_error(std::string("kernel launch: ") + cudaGetErrorString(cudaGetLastError()));
+  if (rc == FFC_EUNSUPPORTED) set_error("no kernel built for this form/precision");
+  return rc;
+}
+
+static int common_checks(const ffc_form* f, int64_t n_elem, const int32_t* cells, const double* vertices,
+                         int64_t n_vert, const double* coeffs, int precision) {
+  if (!f || n_elem < 0 || n_vert < 0) return FFC_EINVAL;
+  if (precision < FFC_FP64 || precision > FFC_TF32X3) return FFC_EINVAL;
+  if (n_elem == 0) return FFC_OK;
+  if (!cells || !vertices || n_vert == 0) return FFC_EINVAL;
+  if (f->ncoeff > 0 && !coeffs) return FFC_EINVAL;
+  if ((reinterpret_cast<uintptr_t>(cells) & 15) || (reinterpret_cast<uintptr_t>(vertices) & 7)) return FFC_EINVAL;
+  return FFC_OK;
+}
+
+}  // namespace ffc
+
+using namespace ffc;
+
+extern "C" {
+
+int ffc_tabulate(const ffc_form* f, int64_t n_elem, const int32_t* cells, const double* vertices, int64_t n_vert,
+                 const double* coeffs, void* A_K, int precision, void* stream) {
+  int rc = common_checks(f, n_elem, cells, vertices, n_vert, coeffs, precision);
+  if (rc != FFC_OK) { set_error("ffc_tabulate: invalid argument"); return rc; }
+  if (n_elem == 0) return FFC_OK;
+  if (!A_K || (reinterpret_cast<uintptr_t>(A_K) & 15)) { set_error("ffc_tabulate: A_K"); return FFC_EINVAL; }
+  DeviceTensors* t = nullptr;
+  if ((rc = ensure_device_tensors(const_cast<ffc_form*>(f), &t)) != FFC_OK) return rc;
+  uint32_t* st = status_word();
+  if (!st) { set_error("status word allocation failed"); return FFC_ECUDA; }
+  LaunchArgs a{f, n_elem, cells, vertices, n_vert, coeffs, A_K, nullptr, nullptr, 0, t, st, stream};
+  return dispatch(a, precision, false);
+}
+
+int ffc_assemble(const ffc_form* f, int64_t n_elem, const int32_t* cells, const double* vertices, int64_t n_vert,
+                 const double* coeffs, const int32_t* slot, double* csr_val, int64_t nnz, int precision,
+                 void* stream) {
+  int rc = common_checks(f, n_elem, cells, vertices, n_vert, coeffs, precision);
+  if (rc != FFC_OK) { set_error("ffc_assemble: invalid argument"); return rc; }
+  if (n_elem == 0) return FFC_OK;
+  if (!slot || !csr_val || nnz <= 0 || nnz > INT32_MAX) { set_error("ffc_assemble: slot/csr"); return FFC_EINVAL; }
+  DeviceTensors* t = nullptr;
+  if ((rc = ensure_device_tensors(const_cast<ffc_form*>(f), &t)) != FFC_OK) return rc;
+  uint32_t* st = status_word();
+  if (!st) { set_error("status word allocation failed"); return FFC_ECUDA; }
+  LaunchArgs a{f, n_elem, cells, vertices, n_vert, coeffs, nullptr, slot, csr_val, nnz, t, st, stream};
+  return dispatch(a, precision, true);
+}
+
+int ffc_tabulate_adjoint(const ffc_form* f, int64_t n_elem, const int32_t* cells, const double* vertices,
+                         int64_t n_vert, const double* dA_K, double* dvertices, void* stream) {
+  int rc = common_checks(f, n_elem, cells, vertices, n_vert, nullptr, FFC_FP64);
+  if (rc != FFC_OK) { set_error("ffc_tabulate_adjoint: invalid argument"); return rc; }
+  if (f->kind != FFC_POISSON) { set_error("adjoint: Poisson forms only"); return FFC_EUNSUPPORTED; }
+  if (n_elem == 0) return FFC_OK;
+  if (!dA_K || !dvertices) return FFC_EINVAL;
+  DeviceTensors* t = nullptr;
+  if ((rc = ensure_device_tensors(const_cast<ffc_form*>(f), &t)) != FFC_OK) return rc;
+  uint32_t* st = status_word();
+  if (!st) return FFC_ECUDA;
+  LaunchArgs a{f, n_elem, cells, vertices, n_vert, nullptr, nullptr, nullptr, nullptr, 0, t, st, stream};
+  return launch_adjoint(a, dA_K, dvertices);
+}
+
+int ffc_status_poll(void* stream, uint32_t* flags) {
+  if (!flags) return FFC_EINVAL;
+  uint32_t* st = status_word();
+  if (!st) return FFC_ECUDA;
+  cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+  e = cudaMemcpy(flags, st, sizeof(uint32_t), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy status");
+  e = cudaMemset(st, 0, sizeof(uint32_t));
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemset status");
+  e = cudaDeviceSynchronize();
+  return e == cudaSuccess ? FFC_OK : cuda_fail(e, "cudaDeviceSynchronize");
+}
+
+}  // extern "C"

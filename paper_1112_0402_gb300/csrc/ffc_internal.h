@@ -1,0 +1,81 @@
+// Internal declarations shared by the host and device translation units of the
+// library. Nothing here is part of the C ABI.
+#pragma once
+
+#include <cstdint>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/ffc_gb300.h"
+
+namespace ffc {
+
+// Device copies of a reference tensor, created lazily per device.
+struct DeviceTensors {
+  double* a0_f64 = nullptr;   // [nn][na]  row i holds A0[i][alpha]
+  double* a0t_f64 = nullptr;  // [na][nn]  transposed (coalesced over i)
+  float* a0_f32 = nullptr;    // [nn][na]
+  float* a0t_f32 = nullptr;   // [na][nn]
+  // tcgen05 operands: K-major B tiles of A0 (rows = i, K = alpha padded), tf32 hi/lo
+  float* b_hi = nullptr;      // [nn_pad][k_pad]
+  float* b_lo = nullptr;      // [nn_pad][k_pad]
+  int nn_pad = 0, k_pad = 0;
+};
+
+}  // namespace ffc
+
+struct ffc_form {
+  int kind = 0;        // ffc_form_kind
+  int d = 0;           // spatial dimension
+  int q = 0;           // polynomial degree
+  int ns = 0;          // scalar local dofs
+  int n = 0;           // local dofs (ns or d*ns)
+  int na = 0;          // |alpha|
+  int ncoeff = 0;      // per-cell coefficients
+  double mu = 1.0, lambda = 1.25;
+  std::vector<double> A0;  // [n*n][na]
+  std::mutex lock;
+  std::map<int, ffc::DeviceTensors> dev;
+};
+
+namespace ffc {
+
+// Host form compiler (reference tensor by collapsed Gauss-Jacobi quadrature).
+int compile_reference_tensor(ffc_form* f);
+int n_scalar_local(int d, int q);
+
+// Error text for ffc_last_error.
+void set_error(const std::string& msg);
+
+// Device side (defined in .cu files).
+int ensure_device_tensors(ffc_form* f, DeviceTensors** out);
+void release_device_tensors(ffc_form* f);
+uint32_t* status_word();  // library-owned device status word of the current device
+
+struct LaunchArgs {
+  const ffc_form* f;
+  int64_t n_elem;
+  const int32_t* cells;
+  const double* vertices;
+  int64_t n_vert;
+  const double* coeffs;
+  void* out;              // A_K (tabulate)
+  const int32_t* slot;    // assemble
+  double* csr_val;        // assemble
+  int64_t nnz;            // assemble
+  const DeviceTensors* t;
+  uint32_t* status;
+  void* stream;
+};
+
+// Each returns FFC_EUNSUPPORTED when it has no instantiation for the form.
+int launch_simt_tri(const LaunchArgs& a, int precision, bool assemble);
+int launch_simt_tet_mass(const LaunchArgs& a, int precision, bool assemble);
+int launch_simt_tet_poisson(const LaunchArgs& a, int precision, bool assemble);
+int launch_simt_vector(const LaunchArgs& a, int precision, bool assemble);
+int launch_tc(const LaunchArgs& a, int precision, bool assemble);
+int launch_adjoint(const LaunchArgs& a, const double* dA, double* dvert);
+
+}  // namespace ffc

@@ -1,0 +1,153 @@
+// Per-cell geometry on the device: affine Jacobian J = [x_1 - x_0, ..., x_d - x_0],
+// |det J|, K = J^{-1} (all FP64), and the geometry tensor G_K of each form
+// (Section 3.2: G = c det F' prod dX/dx; Section 3.3 gives G for each test case).
+#pragma once
+
+#include <cstdint>
+
+#include "../../include/ffc_gb300.h"
+
+namespace ffc {
+
+constexpr int nscalar(int d, int q) { return d == 2 ? (q + 1) * (q + 2) / 2 : (q + 1) * (q + 2) * (q + 3) / 6; }
+constexpr int nlocal(int form, int d, int q) {
+  return (form == FFC_NS_CONVECTION || form == FFC_ELASTICITY) ? d * nscalar(d, q) : nscalar(d, q);
+}
+constexpr int nalpha(int form, int d, int q) {
+  return form == FFC_MASS ? 1
+       : form == FFC_POISSON ? d * d
+       : form == FFC_NS_CONVECTION ? nlocal(form, d, q) * d
+       : d * d * d * d;
+}
+
+// Gathers the cell's vertices and computes K = J^{-1} and |det J|.
+template <int D>
+__device__ __forceinline__ void cell_geometry(const int32_t* __restrict__ cells, const double* __restrict__ vertices,
+                                              int64_t n_vert, int64_t e, double K[D][D], double& det_abs,
+                                              bool& degenerate, bool& bad_index) {
+  double x[D + 1][D];
+  int id[D + 1];
+  if constexpr (D == 3) {
+    const int4 c = __ldg(reinterpret_cast<const int4*>(cells) + e);
+    id[0] = c.x;
+    id[1] = c.y;
+    id[2] = c.z;
+    id[3] = c.w;
+  } else {
+#pragma unroll
+    for (int j = 0; j < 3; ++j) id[j] = __ldg(cells + e * 3 + j);
+  }
+  bad_index = false;
+#pragma unroll
+  for (int j = 0; j <= D; ++j) {
+    // an out-of-range vertex id is reported and replaced by vertex 0 (never read out of bounds)
+    if (id[j] < 0 || id[j] >= n_vert) {
+      bad_index = true;
+      id[j] = 0;
+    }
+#pragma unroll
+    for (int r = 0; r < D; ++r) x[j][r] = __ldg(vertices + int64_t(id[j]) * D + r);
+  }
+  double J[D][D];
+#pragma unroll
+  for (int r = 0; r < D; ++r)
+#pragma unroll
+    for (int c = 0; c < D; ++c) J[r][c] = x[c + 1][r] - x[0][r];
+  double det;
+  if constexpr (D == 3) {
+    const double c00 = J[1][1] * J[2][2] - J[1][2] * J[2][1];
+    const double c01 = J[1][2] * J[2][0] - J[1][0] * J[2][2];
+    const double c02 = J[1][0] * J[2][1] - J[1][1] * J[2][0];
+    det = J[0][0] * c00 + J[0][1] * c01 + J[0][2] * c02;
+    const double inv = 1.0 / det;
+    // K = adj(J) / det; adj(J)[a][b] = cofactor(b, a)
+    K[0][0] = c00 * inv;
+    K[1][0] = c01 * inv;
+    K[2][0] = c02 * inv;
+    K[0][1] = (J[0][2] * J[2][1] - J[0][1] * J[2][2]) * inv;
+    K[1][1] = (J[0][0] * J[2][2] - J[0][2] * J[2][0]) * inv;
+    K[2][1] = (J[0][1] * J[2][0] - J[0][0] * J[2][1]) * inv;
+    K[0][2] = (J[0][1] * J[1][2] - J[0][2] * J[1][1]) * inv;
+    K[1][2] = (J[0][2] * J[1][0] - J[0][0] * J[1][2]) * inv;
+    K[2][2] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) * inv;
+  } else {
+    det = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+    const double inv = 1.0 / det;
+    K[0][0] = J[1][1] * inv;
+    K[0][1] = -J[0][1] * inv;
+    K[1][0] = -J[1][0] * inv;
+    K[1][1] = J[0][0] * inv;
+  }
+  det_abs = fabs(det);
+  double h2 = 0.0;
+#pragma unroll
+  for (int i = 0; i <= D; ++i)
+#pragma unroll
+    for (int j = i + 1; j <= D; ++j) {
+      double s = 0.0;
+#pragma unroll
+      for (int r = 0; r < D; ++r) s += (x[i][r] - x[j][r]) * (x[i][r] - x[j][r]);
+      h2 = fmax(h2, s);
+    }
+  const double h = sqrt(h2);
+  double hd = h;
+#pragma unroll
+  for (int r = 1; r < D; ++r) hd *= h;
+  degenerate = !(det_abs > 1e-14 * hd);
+}
+
+// Geometry tensor of the form, written as G[alpha] (alpha layouts documented in
+// form_compiler.cpp). `w` is the cell's coefficient vector (convection only).
+template <int D, int FORM, int Q, typename Store>
+__device__ __forceinline__ void geometry_tensor(const double K[D][D], double det, const double* w, double mu,
+                                                double lambda, Store&& store) {
+  if constexpr (FORM == FFC_MASS) {
+    store(0, det);
+  } else if constexpr (FORM == FFC_POISSON) {
+#pragma unroll
+    for (int a1 = 0; a1 < D; ++a1)
+#pragma unroll
+      for (int a2 = 0; a2 < D; ++a2) {
+        double s = 0.0;
+#pragma unroll
+        for (int b = 0; b < D; ++b) s += K[a1][b] * K[a2][b];
+        store(a1 * D + a2, det * s);
+      }
+  } else if constexpr (FORM == FFC_NS_CONVECTION) {
+    constexpr int NS = nscalar(D, Q);
+#pragma unroll
+    for (int ct = 0; ct < D; ++ct)
+#pragma unroll
+      for (int st = 0; st < NS; ++st) {
+        const int t = ct * NS + st;
+        const double dw = det * w[t];
+#pragma unroll
+        for (int a = 0; a < D; ++a) store(t * D + a, dw * K[a][ct]);
+      }
+  } else {  // elasticity
+    double KK[D][D];
+#pragma unroll
+    for (int a1 = 0; a1 < D; ++a1)
+#pragma unroll
+      for (int a2 = 0; a2 < D; ++a2) {
+        double s = 0.0;
+#pragma unroll
+        for (int b = 0; b < D; ++b) s += K[a1][b] * K[a2][b];
+        KK[a1][a2] = s;
+      }
+#pragma unroll
+    for (int b1 = 0; b1 < D; ++b1)
+#pragma unroll
+      for (int b2 = 0; b2 < D; ++b2)
+#pragma unroll
+        for (int a1 = 0; a1 < D; ++a1)
+#pragma unroll
+          for (int a2 = 0; a2 < D; ++a2) {
+            double g = mu * K[a1][b2] * K[a2][b1] + lambda * K[a1][b1] * K[a2][b2];
+            if (b1 == b2) g += mu * KK[a1][a2];
+            store(((b1 * D + b2) * D + a1) * D + a2, det * g);
+          }
+  }
+}
+
+}  // namespace ffc

@@ -1,0 +1,211 @@
+// CUDA-core kernels for the tensor representation A^K_i = A0_{i alpha} G_K^alpha
+// (Section 3.2, eq. (tensorproduct)) with an optional fused scatter into CSR
+// (Section 2.2, Algorithm 2).
+//
+// One CTA processes tiles of E consecutive cells (persistent grid-stride loop):
+//   phase 1  one thread per cell: FP64 geometry J, |det J|, J^{-1} and G_K -> shared
+//            memory (cast to the contraction type T);
+//   phase 2  the tile's E*n^2 outputs form one contiguous block of A_K. Thread t owns
+//            the element-tensor entries i = ti + r*NTI (r < R) for cells
+//            e = eg + k*EG, with t = eg*NTI + ti, so consecutive threads write
+//            consecutive addresses. Each output is sum_alpha G[e][alpha] A0[i][alpha];
+//            G is read from shared memory as a broadcast, A0 either sits in the
+//            thread's registers (small |alpha| * R) or is streamed from the L1/L2-
+//            resident transposed copy A0T[alpha][i], reused over KE cells.
+//   epilogue store (tabulate) or atomic add at csr_val[slot] in FP64 (assemble).
+#pragma once
+
+#include <cstdint>
+
+#include "geometry.cuh"
+
+namespace ffc {
+
+template <int D, int FORM, int Q, typename T>
+struct SimtCfg {
+  static constexpr int N = nlocal(FORM, D, Q);
+  static constexpr int NN = N * N;
+  static constexpr int NA = nalpha(FORM, D, Q);
+  static constexpr int VEC = 16 / int(sizeof(T));
+  static constexpr int NAP = (NA + VEC - 1) / VEC * VEC;
+  static constexpr int R = (NN + 511) / 512;
+  static constexpr int NTI = (NN + R - 1) / R;
+  static constexpr int EG = NTI >= 256 ? 1 : 256 / NTI;
+  static constexpr int NT = NTI * EG;
+  static constexpr bool REG_A0 = (R * NA * int(sizeof(T)) / 4) <= 96;
+  static constexpr int KE_TARGET = REG_A0 ? 64 : 16;
+  static constexpr int KE = (KE_TARGET + EG - 1) / EG;
+  static constexpr int E = EG * KE;
+  static constexpr int NCOEF = (FORM == FFC_NS_CONVECTION) ? N : 0;
+  static constexpr size_t SMEM = size_t(E) * NAP * sizeof(T) + size_t(E) * NCOEF * sizeof(double);
+};
+
+struct SimtParams {
+  const int32_t* cells;
+  const double* vertices;
+  long long n_vert;
+  const double* coeffs;
+  const void* a0;       // REG_A0: [NN][NA]; otherwise [NA][NN]
+  void* out;            // A_K [n_elem][NN]
+  const int32_t* slot;  // [n_elem][NN]
+  double* csr_val;
+  long long nnz;
+  long long n_elem;
+  double mu, lambda;
+  unsigned* status;
+};
+
+template <typename OutT>
+__device__ __forceinline__ void put(OutT* p, double v) {
+  __stcs(p, OutT(v));
+}
+
+template <int D, int FORM, int Q, typename T, bool ASSEMBLE>
+__global__ void __launch_bounds__(SimtCfg<D, FORM, Q, T>::NT)
+    simt_tabulate_kernel(SimtParams p) {
+  using C = SimtCfg<D, FORM, Q, T>;
+  using OutT = T;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* Gs = reinterpret_cast<T*>(smem_raw);                                     // [E][NAP]
+  double* Ws = reinterpret_cast<double*>(smem_raw + size_t(C::E) * C::NAP * sizeof(T));  // [E][NCOEF]
+
+  const int t = threadIdx.x;
+  const int ti = t % C::NTI;
+  const int eg = t / C::NTI;
+  const long long n_tiles = (p.n_elem + C::E - 1) / C::E;
+
+  T a0r[C::REG_A0 ? C::R : 1][C::REG_A0 ? C::NA : 1];
+  if constexpr (C::REG_A0) {
+    const T* A0 = static_cast<const T*>(p.a0);
+#pragma unroll
+    for (int r = 0; r < C::R; ++r) {
+      const int i = ti + r * C::NTI;
+#pragma unroll
+      for (int a = 0; a < C::NA; ++a) a0r[r][a] = (i < C::NN) ? A0[size_t(i) * C::NA + a] : T(0);
+    }
+  }
+
+  for (long long tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+    const long long e0 = tile * C::E;
+    // ---- phase 1: geometry tensors of the tile's cells
+    if constexpr (C::NCOEF > 0) {
+      const long long lim = (p.n_elem - e0) * C::NCOEF;
+      const double* src = p.coeffs + e0 * C::NCOEF;
+      for (int k = t; k < C::E * C::NCOEF; k += C::NT) Ws[k] = (k < lim) ? __ldg(src + k) : 0.0;
+      __syncthreads();
+    }
+    for (int el = t; el < C::E; el += C::NT) {
+      const long long e = e0 + el;
+      T* g = Gs + el * C::NAP;
+      if (e < p.n_elem) {
+        double K[D][D], det;
+        bool degenerate, bad_index;
+        cell_geometry<D>(p.cells, p.vertices, p.n_vert, e, K, det, degenerate, bad_index);
+        if (degenerate) atomicOr(p.status, FFC_FLAG_DEGENERATE);
+        if (bad_index) atomicOr(p.status, FFC_FLAG_BOUNDS);
+        geometry_tensor<D, FORM, Q>(K, det, Ws + el * C::NCOEF, p.mu, p.lambda,
+                                    [&](int a, double v) { g[a] = T(v); });
+      } else {
+#pragma unroll 1
+        for (int a = 0; a < C::NA; ++a) g[a] = T(0);
+      }
+#pragma unroll
+      for (int a = C::NA; a < C::NAP; ++a) g[a] = T(0);
+    }
+    __syncthreads();
+    // ---- phase 2: contraction and epilogue
+    if constexpr (C::REG_A0) {
+#pragma unroll 1
+      for (int k = 0; k < C::KE; ++k) {
+        const int el = eg + k * C::EG;
+        const long long e = e0 + el;
+        if (e >= p.n_elem) break;
+        const T* g = Gs + el * C::NAP;
+        T acc[C::R];
+#pragma unroll
+        for (int r = 0; r < C::R; ++r) acc[r] = T(0);
+#pragma unroll
+        for (int a = 0; a < C::NA; ++a) {
+          const T gv = g[a];
+#pragma unroll
+          for (int r = 0; r < C::R; ++r) acc[r] = fma(gv, a0r[r][a], acc[r]);
+        }
+#pragma unroll
+        for (int r = 0; r < C::R; ++r) {
+          const int i = ti + r * C::NTI;
+          if (i < C::NN) {
+            const long long o = e * C::NN + i;
+            if constexpr (ASSEMBLE) {
+              const int s = __ldg(p.slot + o);
+              if (s >= 0 && s < p.nnz) atomicAdd(p.csr_val + s, double(acc[r]));
+              else atomicOr(p.status, FFC_FLAG_BOUNDS);
+            } else {
+              put(static_cast<OutT*>(p.out) + o, double(acc[r]));
+            }
+          }
+        }
+      }
+    } else {
+      const T* A0T = static_cast<const T*>(p.a0);
+#pragma unroll 1
+      for (int r = 0; r < C::R; ++r) {
+        const int i = ti + r * C::NTI;
+        if (i >= C::NN) break;
+        T acc[C::KE];
+#pragma unroll
+        for (int k = 0; k < C::KE; ++k) acc[k] = T(0);
+#pragma unroll 2
+        for (int a = 0; a < C::NA; ++a) {
+          const T av = __ldg(A0T + size_t(a) * C::NN + i);
+#pragma unroll
+          for (int k = 0; k < C::KE; ++k) acc[k] = fma(Gs[(eg + k * C::EG) * C::NAP + a], av, acc[k]);
+        }
+#pragma unroll
+        for (int k = 0; k < C::KE; ++k) {
+          const long long e = e0 + eg + k * C::EG;
+          if (e < p.n_elem) {
+            const long long o = e * C::NN + i;
+            if constexpr (ASSEMBLE) {
+              const int s = __ldg(p.slot + o);
+              if (s >= 0 && s < p.nnz) atomicAdd(p.csr_val + s, double(acc[k]));
+              else atomicOr(p.status, FFC_FLAG_BOUNDS);
+            } else {
+              put(static_cast<OutT*>(p.out) + o, double(acc[k]));
+            }
+          }
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Host-side launcher for one instantiation.
+template <int D, int FORM, int Q, typename T, bool ASSEMBLE>
+int launch_simt_one(const SimtParams& prm, const void* a0_rows, const void* a0_cols, cudaStream_t stream) {
+  using C = SimtCfg<D, FORM, Q, T>;
+  auto kern = simt_tabulate_kernel<D, FORM, Q, T, ASSEMBLE>;
+  static int blocks_per_sm = -1;
+  static int sms = 0;
+  if (blocks_per_sm < 0) {
+    if (C::SMEM > 48 * 1024)
+      if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(C::SMEM)) != cudaSuccess)
+        return FFC_ECUDA;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, C::NT, C::SMEM) != cudaSuccess) return FFC_ECUDA;
+    blocks_per_sm = b > 0 ? b : 1;
+  }
+  SimtParams p = prm;
+  p.a0 = C::REG_A0 ? a0_rows : a0_cols;
+  const long long n_tiles = (p.n_elem + C::E - 1) / C::E;
+  long long grid = (long long)sms * blocks_per_sm;
+  if (grid > n_tiles) grid = n_tiles;
+  if (grid < 1) grid = 1;
+  kern<<<unsigned(grid), C::NT, C::SMEM, stream>>>(p);
+  return cudaPeekAtLastError() == cudaSuccess ? FFC_OK : FFC_ECUDA;
+}
+
+}  // namespace ffc
