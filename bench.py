@@ -1,0 +1,432 @@
+#!/usr/bin/env python3
+"""Throughput of the tensor-representation hot path on one GB300 (or N replicas).
+
+Workload: unit cube, 48^3 hexes x 6 Kuhn tetrahedra (663,552 cells, 117,649
+vertices), interior vertices jittered by +-0.15h (seed 2); the mass and Poisson
+forms with scalar Lagrange P1..P4 -- eight (form, degree) problems.
+
+One step = for each of the eight problems: zero the CSR values and run the fused
+assembly (geometry G_K -> contraction A0:G_K -> atomic scatter into CSR through the
+precomputed slots), i.e. Algorithm 2 with the tensor representation. The headline
+`value` is element tensors computed and inserted per second over the whole step
+(8 x 663,552 per step); `nnz_per_s` is the assembled CSR entries per second.
+
+Also measured (reported under "detail"): ffc_tabulate alone (A_K written to HBM)
+for each problem in FP64 and in the mixed-precision path, the FP64 assembly, and
+the mixed path's error against the FP64 path.
+
+The oracle (a plain CPU quadrature evaluator) is timed as the CPU baseline on a
+bounded sample of the same workload, using the host cores of this machine.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOAD = "tet_scalar_48"
+FORMS = (0, 1)  # mass, Poisson
+DEGREES = (1, 2, 3, 4)
+FORM_NAME = {0: "mass", 1: "poisson"}
+METRIC = "element tensors/s (assembled, mass+Poisson P1..P4 on 48^3x6 tets)"
+REF_FRACTION = 1.0 / 16   # share of each problem's cells in one sampled oracle step
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", default="fp32", help="contraction arithmetic of the headline step")
+    ap.add_argument("--n", type=int, default=48, help="hexes per axis")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-detail", action="store_true")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("pci.bus_id,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, bus_id: str | None):
+        self.bus_id = (bus_id or "").lower()
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                       "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+        time.sleep(0.3)
+
+    def stop(self) -> dict:
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.3)
+        self.p.terminate()
+        self.p.wait()
+        self.f.flush()
+        rows = [r.split(",") for r in open(self.f.name).read().strip().splitlines() if r.count(",") >= 8]
+        os.unlink(self.f.name)
+        if self.bus_id:
+            mine = [r for r in rows if r[0].strip().lower().endswith(self.bus_id[-12:])]
+            rows = mine or rows
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for k, name in enumerate(names):
+                if r[5 + k].strip().lower() == "active":
+                    reasons.add(name)
+        power = [float(r[3]) for r in rows if r[3].strip().replace(".", "").isdigit()]
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(rows),
+                "power_w_max": max(power) if power else None}
+
+
+# ------------------------------------------------------------------ workload
+def build_workload(F, n, device):
+    import torch
+
+    from synthetic import workloads as W
+
+    mesh = W.tet_scalar_mesh(n)
+    ctx = {"mesh": mesh, "cells": torch.as_tensor(mesh.cells, device=device),
+           "verts": torch.as_tensor(mesh.vertices, device=device), "problems": []}
+    for q in DEGREES:
+        p = W.make_problem(mesh, W.POISSON, q)
+        row_ptr, col, slot = F.csr_pattern(p.dofmap, p.n_dof)
+        slot_d = torch.as_tensor(slot, device=device)
+        del slot
+        for form in FORMS:
+            ctx["problems"].append({
+                "form": form, "q": q, "F": F.Form(form, F.TETRAHEDRON, q), "n_local": p.n_local,
+                "nnz": int(col.size), "n_dof": p.n_dof, "slot": slot_d,
+                "val": torch.zeros(int(col.size), dtype=torch.float64, device=device)})
+    return ctx
+
+
+def assemble_step(F, ctx, precision, events=None):
+    for k, pr in enumerate(ctx["problems"]):
+        if events is not None:
+            events[k][0].record()
+        pr["val"].zero_()
+        F.assemble(pr["F"], ctx["cells"], ctx["verts"], pr["slot"], pr["val"], precision=precision)
+        if events is not None:
+            events[k][1].record()
+
+
+def alg_bytes_assemble(ctx, pr):
+    """Algorithmic bytes of one fused assembly: cells + vertices + dofmap + CSR values
+    read and written once (slot map not counted)."""
+    m = ctx["mesh"]
+    return m.n_elem * 16 + m.n_vert * 24 + m.n_elem * 4 * pr["n_local"] + 16 * pr["nnz"]
+
+
+def alg_bytes_tabulate(ctx, n_local, out_bytes):
+    m = ctx["mesh"]
+    return m.n_elem * 16 + m.n_vert * 24 + m.n_elem * n_local * n_local * out_bytes
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------------ CPU oracle baseline
+def _oracle_chunk(args):
+    form, q, verts, dofmap, n_dof = args
+    from oracle import assemble as OA
+    from oracle import element as OE
+
+    A = OE.element_tensors(form, verts, q)
+    OA.assemble_csr(A, dofmap, n_dof)
+    return verts.shape[0]
+
+
+def cpu_oracle_step(n, frac, pool):
+    """One sampled oracle step: the same fraction `frac` of the cells of each of the
+    eight problems (cells spread evenly over the mesh), element tensors by quadrature
+    and their Algorithm-2 insertion, split over the pool's host cores.
+    Returns (cells per problem, seconds)."""
+    from synthetic import mesh as M
+    from synthetic import workloads as W
+
+    cores = pool._processes
+    mesh = W.tet_scalar_mesh(n)
+    S = max(cores, int(round(mesh.n_elem * frac)))
+    idx = np.linspace(0, mesh.n_elem - 1, S).astype(np.int64)
+    verts = M.gather_cell_vertices(mesh)[idx]
+    jobs = []
+    for q in DEGREES:
+        p = W.make_problem(mesh, W.POISSON, q)
+        dm = p.dofmap[idx]
+        for form in FORMS:
+            jobs += [(form, q, verts[c::cores], dm[c::cores], p.n_dof) for c in range(cores)]
+    t0 = time.perf_counter()
+    done = sum(pool.map(_oracle_chunk, jobs, chunksize=1))
+    dt = time.perf_counter() - t0
+    assert done == S * len(FORMS) * len(DEGREES)
+    return S, dt
+
+
+def oracle_pool():
+    import multiprocessing as mp
+
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    pool = mp.get_context("spawn").Pool(cores)
+    warm = (0, 1, np.zeros((1, 4, 3)) + np.eye(4, 3)[None], np.zeros((1, 4), np.int32), 1)
+    pool.map(_oracle_chunk, [warm] * cores)
+    return pool, cores
+
+
+# ------------------------------------------------------------------ reference arm
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    pool, cores = oracle_pool()
+    times = []
+    S = 0
+    for it in range(args.warmup + args.steps):
+        S, t = cpu_oracle_step(args.n, REF_FRACTION, pool)
+        if it >= args.warmup:
+            times.append(t)
+    pool.close()
+    pool.join()
+    t = statistics.mean(times)
+    value = len(FORMS) * len(DEGREES) * S / t
+    sample = (f"{S} of the cells (1/{round(1 / REF_FRACTION)}) of each of the 8 problems per step, "
+              "spread evenly over the mesh; same problem mix as the full step")
+    line = {"metric": METRIC, "value": value, "unit": "elem/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": WORKLOAD, "cells_per_problem_per_step": S},
+            "cpu_baseline": {"value": value, "unit": "elem/s", "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "elem/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ main arm
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    device = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(device)
+
+    # the CPU oracle pool starts before the first GPU call
+    cpu = None
+    pool = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        pool, cores = oracle_pool()
+
+    from paper_1112_0402_gb300 import build as B
+
+    B.build()
+    import paper_1112_0402_gb300 as F
+
+    ctx = build_workload(F, args.n, device)
+    P = len(ctx["problems"])
+    n_elem = ctx["mesh"].n_elem
+    total_nnz = sum(pr["nnz"] for pr in ctx["problems"])
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        assemble_step(F, ctx, args.precision)
+    assert F.status_poll() == 0
+    events = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(P * args.steps)]
+    bus = None
+    try:
+        bus = torch.cuda.get_device_properties(device).pci_bus_id  # noqa
+    except Exception:
+        bus = None
+    clocks = ClockSampler(bus)
+    clocks.start()
+    barrier()
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    start.record()
+    for s in range(args.steps):
+        assemble_step(F, ctx, args.precision, events[s * P:(s + 1) * P])
+    stop.record()
+    barrier()
+    clk = clocks.stop()
+    elapsed = start.elapsed_time(stop) / 1e3
+    t_max = torch.tensor([elapsed], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
+    elapsed = float(t_max.item())
+    assert F.status_poll() == 0
+    per_launch = np.zeros(P)
+    for s in range(args.steps):
+        for k in range(P):
+            ev = events[s * P + k]
+            per_launch[k] += ev[0].elapsed_time(ev[1]) / 1e3
+    per_launch /= args.steps
+    dom = int(np.argmax(per_launch))
+    dpr = ctx["problems"][dom]
+    hbm_peak, peak_kind = measured_peaks()
+    achieved = alg_bytes_assemble(ctx, dpr) / per_launch[dom] / 1e9
+    value = world * P * n_elem / elapsed * args.steps
+
+    # ---- end to end through the C ABI: pinned host inputs in, CSR values out
+    e2e = None
+    if not args.no_e2e:
+        h_cells = torch.as_tensor(ctx["mesh"].cells).pin_memory()
+        h_verts = torch.as_tensor(ctx["mesh"].vertices).pin_memory()
+        h_out = [torch.empty(pr["nnz"], dtype=torch.float64).pin_memory() for pr in ctx["problems"]]
+        d_cells = torch.empty_like(ctx["cells"])
+        d_verts = torch.empty_like(ctx["verts"])
+
+        def e2e_step():
+            d_cells.copy_(h_cells, non_blocking=True)
+            d_verts.copy_(h_verts, non_blocking=True)
+            for pr, ho in zip(ctx["problems"], h_out):
+                pr["val"].zero_()
+                F.assemble(pr["F"], d_cells, d_verts, pr["slot"], pr["val"], precision=args.precision)
+                ho.copy_(pr["val"], non_blocking=True)
+
+        for _ in range(max(1, args.warmup)):
+            e2e_step()
+        barrier()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(args.steps):
+            e2e_step()
+        b.record()
+        barrier()
+        te = a.elapsed_time(b) / 1e3
+        t_e = torch.tensor([te], dtype=torch.float64, device=device)
+        if world > 1:
+            dist.all_reduce(t_e, op=dist.ReduceOp.MAX)
+        te = float(t_e.item())
+        e2e = {"value": world * P * n_elem * args.steps / te, "unit": "elem/s",
+               "h2d_bytes_per_step": int(h_cells.numel() * 4 + h_verts.numel() * 8),
+               "d2h_bytes_per_step": int(sum(pr["nnz"] for pr in ctx["problems"]) * 8),
+               "ms_per_step": te / args.steps * 1e3}
+
+    detail = None
+    if rank == 0 and not args.no_detail:
+        detail = measure_detail(F, ctx, args, device)
+
+    if pool is not None:
+        S, t_cpu = cpu_oracle_step(args.n, 2 * REF_FRACTION, pool)
+        pool.close()
+        pool.join()
+        cpu = {"value": P * S / t_cpu, "unit": "elem/s", "cores": cores, "kind": "oracle",
+               "sample": f"{S} cells (1/8) of each of the 8 problems, spread evenly over the mesh, "
+                         f"{t_cpu:.1f} s; same problem mix as the GPU step"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC,
+            "value": value, "unit": "elem/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": elapsed / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32" if args.precision != "fp64" else "f64", "data": "synthetic",
+            "nnz_per_s": world * total_nnz * args.steps / elapsed,
+            "config": {"workload": WORKLOAD, "cells": n_elem, "vertices": ctx["mesh"].n_vert,
+                       "problems": [f"{FORM_NAME[p['form']]}_p{p['q']}" for p in ctx["problems"]],
+                       "contraction": args.precision, "csr_accumulation": "f64", "nnz_total": total_nnz,
+                       "l2": "inputs larger than L2: the step streams ~20 GB (CSR values, slots) per pass",
+                       "parallelism": f"replicas x{world}"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                         "frac": achieved / hbm_peak, "traffic": None, "peak_kind": peak_kind,
+                         "kernel": f"assemble {FORM_NAME[dpr['form']]} P{dpr['q']} ({args.precision})",
+                         "launch_ms": per_launch[dom] * 1e3},
+            "per_launch_ms": {f"{FORM_NAME[p['form']]}_p{p['q']}": round(per_launch[k] * 1e3, 4)
+                              for k, p in enumerate(ctx["problems"])},
+            "clocks": clk, "gpu_launches": P * args.steps, "e2e": e2e, "cpu_baseline": cpu, "detail": detail,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def measure_detail(F, ctx, args, device, reps=5):
+    """ffc_tabulate alone per problem, FP64 vs the mixed path, plus FP64 assembly."""
+    import torch
+
+    out = {}
+    hbm_peak, _ = measured_peaks()
+    n_elem = ctx["mesh"].n_elem
+    for pr in ctx["problems"]:
+        key = f"{FORM_NAME[pr['form']]}_p{pr['q']}"
+        n = pr["n_local"]
+        rec = {}
+        ref = None
+        for prec in ("fp64", args.precision):
+            dt = torch.float64 if prec == "fp64" else torch.float32
+            A = torch.empty((n_elem, n, n), dtype=dt, device=device)
+            F.tabulate(pr["F"], ctx["cells"], ctx["verts"], out=A, precision=prec)
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            for _ in range(reps):
+                F.tabulate(pr["F"], ctx["cells"], ctx["verts"], out=A, precision=prec)
+            b.record()
+            torch.cuda.synchronize()
+            t = a.elapsed_time(b) / 1e3 / reps
+            byts = alg_bytes_tabulate(ctx, n, 8 if prec == "fp64" else 4)
+            r = {"elem_per_s": n_elem / t, "ms": t * 1e3, "hbm_frac": byts / t / 1e9 / hbm_peak}
+            if prec == "fp64":
+                ref = A
+            else:
+                d = (A.double() - ref).reshape(n_elem, -1).norm(dim=1) / ref.reshape(n_elem, -1).norm(dim=1)
+                r["max_rel_err_vs_fp64"] = float(d.max().item())
+                r["mean_rel_err_vs_fp64"] = float(d.mean().item())
+            rec[prec] = r
+            del A
+        ref = None
+        torch.cuda.empty_cache()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            pr["val"].zero_()
+            F.assemble(pr["F"], ctx["cells"], ctx["verts"], pr["slot"], pr["val"], precision="fp64")
+        b.record()
+        torch.cuda.synchronize()
+        rec["assemble_fp64_ms"] = a.elapsed_time(b) / reps
+        out[key] = rec
+    assert F.status_poll() == 0
+    return out
+
+
+if __name__ == "__main__":
+    sys.exit(main())

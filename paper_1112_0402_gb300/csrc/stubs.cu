@@ -2,6 +2,5 @@
 #include "ffc_internal.h"
 
 namespace ffc {
-int launch_tc(const LaunchArgs&, int, bool) { return FFC_EUNSUPPORTED; }
 int launch_adjoint(const LaunchArgs&, const double*, double*) { return FFC_EUNSUPPORTED; }
 }  // namespace ffc
