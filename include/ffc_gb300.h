@@ -166,6 +166,30 @@ int ffc_tabulate_adjoint(const ffc_form* f, int64_t n_elem, const int32_t* cells
  */
 int ffc_status_poll(void* stream, uint32_t* flags);
 
+/*
+ * ffc_tabulate_static -- ffc_tabulate for callers that cannot allocate device memory.
+ * The paper has no counterpart; this is a deployment variant of ffc_tabulate.
+ *
+ * Frameworks that route every device allocation through their own pool, and
+ * applications that fix their device memory before loading this library, cannot
+ * let the library call cudaMalloc. This entry point allocates nothing: the
+ * reference tensor and the status word live in one fixed 2 MiB (+256 B) device
+ * array compiled into the library, which every GPU that loads the library holds
+ * until the process exits. The caller passes inputs and outputs as for ffc_tabulate.
+ *   precision   FFC_FP64 or FFC_FP32 only
+ *   host_flags  NULL, or receives the FFC_FLAG_* bits of this call; when non-NULL
+ *               the call synchronises `stream` before returning
+ * Forms whose reference tensor does not fit (4 copies of n*n*|alpha| values, e.g.
+ * elasticity P3) are rejected with FFC_EINVAL before any device work.
+ * The first call on a device looks up the array's device address (with that device
+ * current); make it before any stream capture. All calls share the array and leave
+ * their contents in it: each call clears the status word and rewrites the reference
+ * tensor, so calls that overlap on the GPU race and must be serialised by the caller.
+ */
+int ffc_tabulate_static(const ffc_form* f, int64_t n_elem, const int32_t* cells, const double* vertices,
+                        int64_t n_vert, const double* coeffs, void* A_K, int precision, void* stream,
+                        uint32_t* host_flags);
+
 /* Human-readable name of a status code (static string). */
 const char* ffc_status_string(int status);
 

@@ -31,6 +31,8 @@ SIGNATURES = {
     "ffc_assemble": (ctypes.c_int, [c_vp, ctypes.c_int64, c_vp, c_vp, ctypes.c_int64, c_vp, c_vp, c_vp,
                                     ctypes.c_int64, ctypes.c_int, c_vp]),
     "ffc_tabulate_adjoint": (ctypes.c_int, [c_vp, ctypes.c_int64, c_vp, c_vp, ctypes.c_int64, c_vp, c_vp, c_vp]),
+    "ffc_tabulate_static": (ctypes.c_int, [c_vp, ctypes.c_int64, c_vp, c_vp, ctypes.c_int64, c_vp, c_vp,
+                                           ctypes.c_int, c_vp, c_u32p]),
     "ffc_status_poll": (ctypes.c_int, [c_vp, c_u32p]),
     "ffc_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "ffc_last_error": (ctypes.c_char_p, []),
