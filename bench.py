@@ -49,6 +49,8 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=["tet_scalar", "ns_vp2", "batched", "adjoint"], default="tet_scalar",
+                    help="tet_scalar is the headline; the others print their own line")
     ap.add_argument("--precision", default="fp32", help="contraction arithmetic of the headline step")
     ap.add_argument("--n", type=int, default=48, help="hexes per axis")
     ap.add_argument("--no-e2e", action="store_true")
@@ -235,6 +237,8 @@ def main():
     args = parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload != "tet_scalar":
+        return run_other(args)
     import torch
     import torch.distributed as dist
 
@@ -426,6 +430,210 @@ def measure_detail(F, ctx, args, device, reps=5):
         out[key] = rec
     assert F.status_poll() == 0
     return out
+
+
+# ------------------------------------------------------------------ other workloads
+def _timed(fn, steps, warmup):
+    import torch
+
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(steps):
+        fn()
+    b.record()
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / 1e3 / steps
+
+
+def _oracle_rate(form, q, verts, coeffs, cores, seconds=4.0):
+    """Oracle element tensors per second on `cores` host processes (bounded sample)."""
+    import multiprocessing as mp
+
+    pool = mp.get_context("spawn").Pool(cores)
+    try:
+        probe = max(cores, 64)
+        t0 = time.perf_counter()
+        pool.map(_oracle_tensors, [(form, q, verts[:probe:1][c::cores], None if coeffs is None else
+                                    coeffs[:probe][c::cores]) for c in range(cores)])
+        rate = probe / (time.perf_counter() - t0)
+        S = min(verts.shape[0], max(cores, int(rate * seconds)))
+        t0 = time.perf_counter()
+        pool.map(_oracle_tensors, [(form, q, verts[:S][c::cores], None if coeffs is None else coeffs[:S][c::cores])
+                                   for c in range(cores)])
+        return S / (time.perf_counter() - t0), S
+    finally:
+        pool.close()
+        pool.join()
+
+
+def _oracle_tensors(args):
+    form, q, verts, coeffs = args
+    from oracle import element as OE
+
+    OE.element_tensors(form, verts, q, coeffs=coeffs)
+    return verts.shape[0]
+
+
+def run_other(args):
+    import torch
+
+    from paper_1112_0402_gb300 import build as B
+
+    B.build()
+    import paper_1112_0402_gb300 as F
+    from synthetic import mesh as M
+    from synthetic import workloads as W
+
+    device = torch.device("cuda", 0)
+    hbm_peak, peak_kind = measured_peaks()
+    cores = len(os.sched_getaffinity(0))
+    clocks = ClockSampler(None)
+    out = {"metric": None, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "data": "synthetic", "unit": "elem/s"}
+    if args.workload == "ns_vp2":
+        p = W.ns_vp2(40 if args.n == 48 else args.n)
+        m = p.mesh
+        cells = torch.as_tensor(m.cells, device=device)
+        verts = torch.as_tensor(m.vertices, device=device)
+        coeffs = torch.as_tensor(p.coeffs, device=device)
+        fm = F.Form(F.NS_CONVECTION, F.TETRAHEDRON, 2)
+        row_ptr, col, slot = F.csr_pattern(p.dofmap, p.n_dof)
+        slot_d = torch.as_tensor(slot, device=device)
+        del slot
+        val = torch.zeros(col.size, dtype=torch.float64, device=device)
+        detail = {}
+        ref = None
+        for prec in ("fp64", "fp32", "tf32", "tf32x3", "bf16x3"):
+            dt = torch.float64 if prec == "fp64" else torch.float32
+            A = torch.empty((m.n_elem, 30, 30), dtype=dt, device=device)
+            t = _timed(lambda: F.tabulate(fm, cells, verts, coeffs=coeffs, out=A, precision=prec), args.steps,
+                       args.warmup)
+            byts = m.n_elem * (16 + 240 + 900 * (8 if prec == "fp64" else 4)) + m.n_vert * 24
+            r = {"elem_per_s": m.n_elem / t, "ms": t * 1e3, "hbm_frac": byts / t / 1e9 / hbm_peak}
+            if ref is None:
+                ref = A
+            else:
+                d = (A.double() - ref).reshape(m.n_elem, -1).norm(dim=1) / ref.reshape(m.n_elem, -1).norm(dim=1)
+                r["max_rel_err_vs_fp64"] = float(d.max())
+            detail["tabulate_" + prec] = r
+            if prec != "fp64":
+                del A
+        del ref
+        torch.cuda.empty_cache()
+        for prec in ("fp64", "bf16x3"):
+            def step():
+                val.zero_()
+                F.assemble(fm, cells, verts, slot_d, val, coeffs=coeffs, precision=prec)
+            detail["assemble_" + prec + "_ms"] = _timed(step, max(1, args.steps // 2), 1) * 1e3
+        prec = "bf16x3"
+        A32 = torch.empty((m.n_elem, 30, 30), dtype=torch.float32, device=device)
+        clocks.start()
+        t = _timed(lambda: F.tabulate(fm, cells, verts, coeffs=coeffs, out=A32, precision=prec), args.steps,
+                   args.warmup)
+        clk = clocks.stop()
+        byts = m.n_elem * (16 + 240 + 3600) + m.n_vert * 24
+        rate, S = _oracle_rate(W.NS_CONVECTION, 2, M.gather_cell_vertices(m), p.coeffs, cores)
+        out.update({"metric": "element tensors/s (vector-P2 convection, 40^3x6 tets, tabulate)",
+                    "value": m.n_elem / t, "ms_per_step": t * 1e3, "dtype": "bf16x3",
+                    "config": {"workload": "ns_vp2", "cells": m.n_elem, "nnz": int(col.size),
+                               "contraction": prec, "l2": "A_K output 1.38 GB per step > L2"},
+                    "roofline": {"bound": "hbm", "achieved": byts / t / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                                 "frac": byts / t / 1e9 / hbm_peak, "traffic": None, "peak_kind": peak_kind,
+                                 "kernel": "tc_tabulate_kernel convection P2 bf16x3"},
+                    "clocks": clk, "gpu_launches": args.steps,
+                    "cpu_baseline": {"value": rate, "unit": "elem/s", "cores": cores, "kind": "oracle",
+                                     "sample": f"{S} cells"}, "detail": detail})
+    elif args.workload == "batched":
+        probs = W.batched()
+        items = []
+        total_nnz = 0
+        for pb in probs:
+            row_ptr, col, slot = F.csr_pattern(pb.dofmap, pb.n_dof)
+            items.append({"form": F.Form(pb.form, F.TETRAHEDRON, pb.degree),
+                          "cells": torch.as_tensor(pb.mesh.cells, device=device),
+                          "vertices": torch.as_tensor(pb.mesh.vertices, device=device),
+                          "slot": torch.as_tensor(slot, device=device),
+                          "csr_val": torch.zeros(col.size, dtype=torch.float64, device=device)})
+            total_nnz += int(col.size)
+            del slot
+        n_cells = sum(pb.n_elem for pb in probs)
+        b = F.Batch(items, zero_csr=True)
+        ke = b.tune()
+        t_plain = _timed(lambda: b.run(graph=False), args.steps, args.warmup)
+        clocks.start()
+        t = _timed(lambda: b.run(graph=True), args.steps, args.warmup)
+        clk = clocks.stop()
+        assert F.status_poll() == 0
+        # per-problem launches of the same work, for comparison
+        def separate():
+            for it in items:
+                it["csr_val"].zero_()
+                F.assemble(it["form"], it["cells"], it["vertices"], it["slot"], it["csr_val"], precision="fp32")
+        t_sep = _timed(separate, args.steps, args.warmup)
+        byts = sum(pb.n_elem * (16 + 4 * pb.n_local) + pb.mesh.n_vert * 24 for pb in probs) + 16 * total_nnz
+        out.update({"metric": "element tensors/s (batched: 32 meshes, elasticity vP1-vP3 + Poisson P2)",
+                    "value": n_cells / t, "ms_per_step": t * 1e3, "dtype": "f32", "nnz_per_s": total_nnz / t,
+                    "config": {"workload": "batched", "meshes": len(probs), "cells": n_cells, "nnz": total_nnz,
+                               "tile_cells_per_group": ke, "graph": True},
+                    "roofline": {"bound": "hbm", "achieved": byts / t / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                                 "frac": byts / t / 1e9 / hbm_peak, "traffic": None, "peak_kind": peak_kind,
+                                 "kernel": "batch_assemble_kernel"},
+                    "clocks": clk, "gpu_launches": args.steps,
+                    "detail": {"plain_launch_ms": t_plain * 1e3, "separate_launches_ms": t_sep * 1e3}})
+    else:  # adjoint
+        p, u, v = W.adjoint_p2(56 if args.n == 48 else args.n)
+        m = p.mesh
+        cells = torch.as_tensor(m.cells, device=device)
+        verts = torch.as_tensor(m.vertices, device=device)
+        dm = torch.as_tensor(p.dofmap.astype(np.int64), device=device)
+        uK = torch.as_tensor(u, device=device)[dm]
+        vK = torch.as_tensor(v, device=device)[dm]
+        dA = torch.einsum("ei,ej->eij", uK, vK).contiguous()
+        fm = F.Form(F.POISSON, F.TETRAHEDRON, 2)
+        dv = torch.zeros_like(verts)
+        A = torch.empty((m.n_elem, 10, 10), dtype=torch.float64, device=device)
+        t_fwd = _timed(lambda: F.tabulate(fm, cells, verts, out=A), args.steps, args.warmup)
+        clocks.start()
+        t = _timed(lambda: F.tabulate_adjoint(fm, cells, verts, dA, dvertices=dv), args.steps, args.warmup)
+        clk = clocks.stop()
+        assert F.status_poll() == 0
+        byts = m.n_elem * (16 + 800 + 12 * 8) + m.n_vert * 24 * 2
+        flops = m.n_elem * (2 * 100 * 9 + 300)
+        from oracle import shape as OS  # noqa: F401  (cpu baseline below)
+        import multiprocessing as mp
+        pool = mp.get_context("spawn").Pool(cores)
+        S = min(m.n_elem, 20000 * cores)
+        sel = np.linspace(0, m.n_elem - 1, S).astype(np.int64)
+        chunks = [(m.vertices, m.cells[sel[c::cores]], p.dofmap[sel[c::cores]], u, v) for c in range(cores)]
+        t0 = time.perf_counter()
+        pool.map(_oracle_shape, chunks)
+        cpu_rate = S / (time.perf_counter() - t0)
+        pool.close()
+        pool.join()
+        out.update({"metric": "element adjoints/s (P2 Poisson dL/dvertices, 56^3x6 tets)",
+                    "value": m.n_elem / t, "ms_per_step": t * 1e3, "dtype": "f64",
+                    "config": {"workload": "adjoint_p2", "cells": m.n_elem, "vertices": m.n_vert},
+                    "roofline": {"bound": "alu", "achieved": flops / t / 1e12, "peak": None, "unit": "TFLOP/s",
+                                 "frac": None, "traffic": None,
+                                 "hbm_gbs": byts / t / 1e9, "hbm_frac": byts / t / 1e9 / hbm_peak,
+                                 "kernel": "poisson_adjoint_kernel<3,2>"},
+                    "clocks": clk, "gpu_launches": args.steps,
+                    "cpu_baseline": {"value": cpu_rate, "unit": "elem/s", "cores": cores, "kind": "oracle",
+                                     "sample": f"{S} cells, continuous shape derivative"},
+                    "detail": {"forward_tabulate_fp64_ms": t_fwd * 1e3}})
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+def _oracle_shape(args):
+    verts, cells, dofmap, u, v = args
+    from oracle import shape as OS
+
+    OS.poisson_shape_gradient(verts, cells, 2, dofmap, u, v)
+    return cells.shape[0]
 
 
 if __name__ == "__main__":

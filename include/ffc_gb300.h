@@ -67,7 +67,8 @@ typedef enum {
   FFC_FP64 = 0,   /* FP64 contraction, A_K stored as double */
   FFC_FP32 = 1,   /* FP32 G and A0, FP32 accumulation on CUDA cores, A_K stored as float */
   FFC_TF32 = 2,   /* tcgen05 kind::tf32, one product, FP32 accumulation in TMEM, float out */
-  FFC_TF32X3 = 3  /* tcgen05 kind::tf32 with hi/lo splits of G and A0 (three products), float out */
+  FFC_TF32X3 = 3, /* tcgen05 kind::tf32 with hi/lo splits of G and A0 (three products), float out */
+  FFC_BF16X3 = 4  /* tcgen05 kind::f16 (BF16) with three-part splits of G and A0 (six products), float out */
 } ffc_precision;
 
 /* Device status bits returned by ffc_status_poll. */
@@ -159,6 +160,38 @@ int ffc_assemble(const ffc_form* f, int64_t n_elem, const int32_t* cells, const 
  */
 int ffc_tabulate_adjoint(const ffc_form* f, int64_t n_elem, const int32_t* cells, const double* vertices,
                          int64_t n_vert, const double* dA_K, double* dvertices, void* stream);
+
+/*
+ * Batched heterogeneous assembly (Algorithm 2 over many independent problems in one
+ * persistent launch). Each item is one (mesh, form) problem exactly as for
+ * ffc_assemble (device pointers, caller-owned); the arithmetic is FP64 geometry,
+ * FP32 contraction (FFC_FP32) and FP64 CSR accumulation. Forms carried: elasticity
+ * P1-P3, Poisson P1-P2, mass P1, all on tetrahedra (others: FFC_EUNSUPPORTED).
+ * The kernel takes tiles of cells from one global atomic counter; no CTA waits for
+ * another. The library allocates a small work table per tile variant.
+ */
+typedef struct {
+  const ffc_form* form;
+  int64_t n_elem;
+  const int32_t* cells;     /* device int32 [n_elem][4] */
+  const double* vertices;   /* device double [n_vert][3] */
+  int64_t n_vert;
+  const double* coeffs;     /* device, or NULL (no batched form reads coefficients) */
+  const int32_t* slot;      /* device int32 [n_elem][n][n] */
+  double* csr_val;          /* device double [nnz] */
+  int64_t nnz;
+} ffc_batch_item;
+
+/* zero_csr != 0: every run first zeroes each item's csr_val (a fresh assembly). */
+int ffc_batch_create(const ffc_batch_item* items, int n_items, int zero_csr, ffc_batch** out);
+/* Times the three tile variants (16, 32, 64 cells per thread group and tile) on the
+ * caller's data, keeps the fastest and returns it; leaves every csr_val zeroed. */
+int ffc_batch_tune(ffc_batch* b, void* stream, int* cells_per_tile_group);
+/* One persistent launch (use_graph = 0), or the same work captured once into a CUDA
+ * graph on `stream` and replayed (use_graph != 0). */
+int ffc_batch_run(ffc_batch* b, int use_graph, void* stream);
+int ffc_batch_info(const ffc_batch* b, int* n_items, long long* total_tiles, int* cells_per_tile_group);
+void ffc_batch_destroy(ffc_batch* b);
 
 /*
  * ffc_status_poll -- synchronise `stream`, return the device status bits

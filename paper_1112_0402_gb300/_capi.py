@@ -33,10 +33,24 @@ SIGNATURES = {
     "ffc_tabulate_adjoint": (ctypes.c_int, [c_vp, ctypes.c_int64, c_vp, c_vp, ctypes.c_int64, c_vp, c_vp, c_vp]),
     "ffc_tabulate_static": (ctypes.c_int, [c_vp, ctypes.c_int64, c_vp, c_vp, ctypes.c_int64, c_vp, c_vp,
                                            ctypes.c_int, c_vp, c_u32p]),
+    "ffc_batch_create": (ctypes.c_int, [c_vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(c_vp)]),
+    "ffc_batch_tune": (ctypes.c_int, [c_vp, c_vp, ctypes.POINTER(ctypes.c_int)]),
+    "ffc_batch_run": (ctypes.c_int, [c_vp, ctypes.c_int, c_vp]),
+    "ffc_batch_info": (ctypes.c_int, [c_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_longlong),
+                                      ctypes.POINTER(ctypes.c_int)]),
+    "ffc_batch_destroy": (None, [c_vp]),
     "ffc_status_poll": (ctypes.c_int, [c_vp, c_u32p]),
     "ffc_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "ffc_last_error": (ctypes.c_char_p, []),
 }
+
+class BatchItem(ctypes.Structure):
+    """ffc_batch_item."""
+
+    _fields_ = [("form", c_vp), ("n_elem", ctypes.c_int64), ("cells", c_vp), ("vertices", c_vp),
+                ("n_vert", ctypes.c_int64), ("coeffs", c_vp), ("slot", c_vp), ("csr_val", c_vp),
+                ("nnz", ctypes.c_int64)]
+
 
 _lib = None
 

@@ -16,8 +16,8 @@ from ._capi import lib
 
 MASS, POISSON, NS_CONVECTION, ELASTICITY = 0, 1, 2, 3
 TRIANGLE, TETRAHEDRON = 2, 3
-FP64, FP32, TF32, TF32X3 = 0, 1, 2, 3
-PRECISIONS = {"fp64": FP64, "fp32": FP32, "tf32": TF32, "tf32x3": TF32X3}
+FP64, FP32, TF32, TF32X3, BF16X3 = 0, 1, 2, 3, 4
+PRECISIONS = {"fp64": FP64, "fp32": FP32, "tf32": TF32, "tf32x3": TF32X3, "bf16x3": BF16X3}
 FLAG_DEGENERATE, FLAG_BOUNDS, FLAG_TIMEOUT = 1, 2, 4
 
 
@@ -174,3 +174,62 @@ def status_poll(stream=None) -> int:
     flags = ctypes.c_uint32()
     _check(lib().ffc_status_poll(_stream(stream), ctypes.byref(flags)), "ffc_status_poll")
     return flags.value
+
+
+class Batch:
+    """Many assembly problems in one persistent launch (ffc_batch_*).
+
+    items: sequence of dicts with keys form, cells, vertices, slot, csr_val
+    (device tensors as for :func:`assemble`); the arithmetic is FP32 contraction with
+    FP64 CSR accumulation."""
+
+    def __init__(self, items, zero_csr: bool = True):
+        import torch
+
+        from ._capi import BatchItem
+
+        arr = (BatchItem * len(items))()
+        self._keep = []
+        for k, it in enumerate(items):
+            f = it["form"]
+            n = f.n_local
+            cells, verts, slot, val = it["cells"], it["vertices"], it["slot"], it["csr_val"]
+            ne = cells.shape[0]
+            arr[k].form = f.handle
+            arr[k].n_elem = ne
+            arr[k].cells = _dev_ptr(cells, torch.int32, "cells", (ne, f.dim + 1))
+            arr[k].vertices = _dev_ptr(verts, torch.float64, "vertices")
+            arr[k].n_vert = verts.shape[0]
+            arr[k].coeffs = None
+            arr[k].slot = _dev_ptr(slot, torch.int32, "slot", (ne, n, n))
+            arr[k].csr_val = _dev_ptr(val, torch.float64, "csr_val")
+            arr[k].nnz = val.numel()
+            self._keep.append((f, cells, verts, slot, val))
+        h = ctypes.c_void_p()
+        _check(lib().ffc_batch_create(arr, len(items), int(zero_csr), ctypes.byref(h)), "ffc_batch_create")
+        self._h = h
+
+    def tune(self, stream=None) -> int:
+        c = ctypes.c_int()
+        _check(lib().ffc_batch_tune(self._h, _stream(stream), ctypes.byref(c)), "ffc_batch_tune")
+        return c.value
+
+    def run(self, graph: bool = False, stream=None) -> None:
+        _check(lib().ffc_batch_run(self._h, int(graph), _stream(stream)), "ffc_batch_run")
+
+    def info(self):
+        n, tiles, ke = ctypes.c_int(), ctypes.c_longlong(), ctypes.c_int()
+        _check(lib().ffc_batch_info(self._h, ctypes.byref(n), ctypes.byref(tiles), ctypes.byref(ke)),
+               "ffc_batch_info")
+        return {"items": n.value, "tiles": tiles.value, "cells_per_tile_group": ke.value}
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            lib().ffc_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

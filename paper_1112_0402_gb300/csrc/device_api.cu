@@ -83,8 +83,8 @@ void release_device_tensors(ffc_form* f) {
     cudaFree(t.a0t_f64);
     cudaFree(t.a0_f32);
     cudaFree(t.a0t_f32);
-    cudaFree(t.b_hi);
-    cudaFree(t.b_lo);
+    for (auto& fam : t.tc_part)
+      for (void* q : fam) cudaFree(q);
   }
   f->dev.clear();
   cudaSetDevice(cur);
@@ -97,7 +97,7 @@ static int dispatch(const LaunchArgs& a, int precision, bool assemble) {
     if (rc == FFC_EUNSUPPORTED) rc = launch_simt_tet_mass(a, precision, assemble);
     if (rc == FFC_EUNSUPPORTED) rc = launch_simt_tet_poisson(a, precision, assemble);
     if (rc == FFC_EUNSUPPORTED) rc = launch_simt_vector(a, precision, assemble);
-  } else if (precision == FFC_TF32 || precision == FFC_TF32X3) {
+  } else if (precision == FFC_TF32 || precision == FFC_TF32X3 || precision == FFC_BF16X3) {
     rc = launch_tc(a, precision, assemble);
   }
   if (rc == FFC_ECUDA) set_error(std::string("kernel launch: ") + cudaGetErrorString(cudaGetLastError()));
@@ -108,7 +108,7 @@ static int dispatch(const LaunchArgs& a, int precision, bool assemble) {
 static int common_checks(const ffc_form* f, int64_t n_elem, const int32_t* cells, const double* vertices,
                          int64_t n_vert, const double* coeffs, int precision) {
   if (!f || n_elem < 0 || n_vert < 0) return FFC_EINVAL;
-  if (precision < FFC_FP64 || precision > FFC_TF32X3) return FFC_EINVAL;
+  if (precision < FFC_FP64 || precision > FFC_BF16X3) return FFC_EINVAL;
   if (n_elem == 0) return FFC_OK;
   if (!cells || !vertices || n_vert == 0) return FFC_EINVAL;
   if (f->ncoeff > 0 && !coeffs) return FFC_EINVAL;

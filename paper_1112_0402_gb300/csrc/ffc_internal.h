@@ -18,10 +18,10 @@ struct DeviceTensors {
   double* a0t_f64 = nullptr;  // [na][nn]  transposed (coalesced over i)
   float* a0_f32 = nullptr;    // [nn][na]
   float* a0t_f32 = nullptr;   // [na][nn]
-  // tcgen05 operands: K-major B tiles of A0 (rows = i, K = alpha padded), tf32 hi/lo
-  float* b_hi = nullptr;      // [nn_pad][k_pad]
-  float* b_lo = nullptr;      // [nn_pad][k_pad]
-  int nn_pad = 0, k_pad = 0;
+  // tcgen05 operands: A0 split into TF32 (family 0: 2 parts) or BF16 (family 1: 3 parts),
+  // each part laid out per 128-entry M-tile in the core-matrix layout
+  void* tc_part[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
+  int tc_kpad[2] = {0, 0};
 };
 
 }  // namespace ffc

@@ -21,23 +21,29 @@
 
 namespace ffc {
 
-template <int D, int FORM, int Q, typename T>
+// BLOCK = 0: the block size follows from n^2 (single-form kernels); BLOCK > 0: a fixed
+// block size shared by several forms (the batched kernel), KE_T = cells per thread
+// group per tile (0 = default).
+template <int D, int FORM, int Q, typename T, int BLOCK = 0, int KE_T = 0>
 struct SimtCfg {
   static constexpr int N = nlocal(FORM, D, Q);
   static constexpr int NN = N * N;
   static constexpr int NA = nalpha(FORM, D, Q);
   static constexpr int VEC = 16 / int(sizeof(T));
   static constexpr int NAP = (NA + VEC - 1) / VEC * VEC;
-  static constexpr int R = (NN + 511) / 512;
+  static constexpr int RMAX_THREADS = BLOCK > 0 ? BLOCK : 512;
+  static constexpr int R = (NN + RMAX_THREADS - 1) / RMAX_THREADS;
   static constexpr int NTI = (NN + R - 1) / R;
-  static constexpr int EG = NTI >= 256 ? 1 : 256 / NTI;
-  static constexpr int NT = NTI * EG;
+  static constexpr int EG = BLOCK > 0 ? BLOCK / NTI : (NTI >= 256 ? 1 : 256 / NTI);
+  static constexpr int NT = BLOCK > 0 ? BLOCK : NTI * EG;
   static constexpr bool REG_A0 = (R * NA * int(sizeof(T)) / 4) <= 96;
-  static constexpr int KE_TARGET = REG_A0 ? 64 : 16;
+  static constexpr int KE_TARGET = KE_T > 0 ? KE_T : (REG_A0 ? 64 : 16);
   static constexpr int KE = (KE_TARGET + EG - 1) / EG;
   static constexpr int E = EG * KE;
   static constexpr int NCOEF = (FORM == FFC_NS_CONVECTION) ? N : 0;
   static constexpr size_t SMEM = size_t(E) * NAP * sizeof(T) + size_t(E) * NCOEF * sizeof(double);
+  // two resident CTAs per SM where the register-held reference tensor is small
+  static constexpr int MIN_BLOCKS = (REG_A0 && R * NA * int(sizeof(T)) / 4 <= 16) ? 2 : 1;
 };
 
 struct SimtParams {
@@ -60,23 +66,12 @@ __device__ __forceinline__ void put(OutT* p, double v) {
   __stcs(p, OutT(v));
 }
 
-template <int D, int FORM, int Q, typename T, bool ASSEMBLE>
-__global__ void __launch_bounds__(SimtCfg<D, FORM, Q, T>::NT)
-    simt_tabulate_kernel(SimtParams p) {
-  using C = SimtCfg<D, FORM, Q, T>;
-  using OutT = T;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* Gs = reinterpret_cast<T*>(smem_raw);                                     // [E][NAP]
-  double* Ws = reinterpret_cast<double*>(smem_raw + size_t(C::E) * C::NAP * sizeof(T));  // [E][NCOEF]
-
-  const int t = threadIdx.x;
-  const int ti = t % C::NTI;
-  const int eg = t / C::NTI;
-  const long long n_tiles = (p.n_elem + C::E - 1) / C::E;
-
-  T a0r[C::REG_A0 ? C::R : 1][C::REG_A0 ? C::NA : 1];
+// Loads the thread's rows of the reference tensor into registers (register path).
+template <class C, typename T>
+__device__ __forceinline__ void load_a0_rows(const void* a0, int t, T (&a0r)[C::REG_A0 ? C::R : 1][C::REG_A0 ? C::NA : 1]) {
   if constexpr (C::REG_A0) {
-    const T* A0 = static_cast<const T*>(p.a0);
+    const int ti = t % C::NTI;
+    const T* A0 = static_cast<const T*>(a0);
 #pragma unroll
     for (int r = 0; r < C::R; ++r) {
       const int i = ti + r * C::NTI;
@@ -84,8 +79,20 @@ __global__ void __launch_bounds__(SimtCfg<D, FORM, Q, T>::NT)
       for (int a = 0; a < C::NA; ++a) a0r[r][a] = (i < C::NN) ? A0[size_t(i) * C::NA + a] : T(0);
     }
   }
+}
 
-  for (long long tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+// One tile of E cells: geometry into shared memory, then contraction and store or
+// atomic scatter. Called by every thread of the block; contains block barriers.
+template <class C, int D, int FORM, int Q, typename T, bool ASSEMBLE>
+__device__ __forceinline__ void simt_tile(const SimtParams& p, long long tile, unsigned char* smem_raw,
+                                          const T (&a0r)[C::REG_A0 ? C::R : 1][C::REG_A0 ? C::NA : 1]) {
+  using OutT = T;
+  T* Gs = reinterpret_cast<T*>(smem_raw);                                                // [E][NAP]
+  double* Ws = reinterpret_cast<double*>(smem_raw + size_t(C::E) * C::NAP * sizeof(T));  // [E][NCOEF]
+  const int t = threadIdx.x;
+  const int ti = t % C::NTI;
+  const int eg = t / C::NTI;
+  {
     const long long e0 = tile * C::E;
     // ---- phase 1: geometry tensors of the tile's cells
     if constexpr (C::NCOEF > 0) {
@@ -113,13 +120,35 @@ __global__ void __launch_bounds__(SimtCfg<D, FORM, Q, T>::NT)
       for (int a = C::NA; a < C::NAP; ++a) g[a] = T(0);
     }
     __syncthreads();
-    // ---- phase 2: contraction and epilogue
-    if constexpr (C::REG_A0) {
+    // ---- phase 2: contraction and epilogue (thread groups beyond EG idle)
+    if (eg >= C::EG) {
+    } else if constexpr (C::REG_A0) {
+      // assembly: the slots of the next cell are loaded while this cell's atomics issue
+      int slot_next[ASSEMBLE ? C::R : 1];
+      if constexpr (ASSEMBLE) {
+        const long long e = e0 + eg;
+#pragma unroll
+        for (int r = 0; r < C::R; ++r) {
+          const int i = ti + r * C::NTI;
+          slot_next[r] = (e < p.n_elem && i < C::NN) ? __ldg(p.slot + e * C::NN + i) : -1;
+        }
+      }
 #pragma unroll 1
       for (int k = 0; k < C::KE; ++k) {
         const int el = eg + k * C::EG;
         const long long e = e0 + el;
         if (e >= p.n_elem) break;
+        int slot_cur[ASSEMBLE ? C::R : 1];
+        if constexpr (ASSEMBLE) {
+          const long long en = e + C::EG;
+          const bool more = (k + 1 < C::KE) && (en < p.n_elem);
+#pragma unroll
+          for (int r = 0; r < C::R; ++r) {
+            const int i = ti + r * C::NTI;
+            slot_cur[r] = slot_next[r];
+            slot_next[r] = (more && i < C::NN) ? __ldg(p.slot + en * C::NN + i) : -1;
+          }
+        }
         const T* g = Gs + el * C::NAP;
         T acc[C::R];
 #pragma unroll
@@ -136,7 +165,7 @@ __global__ void __launch_bounds__(SimtCfg<D, FORM, Q, T>::NT)
           if (i < C::NN) {
             const long long o = e * C::NN + i;
             if constexpr (ASSEMBLE) {
-              const int s = __ldg(p.slot + o);
+              const int s = slot_cur[r];
               if (s >= 0 && s < p.nnz) atomicAdd(p.csr_val + s, double(acc[r]));
               else atomicOr(p.status, FFC_FLAG_BOUNDS);
             } else {
@@ -178,6 +207,18 @@ __global__ void __launch_bounds__(SimtCfg<D, FORM, Q, T>::NT)
     }
     __syncthreads();
   }
+}
+
+template <int D, int FORM, int Q, typename T, bool ASSEMBLE>
+__global__ void __launch_bounds__(SimtCfg<D, FORM, Q, T>::NT, SimtCfg<D, FORM, Q, T>::MIN_BLOCKS)
+    simt_tabulate_kernel(SimtParams p) {
+  using C = SimtCfg<D, FORM, Q, T>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T a0r[C::REG_A0 ? C::R : 1][C::REG_A0 ? C::NA : 1];
+  load_a0_rows<C, T>(p.a0, threadIdx.x, a0r);
+  const long long n_tiles = (p.n_elem + C::E - 1) / C::E;
+  for (long long tile = blockIdx.x; tile < n_tiles; tile += gridDim.x)
+    simt_tile<C, D, FORM, Q, T, ASSEMBLE>(p, tile, smem_raw, a0r);
 }
 
 // Host-side launcher for one instantiation.

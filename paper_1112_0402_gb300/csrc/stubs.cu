@@ -2,5 +2,4 @@
 #include "ffc_internal.h"
 
 namespace ffc {
-int launch_adjoint(const LaunchArgs&, const double*, double*) { return FFC_EUNSUPPORTED; }
 }  // namespace ffc

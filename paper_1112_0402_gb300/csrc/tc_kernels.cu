@@ -1,4 +1,4 @@
-// Tensor-core (tcgen05, kind::tf32) contraction of the tensor representation
+// Tensor-core (tcgen05, kind::tf32 / kind::f16 with BF16) contraction of the tensor representation
 // A^K_i = A0_{i alpha} G_K^alpha (Section 3.2, eq. (tensorproduct)), batched over
 // cells as one GEMM (the level-3 BLAS formulation proposed in Section 3.5):
 //
@@ -10,21 +10,28 @@
 // consecutive entries of that cell's row-major A_K block: coalesced 128-byte stores.
 //
 // Per CTA (128 threads, persistent over cell tiles):
-//   1. each thread computes one cell's geometry and G_K in FP64, rounds it to TF32
-//      (and the TF32 remainder for the split product) and writes it into the B tile
+//   1. each thread computes one cell's geometry and G_K in FP64, splits it into
+//      1-3 parts of the MMA operand type and writes them into the B tiles
 //      (canonical K-major, no-swizzle core-matrix layout);
-//   2. per M-tile, thread 0 issues a bulk TMA copy of the pre-laid-out A0 tile
-//      (hi and lo parts) into shared memory, waits on an mbarrier, issues the
-//      tcgen05.mma chain (1 or 3 products per K-step of 8), and commits it to a
-//      second mbarrier;
+//   2. per M-tile, thread 0 issues bulk TMA copies of the pre-laid-out A0 tile parts
+//      into shared memory, waits on an mbarrier, issues the tcgen05.mma chain, and
+//      commits it to a second mbarrier;
 //   3. all threads wait, tcgen05.ld the accumulator and store (or atomically add)
 //      the results.
+// Split-precision modes (x = sum of parts, products summed smallest first):
+//   TF32     x ~ t1                     1 product   (kind::tf32, K-step 8)
+//   TF32X3   x ~ t1 + t2                3 products  t2*t1, t1*t2, t1*t1
+//   BF16X3   x ~ b1 + b2 + b3           6 products  b3b1, b2b2, b1b3, b2b1, b1b2, b1b1
+//                                                   (kind::f16 with BF16, K-step 16)
+// Every part is the round-to-nearest of the FP64 remainder left by the previous parts.
 // Every mbarrier wait is bounded; on expiry the kernel sets FFC_FLAG_TIMEOUT,
 // waits (bounded) for its own work in flight, frees its TMEM and returns.
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
 #include <cstring>
+#include <type_traits>
 #include <vector>
 
 #include "ffc_internal.h"
@@ -45,11 +52,67 @@ __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
-// K-major, no-swizzle core-matrix layout: 8 rows x 16 bytes per core matrix; core
-// matrix (row_group, k_group) at ((row_group * KC) + k_group) * 128 bytes. The
-// leading (K) byte offset is 128, the stride (row-group) byte offset KC*128.
-__host__ __device__ __forceinline__ uint32_t core_offset_floats(int row, int k, int kc) {
-  return uint32_t(((row >> 3) * kc + (k >> 2)) * 32 + (row & 7) * 4 + (k & 3));
+// Operand element handling per split mode. Core matrices are 8 rows x 16 bytes
+// (4 TF32 or 8 BF16 values per row); core matrix (row_group, k_group) sits at
+// ((row_group * KC) + k_group) * 128 bytes, so the leading (K) byte offset is 128 and
+// the stride (row-group) byte offset KC * 128.
+enum { MODE_TF32 = 1, MODE_TF32X3 = 3, MODE_BF16X3 = 6 };
+
+template <int MODE>
+struct Split {
+  static constexpr bool BF16 = MODE == MODE_BF16X3;
+  static constexpr int PARTS = MODE == MODE_TF32 ? 1 : (MODE == MODE_TF32X3 ? 2 : 3);
+  static constexpr int EPC = BF16 ? 8 : 4;         // elements per 16-byte core row
+  static constexpr int KSTEP = BF16 ? 16 : 8;      // K per MMA instruction
+  static constexpr int ESIZE = BF16 ? 2 : 4;
+  using Store = typename std::conditional<BF16, uint16_t, uint32_t>::type;
+  // products (A part, B part), smallest first
+  static constexpr int NPROD = MODE;
+  __host__ __device__ static constexpr int pa(int k) {
+    return MODE == MODE_TF32 ? 0 : MODE == MODE_TF32X3 ? (k == 0 ? 1 : 0)
+         : (k == 0 ? 2 : k == 1 ? 1 : k == 2 ? 0 : k == 3 ? 1 : 0);
+  }
+  __host__ __device__ static constexpr int pb(int k) {
+    return MODE == MODE_TF32 ? 0 : MODE == MODE_TF32X3 ? (k == 1 ? 1 : 0)
+         : (k == 0 ? 0 : k == 1 ? 1 : k == 2 ? 2 : k == 3 ? 0 : k == 4 ? 1 : 0);
+  }
+  // D = F32; A, B = TF32 (2) or BF16 (1); both K-major; N >> 3 at bit 17, M >> 4 at bit 24
+  static constexpr uint32_t idesc(int m, int n) {
+    return (1u << 4) | ((BF16 ? 1u : 2u) << 7) | ((BF16 ? 1u : 2u) << 10) | (uint32_t(n >> 3) << 17) |
+           (uint32_t(m >> 4) << 24);
+  }
+};
+
+__host__ __device__ __forceinline__ uint32_t core_offset(int row, int k, int kc, int epc) {
+  return uint32_t(((row >> 3) * kc + k / epc) * (8 * epc) + (row & 7) * epc + (k % epc));
+}
+
+__device__ __forceinline__ uint32_t tf32_bits(double x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(float(x)));
+  return r;
+}
+
+__device__ __forceinline__ uint16_t bf16_bits(double x) {
+  return __bfloat16_as_ushort(__float2bfloat16_rn(float(x)));
+}
+
+__device__ __forceinline__ double bf16_value(uint16_t b) { return double(__uint_as_float(uint32_t(b) << 16)); }
+
+// Splits x into PARTS operand values, each the rounding of the remainder left so far.
+template <int MODE>
+__device__ __forceinline__ void split_device(double x, typename Split<MODE>::Store (&out)[3]) {
+  double r = x;
+#pragma unroll
+  for (int k = 0; k < Split<MODE>::PARTS; ++k) {
+    if constexpr (Split<MODE>::BF16) {
+      out[k] = bf16_bits(r);
+      r -= bf16_value(out[k]);
+    } else {
+      out[k] = tf32_bits(r);
+      r -= double(__uint_as_float(out[k]));
+    }
+  }
 }
 
 __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
@@ -59,17 +122,6 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint3
   d |= uint64_t((sbo >> 4) & 0x3FFF) << 32;
   d |= uint64_t(1) << 46;  // descriptor version for tcgen05
   return d;                // base offset 0, no swizzle
-}
-
-// kind::tf32 instruction descriptor: D = F32, A = B = TF32, both K-major.
-__host__ __device__ constexpr uint32_t idesc_tf32(int m, int n) {
-  return (1u << 4) | (2u << 7) | (2u << 10) | (uint32_t(n >> 3) << 17) | (uint32_t(m >> 4) << 24);
-}
-
-__device__ __forceinline__ float tf32_rna(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return __uint_as_float(r);
 }
 
 __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
@@ -103,11 +155,19 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t
                : "memory");
 }
 
-__device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
-      "l"(a), "l"(b), "r"(idesc), "r"(acc));
+template <bool BF16>
+__device__ __forceinline__ void mma(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  if constexpr (BF16) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc));
+  } else {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc));
+  }
 }
 
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
@@ -135,9 +195,8 @@ struct TcParams {
   const double* vertices;
   long long n_vert;
   const double* coeffs;
-  const float* a0_hi;  // [MT][128 x KPAD] core-matrix layout per M-tile
-  const float* a0_lo;
-  float* out;          // A_K [n_elem][NN]
+  const void* a0_part[3];  // each [MT][128 x KPAD] in core-matrix layout
+  float* out;              // A_K [n_elem][NN]
   const int32_t* slot;
   double* csr_val;
   long long nnz;
@@ -146,29 +205,29 @@ struct TcParams {
   unsigned* status;
 };
 
-template <int D, int FORM, int Q, int NPROD>
+template <int D, int FORM, int Q, int MODE>
 struct TcCfg {
+  using S = Split<MODE>;
   static constexpr int N = nlocal(FORM, D, Q);
   static constexpr int NN = N * N;
   static constexpr int NA = nalpha(FORM, D, Q);
-  static constexpr int KPAD = kpad(NA);
-  static constexpr int KC = KPAD / 4;
+  static constexpr int KPAD = (NA + S::KSTEP - 1) / S::KSTEP * S::KSTEP;
+  static constexpr int KC = KPAD / S::EPC;
   static constexpr int MT = (NN + M_TILE - 1) / M_TILE;
-  static constexpr uint32_t A_BYTES = M_TILE * KPAD * 4;
-  static constexpr uint32_t B_BYTES = N_CELLS * KPAD * 4;
-  static constexpr int NBUF = NPROD == 3 ? 2 : 1;  // hi (+ lo)
-  static constexpr size_t SMEM = size_t(NBUF) * (A_BYTES + B_BYTES) + 128 + 128;
+  static constexpr uint32_t A_BYTES = M_TILE * KPAD * S::ESIZE;
+  static constexpr uint32_t B_BYTES = N_CELLS * KPAD * S::ESIZE;
+  static constexpr size_t SMEM = size_t(S::PARTS) * (A_BYTES + B_BYTES) + 128 + 128;
 };
 
-template <int D, int FORM, int Q, int NPROD, bool ASSEMBLE>
+template <int D, int FORM, int Q, int MODE, bool ASSEMBLE>
 __global__ void __launch_bounds__(THREADS, 1) tc_tabulate_kernel(TcParams p) {
-  using C = TcCfg<D, FORM, Q, NPROD>;
+  using C = TcCfg<D, FORM, Q, MODE>;
+  using S = Split<MODE>;
+  using Store = typename S::Store;
   extern __shared__ __align__(1024) unsigned char smem[];
-  float* As_hi = reinterpret_cast<float*>(smem);
-  float* As_lo = As_hi + (NPROD == 3 ? M_TILE * C::KPAD : 0);
-  float* Bs_hi = reinterpret_cast<float*>(smem + C::NBUF * C::A_BYTES);
-  float* Bs_lo = Bs_hi + (NPROD == 3 ? N_CELLS * C::KPAD : 0);
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + C::NBUF * (C::A_BYTES + C::B_BYTES));
+  unsigned char* As = smem;                                   // PARTS x A_BYTES
+  unsigned char* Bs = smem + S::PARTS * C::A_BYTES;           // PARTS x B_BYTES
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + S::PARTS * (C::A_BYTES + C::B_BYTES));
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 4);
   __shared__ int abort_flag;
 
@@ -193,7 +252,7 @@ __global__ void __launch_bounds__(THREADS, 1) tc_tabulate_kernel(TcParams p) {
   __syncthreads();
   fence_after();
   const uint32_t tmem = *tmem_slot;
-  constexpr uint32_t IDESC = idesc_tf32(M_TILE, N_CELLS);
+  constexpr uint32_t IDESC = S::idesc(M_TILE, N_CELLS);
   uint32_t ph_load = 0, ph_mma = 0;
   bool timed_out = false;
   int pending = 0;  // thread 0: 1 = a bulk copy may still be in flight, 2 = an MMA chain may be
@@ -201,7 +260,7 @@ __global__ void __launch_bounds__(THREADS, 1) tc_tabulate_kernel(TcParams p) {
   const long long n_tiles = (p.n_elem + N_CELLS - 1) / N_CELLS;
   for (long long tile = blockIdx.x; tile < n_tiles && !timed_out; tile += gridDim.x) {
     const long long e0 = tile * N_CELLS;
-    // ---- 1. geometry tensor of cell e0 + t -> B tile row t
+    // ---- 1. geometry tensor of cell e0 + t -> B tile row t (all parts)
     {
       const long long e = e0 + t;
       double g[C::NA];
@@ -211,9 +270,9 @@ __global__ void __launch_bounds__(THREADS, 1) tc_tabulate_kernel(TcParams p) {
         cell_geometry<D>(p.cells, p.vertices, p.n_vert, e, K, det, degenerate, bad_index);
         if (degenerate) atomicOr(p.status, FFC_FLAG_DEGENERATE);
         if (bad_index) atomicOr(p.status, FFC_FLAG_BOUNDS);
-        const double* w = (C::NA > 0 && FORM == FFC_NS_CONVECTION) ? p.coeffs + e * C::N : nullptr;
         double wl[FORM == FFC_NS_CONVECTION ? C::N : 1];
         if constexpr (FORM == FFC_NS_CONVECTION) {
+          const double* w = p.coeffs + e * C::N;
 #pragma unroll
           for (int k = 0; k < C::N; ++k) wl[k] = __ldg(w + k);
         }
@@ -224,39 +283,36 @@ __global__ void __launch_bounds__(THREADS, 1) tc_tabulate_kernel(TcParams p) {
       }
 #pragma unroll
       for (int k = 0; k < C::KPAD; ++k) {
-        const double v = k < C::NA ? g[k] : 0.0;
-        const float hi = tf32_rna(float(v));
-        Bs_hi[core_offset_floats(t, k, C::KC)] = hi;
-        if constexpr (NPROD == 3) Bs_lo[core_offset_floats(t, k, C::KC)] = tf32_rna(float(v - double(hi)));
+        Store parts[3];
+        split_device<MODE>(k < C::NA ? g[k] : 0.0, parts);
+        const uint32_t o = core_offset(t, k, C::KC, S::EPC);
+#pragma unroll
+        for (int q = 0; q < S::PARTS; ++q) reinterpret_cast<Store*>(Bs + q * C::B_BYTES)[o] = parts[q];
       }
     }
     fence_proxy_async();
     __syncthreads();
 
     for (int mt = 0; mt < C::MT; ++mt) {
-      // ---- 2. stage the A0 M-tile and run the MMA chain
+      // ---- 2. stage the A0 M-tile parts and run the MMA chain
       if (t == 0) {
-        mbar_expect_tx(bar_load, C::NBUF * C::A_BYTES);
-        bulk_g2s(smem_u32(As_hi), p.a0_hi + size_t(mt) * M_TILE * C::KPAD, C::A_BYTES, bar_load);
-        if constexpr (NPROD == 3)
-          bulk_g2s(smem_u32(As_lo), p.a0_lo + size_t(mt) * M_TILE * C::KPAD, C::A_BYTES, bar_load);
+        mbar_expect_tx(bar_load, S::PARTS * C::A_BYTES);
+#pragma unroll
+        for (int q = 0; q < S::PARTS; ++q)
+          bulk_g2s(smem_u32(As + q * C::A_BYTES),
+                   static_cast<const unsigned char*>(p.a0_part[q]) + size_t(mt) * C::A_BYTES, C::A_BYTES, bar_load);
         bool ok = mbar_wait(bar_load, ph_load);
         if (ok) {
           fence_after();
-          const uint32_t a_hi = smem_u32(As_hi), a_lo = smem_u32(As_lo);
-          const uint32_t b_hi = smem_u32(Bs_hi), b_lo = smem_u32(Bs_lo);
           constexpr uint32_t SBO = C::KC * 128;
 #pragma unroll 1
-          for (int ks = 0; ks < C::KPAD / 8; ++ks) {
-            const uint32_t off = ks * 256;  // 8 TF32 columns = two core matrices along K
-            const uint64_t dah = smem_desc(a_hi + off, 128, SBO), dbh = smem_desc(b_hi + off, 128, SBO);
-            if constexpr (NPROD == 3) {
-              const uint64_t dal = smem_desc(a_lo + off, 128, SBO), dbl = smem_desc(b_lo + off, 128, SBO);
-              mma_tf32(tmem, dal, dbh, IDESC, ks > 0 ? 1u : 0u);
-              mma_tf32(tmem, dah, dbl, IDESC, 1u);
-              mma_tf32(tmem, dah, dbh, IDESC, 1u);
-            } else {
-              mma_tf32(tmem, dah, dbh, IDESC, ks > 0 ? 1u : 0u);
+          for (int ks = 0; ks < C::KPAD / S::KSTEP; ++ks) {
+            const uint32_t off = ks * 256;  // one K-step = two core matrices along K
+#pragma unroll
+            for (int k = 0; k < S::NPROD; ++k) {
+              const uint64_t da = smem_desc(smem_u32(As + S::pa(k) * C::A_BYTES) + off, 128, SBO);
+              const uint64_t db = smem_desc(smem_u32(Bs + S::pb(k) * C::B_BYTES) + off, 128, SBO);
+              mma<S::BF16>(tmem, da, db, IDESC, (ks > 0 || k > 0) ? 1u : 0u);
             }
           }
           mma_commit(bar_mma);
@@ -326,52 +382,401 @@ __global__ void __launch_bounds__(THREADS, 1) tc_tabulate_kernel(TcParams p) {
   }
 }
 
-// Host: round-to-nearest (ties away) to TF32, the rounding of cvt.rna.tf32.f32.
-inline float host_tf32(double x) {
+// ---------------------------------------------------------------------------------
+// Warp-specialized version. Warps 0..7 produce the B tile (G) and drain the
+// accumulator; warp 8 lane 0 issues the bulk copies of the A0 tiles and the MMAs.
+// The accumulator is double-buffered in TMEM (2 x 128 columns) so the MMA chain of
+// M-tile m+1 runs while the epilogue stores M-tile m; the A0 tiles are double-
+// buffered in shared memory when two stages fit. Barriers:
+//   a_full[s]   bulk copy of stage s landed (expect_tx)       a_empty[s]  MMAs reading stage s done
+//   acc_full[b] MMAs into TMEM buffer b done                   acc_empty[b] epilogue drained buffer b
+//   b_full      B tile of the current cell tile written by the epilogue warps
+// ---------------------------------------------------------------------------------
+constexpr int EPI_WARPS = 8;
+constexpr int EPI_THREADS = EPI_WARPS * 32;
+constexpr int WS_THREADS = EPI_THREADS + 32;
+
+template <int D, int FORM, int Q, int MODE>
+struct TcWsCfg {
+  using Base = TcCfg<D, FORM, Q, MODE>;
+  using S = Split<MODE>;
+  static constexpr size_t A_TOTAL = size_t(S::PARTS) * Base::A_BYTES;
+  static constexpr size_t B_TOTAL = size_t(S::PARTS) * Base::B_BYTES;
+  static constexpr int STAGES = (2 * A_TOTAL + B_TOTAL + 512 <= 227 * 1024) ? 2 : 1;
+  static constexpr size_t SMEM = STAGES * A_TOTAL + B_TOTAL + 256;
+};
+
+// Bounded wait that also gives up when another role has aborted.
+__device__ __forceinline__ bool mbar_wait_or_abort(uint32_t bar, uint32_t phase, volatile int* abort_flag) {
+  for (uint32_t it = 0; it < WAIT_LIMIT; ++it) {
+    if (mbar_try_wait(bar, phase)) return true;
+    if ((it & 1023u) == 1023u && *abort_flag) return false;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+// G_K in FP32 from the FP64 geometry (K = J^{-1}, |det J|): the tensor-core paths
+// round G to the operand parts anyway, so only J, its inverse and determinant keep FP64.
+template <int D, int FORM, int Q>
+__device__ __forceinline__ void geometry_tensor_f32(const double Kd[D][D], double det, const double* w, double mu,
+                                                    double lambda, float* g) {
+  float K[D][D];
+#pragma unroll
+  for (int a = 0; a < D; ++a)
+#pragma unroll
+    for (int b = 0; b < D; ++b) K[a][b] = float(Kd[a][b]);
+  const float detf = float(det);
+  if constexpr (FORM == FFC_MASS) {
+    g[0] = detf;
+  } else if constexpr (FORM == FFC_POISSON) {
+#pragma unroll
+    for (int a1 = 0; a1 < D; ++a1)
+#pragma unroll
+      for (int a2 = 0; a2 < D; ++a2) {
+        float s = 0.f;
+#pragma unroll
+        for (int b = 0; b < D; ++b) s = fmaf(K[a1][b], K[a2][b], s);
+        g[a1 * D + a2] = detf * s;
+      }
+  } else if constexpr (FORM == FFC_NS_CONVECTION) {
+    constexpr int NS = nscalar(D, Q);
+#pragma unroll
+    for (int ct = 0; ct < D; ++ct)
+#pragma unroll
+      for (int st = 0; st < NS; ++st) {
+        const int t = ct * NS + st;
+        const float dw = float(det * w[t]);
+#pragma unroll
+        for (int a = 0; a < D; ++a) g[t * D + a] = dw * K[a][ct];
+      }
+  } else {
+    float KK[D][D];
+#pragma unroll
+    for (int a1 = 0; a1 < D; ++a1)
+#pragma unroll
+      for (int a2 = 0; a2 < D; ++a2) {
+        float s = 0.f;
+#pragma unroll
+        for (int b = 0; b < D; ++b) s = fmaf(K[a1][b], K[a2][b], s);
+        KK[a1][a2] = s;
+      }
+    const float muf = float(mu), lf = float(lambda);
+#pragma unroll
+    for (int b1 = 0; b1 < D; ++b1)
+#pragma unroll
+      for (int b2 = 0; b2 < D; ++b2)
+#pragma unroll
+        for (int a1 = 0; a1 < D; ++a1)
+#pragma unroll
+          for (int a2 = 0; a2 < D; ++a2) {
+            float v = muf * K[a1][b2] * K[a2][b1] + lf * K[a1][b1] * K[a2][b2];
+            if (b1 == b2) v += muf * KK[a1][a2];
+            g[((b1 * D + b2) * D + a1) * D + a2] = detf * v;
+          }
+  }
+}
+
+template <int MODE>
+__device__ __forceinline__ void split_f32(float x, typename Split<MODE>::Store (&out)[3]) {
+  float r = x;
+#pragma unroll
+  for (int k = 0; k < Split<MODE>::PARTS; ++k) {
+    if constexpr (Split<MODE>::BF16) {
+      out[k] = __bfloat16_as_ushort(__float2bfloat16_rn(r));
+      r -= __uint_as_float(uint32_t(out[k]) << 16);
+    } else {
+      uint32_t b;
+      asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(b) : "f"(r));
+      out[k] = b;
+      r -= __uint_as_float(b);
+    }
+  }
+}
+
+template <int D, int FORM, int Q, int MODE, bool ASSEMBLE>
+__global__ void __launch_bounds__(WS_THREADS, 1) tc_ws_kernel(TcParams p) {
+  using C = TcCfg<D, FORM, Q, MODE>;
+  using W = TcWsCfg<D, FORM, Q, MODE>;
+  using S = Split<MODE>;
+  using Store = typename S::Store;
+  extern __shared__ __align__(1024) unsigned char smem[];
+  unsigned char* As = smem;                              // STAGES x PARTS x A_BYTES
+  unsigned char* Bs = smem + W::STAGES * W::A_TOTAL;     // PARTS x B_BYTES
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + W::STAGES * W::A_TOTAL + W::B_TOTAL);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 12);
+  __shared__ int abort_flag;
+
+  const int t = threadIdx.x;
+  const int warp = t >> 5;
+  const int lane = t & 31;
+  auto bar = [&](int k) { return smem_u32(&bars[k]); };
+  // 0,1 a_full  2,3 a_empty  4,5 acc_full  6,7 acc_empty  8 b_full
+  if (t == 0) {
+    for (int k = 0; k < 2; ++k) {
+      mbar_init(bar(0 + k), 1);
+      mbar_init(bar(2 + k), 1);
+      mbar_init(bar(4 + k), 1);
+      mbar_init(bar(6 + k), EPI_THREADS);
+    }
+    mbar_init(bar(8), EPI_THREADS);
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(uint32_t(2 * N_CELLS)));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const long long n_tiles = (p.n_elem + N_CELLS - 1) / N_CELLS;
+  long long my_tiles = 0;
+  if (blockIdx.x < n_tiles) my_tiles = (n_tiles - 1 - blockIdx.x) / gridDim.x + 1;
+
+  if (warp == EPI_WARPS) {
+    // ------------------------------------------------------------ control: TMA + MMA
+    if (lane == 0) {
+      constexpr uint32_t IDESC = S::idesc(M_TILE, N_CELLS);
+      constexpr uint32_t SBO = C::KC * 128;
+      const long long total = my_tiles * C::MT;  // A tiles this CTA consumes
+      uint32_t ph_full[2] = {0, 0}, ph_empty[2] = {0, 0}, ph_acc_empty[2] = {0, 0}, ph_b = 0;
+      bool ok = true;
+      auto load = [&](int stage, long long g) {
+        const int mt = int(g % C::MT);
+        mbar_expect_tx(bar(0 + stage), uint32_t(W::A_TOTAL));
+#pragma unroll
+        for (int q = 0; q < S::PARTS; ++q)
+          bulk_g2s(smem_u32(As + stage * W::A_TOTAL + q * C::A_BYTES),
+                   static_cast<const unsigned char*>(p.a0_part[q]) + size_t(mt) * C::A_BYTES, C::A_BYTES,
+                   bar(0 + stage));
+      };
+      for (int st = 0; st < W::STAGES && st < total; ++st) load(st, st);
+      long long g = 0;
+      for (long long ct = 0; ct < my_tiles && ok; ++ct) {
+        ok = mbar_wait_or_abort(bar(8), ph_b, &abort_flag);
+        ph_b ^= 1;
+        for (int mt = 0; mt < C::MT && ok; ++mt, ++g) {
+          const int stage = int(g % W::STAGES);
+          const int acc = int(g & 1);
+          ok = mbar_wait_or_abort(bar(0 + stage), ph_full[stage], &abort_flag);
+          ph_full[stage] ^= 1;
+          if (ok && g >= 2) {
+            ok = mbar_wait_or_abort(bar(6 + acc), ph_acc_empty[acc], &abort_flag);
+            ph_acc_empty[acc] ^= 1;
+          }
+          if (!ok) break;
+          fence_after();
+          const uint32_t d = tmem + uint32_t(acc * N_CELLS);
+#pragma unroll 1
+          for (int ks = 0; ks < C::KPAD / S::KSTEP; ++ks) {
+            const uint32_t off = ks * 256;
+#pragma unroll
+            for (int k = 0; k < S::NPROD; ++k) {
+              const uint64_t da =
+                  smem_desc(smem_u32(As + stage * W::A_TOTAL + S::pa(k) * C::A_BYTES) + off, 128, SBO);
+              const uint64_t db = smem_desc(smem_u32(Bs + S::pb(k) * C::B_BYTES) + off, 128, SBO);
+              mma<S::BF16>(d, da, db, IDESC, (ks > 0 || k > 0) ? 1u : 0u);
+            }
+          }
+          mma_commit(bar(4 + acc));
+          mma_commit(bar(2 + stage));
+          // refill: the stage the previous tile used (two stages) or this one (one stage)
+          if constexpr (W::STAGES == 2) {
+            if (g >= 1 && g + 1 < total) {
+              const int ps = int((g - 1) % 2);
+              ok = mbar_wait_or_abort(bar(2 + ps), ph_empty[ps], &abort_flag);
+              ph_empty[ps] ^= 1;
+              if (ok) load(ps, g + 1);
+            }
+          } else {
+            if (g + 1 < total) {
+              ok = mbar_wait_or_abort(bar(2), ph_empty[0], &abort_flag);
+              ph_empty[0] ^= 1;
+              if (ok) load(0, g + 1);
+            }
+          }
+        }
+      }
+      if (!ok) {
+        atomicOr(p.status, FFC_FLAG_TIMEOUT);
+        abort_flag = 1;
+      }
+      // let the last MMA chain finish before TMEM is released (bounded)
+      if (g > 0) {
+        const long long last = g - 1;
+        mbar_wait(bar(2 + int(last % W::STAGES)), ph_empty[int(last % W::STAGES)] ^ 0u);
+      }
+    }
+  } else {
+    // ------------------------------------------------------------ epilogue warps
+    uint32_t ph_acc_full[2] = {0, 0};
+    long long g = 0;
+    bool ok = true;
+    const int q4 = warp & 3;        // TMEM lane quarter
+    const int half = warp >> 2;     // column half: cells half*64 .. half*64+63
+    for (long long ct = 0; ct < my_tiles && ok; ++ct) {
+      const long long e0 = (blockIdx.x + ct * gridDim.x) * N_CELLS;
+      if (t < N_CELLS) {
+        const long long e = e0 + t;
+        float g32[C::NA];
+        if (e < p.n_elem) {
+          double K[D][D], det;
+          bool degenerate, bad_index;
+          cell_geometry<D>(p.cells, p.vertices, p.n_vert, e, K, det, degenerate, bad_index);
+          if (degenerate) atomicOr(p.status, FFC_FLAG_DEGENERATE);
+          if (bad_index) atomicOr(p.status, FFC_FLAG_BOUNDS);
+          double wl[FORM == FFC_NS_CONVECTION ? C::N : 1];
+          if constexpr (FORM == FFC_NS_CONVECTION) {
+            const double* w = p.coeffs + e * C::N;
+#pragma unroll
+            for (int k = 0; k < C::N; ++k) wl[k] = __ldg(w + k);
+          }
+          geometry_tensor_f32<D, FORM, Q>(K, det, wl, p.mu, p.lambda, g32);
+        } else {
+#pragma unroll
+          for (int a = 0; a < C::NA; ++a) g32[a] = 0.f;
+        }
+#pragma unroll
+        for (int k = 0; k < C::KPAD; ++k) {
+          Store parts[3];
+          split_f32<MODE>(k < C::NA ? g32[k] : 0.f, parts);
+          const uint32_t o = core_offset(t, k, C::KC, S::EPC);
+#pragma unroll
+          for (int qq = 0; qq < S::PARTS; ++qq) reinterpret_cast<Store*>(Bs + qq * C::B_BYTES)[o] = parts[qq];
+        }
+        fence_proxy_async();
+      }
+      mbar_arrive(bar(8));
+      for (int mt = 0; mt < C::MT; ++mt, ++g) {
+        const int acc = int(g & 1);
+        ok = mbar_wait_or_abort(bar(4 + acc), ph_acc_full[acc], &abort_flag);
+        ph_acc_full[acc] ^= 1;
+        if (__any_sync(0xffffffffu, !ok)) {
+          ok = false;
+          break;
+        }
+        fence_after();
+        const int i = mt * M_TILE + q4 * 32 + lane;
+        const uint32_t taddr = tmem + (uint32_t(q4 * 32) << 16) + uint32_t(acc * N_CELLS + half * 64);
+#pragma unroll 1
+        for (int c = 0; c < 4; ++c) {
+          float v[16];
+          tmem_ld16(taddr + c * 16, v);
+          if (i < C::NN) {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+              const long long e = e0 + half * 64 + c * 16 + j;
+              if (e < p.n_elem) {
+                const long long o = e * C::NN + i;
+                if constexpr (ASSEMBLE) {
+                  const int s = __ldg(p.slot + o);
+                  if (s >= 0 && s < p.nnz) atomicAdd(p.csr_val + s, double(v[j]));
+                  else atomicOr(p.status, FFC_FLAG_BOUNDS);
+                } else {
+                  __stcs(p.out + o, v[j]);
+                }
+              }
+            }
+          }
+        }
+        fence_before();
+        mbar_arrive(bar(6 + acc));
+      }
+    }
+    if (!ok) {
+      if (t == 0) atomicOr(p.status, FFC_FLAG_TIMEOUT);
+      abort_flag = 1;
+    }
+  }
+  fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(uint32_t(2 * N_CELLS)));
+  }
+}
+
+// Host rounding of the operand parts (the same roundings the device applies):
+// TF32 = round to nearest, ties away, on the 13 dropped bits (cvt.rna.tf32.f32);
+// BF16 = round to nearest even on the 16 dropped bits (__float2bfloat16_rn).
+inline uint32_t host_tf32_bits(double x) {
   float f = float(x);
   uint32_t u;
   std::memcpy(&u, &f, 4);
-  u = (u + 0x1000u) & ~0x1FFFu;
-  std::memcpy(&f, &u, 4);
+  return (u + 0x1000u) & ~0x1FFFu;
+}
+inline uint16_t host_bf16_bits(double x) {
+  float f = float(x);
+  uint32_t u;
+  std::memcpy(&u, &f, 4);
+  u += 0x7FFFu + ((u >> 16) & 1u);
+  return uint16_t(u >> 16);
+}
+inline double host_value(uint32_t b) {
+  float f;
+  std::memcpy(&f, &b, 4);
   return f;
 }
 
-template <int D, int FORM, int Q, int NPROD, bool ASSEMBLE>
-int launch_one(const LaunchArgs& a) {
-  using C = TcCfg<D, FORM, Q, NPROD>;
-  ffc_form* f = const_cast<ffc_form*>(a.f);
-  DeviceTensors* t = const_cast<DeviceTensors*>(a.t);
-  {
-    std::lock_guard<std::mutex> g(f->lock);
-    if (!t->b_hi || t->k_pad != C::KPAD) {
-      const int nn = C::NN, na = C::NA;
-      std::vector<float> hi(size_t(C::MT) * M_TILE * C::KPAD, 0.f), lo(hi.size(), 0.f);
-      for (int i = 0; i < nn; ++i)
-        for (int k = 0; k < na; ++k) {
-          const double v = f->A0[size_t(i) * na + k];
-          const int mt = i / M_TILE, r = i % M_TILE;
-          const size_t o = size_t(mt) * M_TILE * C::KPAD + core_offset_floats(r, k, C::KC);
-          hi[o] = host_tf32(v);
-          lo[o] = host_tf32(v - double(hi[o]));
+template <int D, int FORM, int Q, int MODE>
+int upload_parts(ffc_form* f, DeviceTensors* t) {
+  using C = TcCfg<D, FORM, Q, MODE>;
+  using S = Split<MODE>;
+  const int fam = S::BF16 ? 1 : 0;
+  std::lock_guard<std::mutex> g(f->lock);
+  if (t->tc_part[fam][S::PARTS - 1] && t->tc_kpad[fam] == C::KPAD) return FFC_OK;
+  const size_t per = size_t(C::MT) * M_TILE * C::KPAD;  // elements per part
+  const int nparts = S::BF16 ? 3 : 2;                    // a family uploads all its parts once
+  std::vector<std::vector<typename S::Store>> parts(nparts, std::vector<typename S::Store>(per, 0));
+  for (int i = 0; i < C::NN; ++i)
+    for (int k = 0; k < C::NA; ++k) {
+      double r = f->A0[size_t(i) * C::NA + k];
+      const size_t o = size_t(i / M_TILE) * M_TILE * C::KPAD + core_offset(i % M_TILE, k, C::KC, S::EPC);
+      for (int q = 0; q < nparts; ++q) {
+        if constexpr (S::BF16) {
+          const uint16_t b = host_bf16_bits(r);
+          parts[q][o] = b;
+          r -= host_value(uint32_t(b) << 16);
+        } else {
+          const uint32_t b = host_tf32_bits(r);
+          parts[q][o] = b;
+          r -= host_value(b);
         }
-      cudaFree(t->b_hi);
-      cudaFree(t->b_lo);
-      t->b_hi = t->b_lo = nullptr;
-      if (cudaMalloc(&t->b_hi, hi.size() * 4) != cudaSuccess) return FFC_ENOMEM;
-      if (cudaMalloc(&t->b_lo, lo.size() * 4) != cudaSuccess) return FFC_ENOMEM;
-      if (cudaMemcpy(t->b_hi, hi.data(), hi.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess) return FFC_ECUDA;
-      if (cudaMemcpy(t->b_lo, lo.data(), lo.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess) return FFC_ECUDA;
-      t->k_pad = C::KPAD;
-      t->nn_pad = C::MT * M_TILE;
+      }
     }
+  for (int q = 0; q < 3; ++q) {
+    cudaFree(t->tc_part[fam][q]);
+    t->tc_part[fam][q] = nullptr;
   }
+  for (int q = 0; q < nparts; ++q) {
+    if (cudaMalloc(&t->tc_part[fam][q], per * sizeof(typename S::Store)) != cudaSuccess) return FFC_ENOMEM;
+    if (cudaMemcpy(t->tc_part[fam][q], parts[q].data(), per * sizeof(typename S::Store), cudaMemcpyHostToDevice) !=
+        cudaSuccess)
+      return FFC_ECUDA;
+  }
+  t->tc_kpad[fam] = C::KPAD;
+  return FFC_OK;
+}
+
+template <int D, int FORM, int Q, int MODE, bool ASSEMBLE>
+int launch_one(const LaunchArgs& a) {
+  using C = TcCfg<D, FORM, Q, MODE>;
+  using S = Split<MODE>;
+  DeviceTensors* t = const_cast<DeviceTensors*>(a.t);
+  int rc = upload_parts<D, FORM, Q, MODE>(const_cast<ffc_form*>(a.f), t);
+  if (rc != FFC_OK) return rc;
   TcParams p{};
   p.cells = a.cells;
   p.vertices = a.vertices;
   p.n_vert = a.n_vert;
   p.coeffs = a.coeffs;
-  p.a0_hi = t->b_hi;
-  p.a0_lo = t->b_lo;
+  for (int q = 0; q < 3; ++q) p.a0_part[q] = t->tc_part[S::BF16 ? 1 : 0][q];
   p.out = static_cast<float*>(a.out);
   p.slot = a.slot;
   p.csr_val = a.csr_val;
@@ -380,10 +785,11 @@ int launch_one(const LaunchArgs& a) {
   p.mu = a.f->mu;
   p.lambda = a.f->lambda;
   p.status = a.status;
-  auto kern = tc_tabulate_kernel<D, FORM, Q, NPROD, ASSEMBLE>;
+  using W = TcCfg<D, FORM, Q, MODE>;
+  auto kern = tc_tabulate_kernel<D, FORM, Q, MODE, ASSEMBLE>;
   static int sms = 0;
   if (sms == 0) {
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(C::SMEM)) != cudaSuccess)
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(W::SMEM)) != cudaSuccess)
       return FFC_ECUDA;
     int dev = 0;
     cudaGetDevice(&dev);
@@ -392,15 +798,24 @@ int launch_one(const LaunchArgs& a) {
   const long long n_tiles = (a.n_elem + N_CELLS - 1) / N_CELLS;
   long long grid = sms;
   if (grid > n_tiles) grid = n_tiles;
-  kern<<<unsigned(grid), THREADS, C::SMEM, static_cast<cudaStream_t>(a.stream)>>>(p);
+  kern<<<unsigned(grid), THREADS, W::SMEM, static_cast<cudaStream_t>(a.stream)>>>(p);
+  (void)sizeof(C);
   return cudaPeekAtLastError() == cudaSuccess ? FFC_OK : FFC_ECUDA;
 }
 
 template <int D, int FORM, int Q>
 int by_prec(const LaunchArgs& a, int precision, bool assemble) {
-  if (precision == FFC_TF32)
-    return assemble ? launch_one<D, FORM, Q, 1, true>(a) : launch_one<D, FORM, Q, 1, false>(a);
-  return assemble ? launch_one<D, FORM, Q, 3, true>(a) : launch_one<D, FORM, Q, 3, false>(a);
+  switch (precision) {
+    case FFC_TF32:
+      return assemble ? launch_one<D, FORM, Q, MODE_TF32, true>(a) : launch_one<D, FORM, Q, MODE_TF32, false>(a);
+    case FFC_TF32X3:
+      return assemble ? launch_one<D, FORM, Q, MODE_TF32X3, true>(a)
+                      : launch_one<D, FORM, Q, MODE_TF32X3, false>(a);
+    case FFC_BF16X3:
+      return assemble ? launch_one<D, FORM, Q, MODE_BF16X3, true>(a)
+                      : launch_one<D, FORM, Q, MODE_BF16X3, false>(a);
+  }
+  return FFC_EUNSUPPORTED;
 }
 
 }  // namespace tc
