@@ -535,14 +535,15 @@ def run_other(args):
                    args.warmup)
         clk = clocks.stop()
         byts = m.n_elem * (16 + 240 + 3600) + m.n_vert * 24
-        rate, S = _oracle_rate(W.NS_CONVECTION, 2, M.gather_cell_vertices(m), p.coeffs, cores)
+        rate, S = (None, 0) if args.no_cpu_baseline else _oracle_rate(W.NS_CONVECTION, 2,
+                                                                       M.gather_cell_vertices(m), p.coeffs, cores)
         out.update({"metric": "element tensors/s (vector-P2 convection, 40^3x6 tets, tabulate)",
                     "value": m.n_elem / t, "ms_per_step": t * 1e3, "dtype": "bf16x3",
                     "config": {"workload": "ns_vp2", "cells": m.n_elem, "nnz": int(col.size),
                                "contraction": prec, "l2": "A_K output 1.38 GB per step > L2"},
                     "roofline": {"bound": "hbm", "achieved": byts / t / 1e9, "peak": hbm_peak, "unit": "GB/s",
                                  "frac": byts / t / 1e9 / hbm_peak, "traffic": None, "peak_kind": peak_kind,
-                                 "kernel": "tc_tabulate_kernel convection P2 bf16x3"},
+                                 "kernel": "tc_ws_kernel convection P2 bf16x3"},
                     "clocks": clk, "gpu_launches": args.steps,
                     "cpu_baseline": {"value": rate, "unit": "elem/s", "cores": cores, "kind": "oracle",
                                      "sample": f"{S} cells"}, "detail": detail})
@@ -602,17 +603,18 @@ def run_other(args):
         assert F.status_poll() == 0
         byts = m.n_elem * (16 + 800 + 12 * 8) + m.n_vert * 24 * 2
         flops = m.n_elem * (2 * 100 * 9 + 300)
-        from oracle import shape as OS  # noqa: F401  (cpu baseline below)
-        import multiprocessing as mp
-        pool = mp.get_context("spawn").Pool(cores)
-        S = min(m.n_elem, 20000 * cores)
-        sel = np.linspace(0, m.n_elem - 1, S).astype(np.int64)
-        chunks = [(m.vertices, m.cells[sel[c::cores]], p.dofmap[sel[c::cores]], u, v) for c in range(cores)]
-        t0 = time.perf_counter()
-        pool.map(_oracle_shape, chunks)
-        cpu_rate = S / (time.perf_counter() - t0)
-        pool.close()
-        pool.join()
+        cpu_rate, S = None, 0
+        if not args.no_cpu_baseline:
+            import multiprocessing as mp
+            pool = mp.get_context("spawn").Pool(cores)
+            S = min(m.n_elem, 20000 * cores)
+            sel = np.linspace(0, m.n_elem - 1, S).astype(np.int64)
+            chunks = [(m.vertices, m.cells[sel[c::cores]], p.dofmap[sel[c::cores]], u, v) for c in range(cores)]
+            t0 = time.perf_counter()
+            pool.map(_oracle_shape, chunks)
+            cpu_rate = S / (time.perf_counter() - t0)
+            pool.close()
+            pool.join()
         out.update({"metric": "element adjoints/s (P2 Poisson dL/dvertices, 56^3x6 tets)",
                     "value": m.n_elem / t, "ms_per_step": t * 1e3, "dtype": "f64",
                     "config": {"workload": "adjoint_p2", "cells": m.n_elem, "vertices": m.n_vert},

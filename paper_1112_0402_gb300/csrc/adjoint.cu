@@ -10,10 +10,10 @@
 // x_{c+1} - x_0, so dL/dx_{c+1} += dL/dJ[:, c] and dL/dx_0 -= sum_c dL/dJ[:, c]; the
 // vertex gradients are accumulated with FP64 atomic adds.
 //
-// One warp per cell: the lanes stride over the n^2 entries (coalesced reads of dA),
-// keep |alpha| = d^2 partial sums against the transposed reference tensor held in
-// shared memory, reduce them with warp shuffles, and lane 0 finishes the geometry
-// chain rule. FP64 throughout.
+// A warp takes 32 cells: for each, the lanes stride over the n^2 entries (coalesced
+// reads of dA) keeping |alpha| = d^2 partial sums against the transposed reference
+// tensor held in shared memory, and reduce them with warp shuffles; lane k keeps cell
+// k's Gbar. Then all 32 lanes run the geometry chain rule, one cell each. FP64.
 #include <cuda_runtime.h>
 
 #include "ffc_internal.h"
@@ -39,21 +39,36 @@ __global__ void __launch_bounds__(WARPS * 32) poisson_adjoint_kernel(const int32
   const int lane = threadIdx.x & 31;
   const long long warp_global = (long long)blockIdx.x * WARPS + (threadIdx.x >> 5);
   const long long n_warps = (long long)gridDim.x * WARPS;
-  for (long long e = warp_global; e < n_elem; e += n_warps) {
-    double gb[NA];
+  // each warp takes 32 consecutive cells: the lanes reduce Gbar for one cell at a
+  // time (lane k keeps cell k's sums), then every lane runs the chain rule of its cell
+  for (long long base = warp_global * 32; base < n_elem; base += n_warps * 32) {
+    double mine[NA];
 #pragma unroll
-    for (int a = 0; a < NA; ++a) gb[a] = 0.0;
-    const double* row = dA + e * NN;
-    for (int i = lane; i < NN; i += 32) {
-      const double g = __ldg(row + i);
+    for (int a = 0; a < NA; ++a) mine[a] = 0.0;
+    const int count = (n_elem - base) < 32 ? int(n_elem - base) : 32;
+#pragma unroll 1
+    for (int k = 0; k < count; ++k) {
+      double gb[NA];
 #pragma unroll
-      for (int a = 0; a < NA; ++a) gb[a] = fma(a0s[a * NN + i], g, gb[a]);
+      for (int a = 0; a < NA; ++a) gb[a] = 0.0;
+      const double* row = dA + (base + k) * NN;
+      for (int i = lane; i < NN; i += 32) {
+        const double g = __ldg(row + i);
+#pragma unroll
+        for (int a = 0; a < NA; ++a) gb[a] = fma(a0s[a * NN + i], g, gb[a]);
+      }
+#pragma unroll
+      for (int a = 0; a < NA; ++a) {
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) gb[a] += __shfl_xor_sync(0xffffffffu, gb[a], off);
+        if (lane == k) mine[a] = gb[a];
+      }
     }
+    if (lane < count) {
+      const long long e = base + lane;
+      double gb[NA];
 #pragma unroll
-    for (int a = 0; a < NA; ++a)
-#pragma unroll
-      for (int off = 16; off > 0; off >>= 1) gb[a] += __shfl_xor_sync(0xffffffffu, gb[a], off);
-    if (lane == 0) {
+      for (int a = 0; a < NA; ++a) gb[a] = mine[a];
       double K[D][D], s;
       bool degenerate, bad_index;
       cell_geometry<D>(cells, vertices, n_vert, e, K, s, degenerate, bad_index);
@@ -133,7 +148,7 @@ int run(const LaunchArgs& a, const double* dA, double* dvert) {
     if (per_sm < 1) per_sm = 1;
   }
   long long grid = (long long)sms * per_sm;
-  const long long need = (a.n_elem + WARPS - 1) / WARPS;
+  const long long need = (a.n_elem + 32 * WARPS - 1) / (32 * WARPS);
   if (grid > need) grid = need;
   kern<<<unsigned(grid), WARPS * 32, SMEM, static_cast<cudaStream_t>(a.stream)>>>(
       a.cells, a.vertices, a.n_vert, a.t->a0t_f64, dA, dvert, a.n_elem, a.status);

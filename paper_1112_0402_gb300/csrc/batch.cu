@@ -61,7 +61,7 @@ __device__ __forceinline__ void run_tile(const SimtParams& p, long long tile, un
 }
 
 template <int KE>
-__global__ void __launch_bounds__(BATCH_BLOCK, 1)
+__global__ void __launch_bounds__(BATCH_BLOCK, 2)
     batch_assemble_kernel(const WorkItem* __restrict__ items, int n_items, long long total_tiles,
                           unsigned long long* queue) {
   extern __shared__ __align__(16) unsigned char smem[];

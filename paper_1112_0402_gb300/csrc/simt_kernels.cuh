@@ -16,6 +16,7 @@
 #pragma once
 
 #include <cstdint>
+#include <type_traits>
 
 #include "geometry.cuh"
 
@@ -36,7 +37,9 @@ struct SimtCfg {
   static constexpr int NTI = (NN + R - 1) / R;
   static constexpr int EG = BLOCK > 0 ? BLOCK / NTI : (NTI >= 256 ? 1 : 256 / NTI);
   static constexpr int NT = BLOCK > 0 ? BLOCK : NTI * EG;
-  static constexpr bool REG_A0 = (R * NA * int(sizeof(T)) / 4) <= 96;
+  // register-resident reference tensor rows; a shared block size (several forms in one
+  // kernel) keeps it only for small |alpha| so the kernel's register count stays low
+  static constexpr bool REG_A0 = (R * NA * int(sizeof(T)) / 4) <= (BLOCK > 0 ? 32 : 96);
   static constexpr int KE_TARGET = KE_T > 0 ? KE_T : (REG_A0 ? 64 : 16);
   static constexpr int KE = (KE_TARGET + EG - 1) / EG;
   static constexpr int E = EG * KE;
@@ -183,11 +186,26 @@ __device__ __forceinline__ void simt_tile(const SimtParams& p, long long tile, u
         T acc[C::KE];
 #pragma unroll
         for (int k = 0; k < C::KE; ++k) acc[k] = T(0);
-#pragma unroll 2
-        for (int a = 0; a < C::NA; ++a) {
-          const T av = __ldg(A0T + size_t(a) * C::NN + i);
+        // VEC alphas per step: one 16-byte shared-memory load of G feeds VEC FMAs
+        using V = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+#pragma unroll 1
+        for (int a0 = 0; a0 < C::NAP; a0 += C::VEC) {
+          T av[C::VEC];
 #pragma unroll
-          for (int k = 0; k < C::KE; ++k) acc[k] = fma(Gs[(eg + k * C::EG) * C::NAP + a], av, acc[k]);
+          for (int j = 0; j < C::VEC; ++j) av[j] = (a0 + j < C::NA) ? __ldg(A0T + size_t(a0 + j) * C::NN + i) : T(0);
+#pragma unroll
+          for (int k = 0; k < C::KE; ++k) {
+            const V gv = *reinterpret_cast<const V*>(Gs + (eg + k * C::EG) * C::NAP + a0);
+            if constexpr (sizeof(T) == 4) {
+              acc[k] = fma(gv.x, av[0], acc[k]);
+              acc[k] = fma(gv.y, av[1], acc[k]);
+              acc[k] = fma(gv.z, av[2], acc[k]);
+              acc[k] = fma(gv.w, av[3], acc[k]);
+            } else {
+              acc[k] = fma(gv.x, av[0], acc[k]);
+              acc[k] = fma(gv.y, av[1], acc[k]);
+            }
+          }
         }
 #pragma unroll
         for (int k = 0; k < C::KE; ++k) {

@@ -404,6 +404,9 @@ struct TcWsCfg {
   static constexpr size_t B_TOTAL = size_t(S::PARTS) * Base::B_BYTES;
   static constexpr int STAGES = (2 * A_TOTAL + B_TOTAL + 512 <= 227 * 1024) ? 2 : 1;
   static constexpr size_t SMEM = STAGES * A_TOTAL + B_TOTAL + 256;
+  // TMEM columns per accumulator buffer: main (+ correction) x 128 cells
+  static constexpr int ACC_COLS = S::NPROD > 1 ? 2 * N_CELLS : N_CELLS;
+  static constexpr uint32_t TMEM_COLS = 2 * ACC_COLS;
 };
 
 // Bounded wait that also gives up when another role has aborted.
@@ -528,7 +531,7 @@ __global__ void __launch_bounds__(WS_THREADS, 1) tc_ws_kernel(TcParams p) {
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                 "r"(uint32_t(2 * N_CELLS)));
+                 "r"(W::TMEM_COLS));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   fence_before();
@@ -572,7 +575,10 @@ __global__ void __launch_bounds__(WS_THREADS, 1) tc_ws_kernel(TcParams p) {
           }
           if (!ok) break;
           fence_after();
-          const uint32_t d = tmem + uint32_t(acc * N_CELLS);
+          // main product (part 0 x part 0) and the correction products accumulate
+          // separately; the epilogue adds them once
+          const uint32_t d_main = tmem + uint32_t(acc * W::ACC_COLS);
+          const uint32_t d_corr = d_main + uint32_t(N_CELLS);
 #pragma unroll 1
           for (int ks = 0; ks < C::KPAD / S::KSTEP; ++ks) {
             const uint32_t off = ks * 256;
@@ -581,7 +587,8 @@ __global__ void __launch_bounds__(WS_THREADS, 1) tc_ws_kernel(TcParams p) {
               const uint64_t da =
                   smem_desc(smem_u32(As + stage * W::A_TOTAL + S::pa(k) * C::A_BYTES) + off, 128, SBO);
               const uint64_t db = smem_desc(smem_u32(Bs + S::pb(k) * C::B_BYTES) + off, 128, SBO);
-              mma<S::BF16>(d, da, db, IDESC, (ks > 0 || k > 0) ? 1u : 0u);
+              if (k == S::NPROD - 1) mma<S::BF16>(d_main, da, db, IDESC, ks > 0 ? 1u : 0u);
+              else mma<S::BF16>(d_corr, da, db, IDESC, (ks > 0 || k > 0) ? 1u : 0u);
             }
           }
           mma_commit(bar(4 + acc));
@@ -663,11 +670,17 @@ __global__ void __launch_bounds__(WS_THREADS, 1) tc_ws_kernel(TcParams p) {
         }
         fence_after();
         const int i = mt * M_TILE + q4 * 32 + lane;
-        const uint32_t taddr = tmem + (uint32_t(q4 * 32) << 16) + uint32_t(acc * N_CELLS + half * 64);
+        const uint32_t taddr = tmem + (uint32_t(q4 * 32) << 16) + uint32_t(acc * W::ACC_COLS + half * 64);
 #pragma unroll 1
         for (int c = 0; c < 4; ++c) {
           float v[16];
           tmem_ld16(taddr + c * 16, v);
+          if constexpr (S::NPROD > 1) {
+            float w[16];
+            tmem_ld16(taddr + N_CELLS + c * 16, w);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) v[j] += w[j];
+          }
           if (i < C::NN) {
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
@@ -698,7 +711,7 @@ __global__ void __launch_bounds__(WS_THREADS, 1) tc_ws_kernel(TcParams p) {
   __syncthreads();
   if (warp == 0) {
     fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(uint32_t(2 * N_CELLS)));
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(W::TMEM_COLS));
   }
 }
 
@@ -785,8 +798,8 @@ int launch_one(const LaunchArgs& a) {
   p.mu = a.f->mu;
   p.lambda = a.f->lambda;
   p.status = a.status;
-  using W = TcCfg<D, FORM, Q, MODE>;
-  auto kern = tc_tabulate_kernel<D, FORM, Q, MODE, ASSEMBLE>;
+  using W = TcWsCfg<D, FORM, Q, MODE>;
+  auto kern = tc_ws_kernel<D, FORM, Q, MODE, ASSEMBLE>;
   static int sms = 0;
   if (sms == 0) {
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(W::SMEM)) != cudaSuccess)
@@ -798,7 +811,7 @@ int launch_one(const LaunchArgs& a) {
   const long long n_tiles = (a.n_elem + N_CELLS - 1) / N_CELLS;
   long long grid = sms;
   if (grid > n_tiles) grid = n_tiles;
-  kern<<<unsigned(grid), THREADS, W::SMEM, static_cast<cudaStream_t>(a.stream)>>>(p);
+  kern<<<unsigned(grid), WS_THREADS, W::SMEM, static_cast<cudaStream_t>(a.stream)>>>(p);
   (void)sizeof(C);
   return cudaPeekAtLastError() == cudaSuccess ? FFC_OK : FFC_ECUDA;
 }
