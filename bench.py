@@ -59,6 +59,30 @@ def parse_args():
     return ap.parse_args()
 
 
+# ------------------------------------------------------------------ ranks
+def dist_env():
+    """(world, rank, local_rank) from the launcher's environment (1, 0, 0 without one)."""
+    return (int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def shard(n_units: int, rank: int, world: int) -> list[int]:
+    """Independent units (meshes, problems) of this rank: round-robin, no data exchange."""
+    return list(range(rank, n_units, world))
+
+
+def max_over_ranks(seconds: float, world: int, device=None) -> float:
+    """Slowest rank's time (the job's time); a no-op with one rank."""
+    if world <= 1:
+        return seconds
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([seconds], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 # ------------------------------------------------------------------ clocks
 class ClockSampler:
     FIELDS = ("pci.bus_id,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -242,9 +266,7 @@ def main():
     import torch
     import torch.distributed as dist
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    world, rank, local = dist_env()
     if world > 1:
         torch.cuda.set_device(local)
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
@@ -291,11 +313,7 @@ def main():
     stop.record()
     barrier()
     clk = clocks.stop()
-    elapsed = start.elapsed_time(stop) / 1e3
-    t_max = torch.tensor([elapsed], dtype=torch.float64, device=device)
-    if world > 1:
-        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
-    elapsed = float(t_max.item())
+    elapsed = max_over_ranks(start.elapsed_time(stop) / 1e3, world, device)
     assert F.status_poll() == 0
     per_launch = np.zeros(P)
     for s in range(args.steps):
@@ -346,11 +364,7 @@ def main():
             e2e_step()
         b.record()
         barrier()
-        te = a.elapsed_time(b) / 1e3
-        t_e = torch.tensor([te], dtype=torch.float64, device=device)
-        if world > 1:
-            dist.all_reduce(t_e, op=dist.ReduceOp.MAX)
-        te = float(t_e.item())
+        te = max_over_ranks(a.elapsed_time(b) / 1e3, world, device)
         e2e = {"value": world * P * n_elem * args.steps / te, "unit": "elem/s",
                "h2d_bytes_per_step": int(h_cells.numel() * 4 + h_verts.numel() * 8),
                "d2h_bytes_per_step": int(sum(pr["nnz"] for pr in ctx["problems"]) * 8),

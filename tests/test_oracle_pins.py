@@ -158,7 +158,7 @@ RATIONAL_TETS = [
     [(0, 0, 0), (1, 0, 0), (0, 1, 0), (0, 0, 1)],
     [(Fraction(1, 3), 0, 0), (Fraction(1, 2), Fraction(1, 10), 0), (Fraction(1, 5), Fraction(3, 5), Fraction(1, 7)),
      (Fraction(1, 9), Fraction(1, 4), Fraction(2, 3))],
-    [(0, 0, 0), (0, 1, 0), (1, 0, 0), (Fraction(1, 2), Fraction(1, 2), Fraction(-3, 4))],  # negative orientation
+    [(0, 0, 0), (1, 0, 0), (0, 1, 0), (Fraction(1, 2), Fraction(1, 2), Fraction(-3, 4))],  # negative orientation
 ]
 
 
