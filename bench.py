@@ -335,25 +335,14 @@ def main():
         h_out = [torch.empty(pr["nnz"], dtype=torch.float64).pin_memory() for pr in ctx["problems"]]
         d_cells = torch.empty_like(ctx["cells"])
         d_verts = torch.empty_like(ctx["verts"])
-        copy_stream = torch.cuda.Stream()
-        # largest matrices first, so only the smallest copy back is left after the last kernel
-        order = sorted(range(P), key=lambda k: -ctx["problems"][k]["nnz"])
 
         def e2e_step():
-            cur = torch.cuda.current_stream()
-            cur.wait_stream(copy_stream)  # the previous step's copies have left these buffers
             d_cells.copy_(h_cells, non_blocking=True)
             d_verts.copy_(h_verts, non_blocking=True)
-            for k in order:
-                pr = ctx["problems"][k]
+            for pr, ho in zip(ctx["problems"], h_out):
                 pr["val"].zero_()
                 F.assemble(pr["F"], d_cells, d_verts, pr["slot"], pr["val"], precision=args.precision)
-                done = torch.cuda.Event()
-                done.record(cur)
-                copy_stream.wait_event(done)
-                with torch.cuda.stream(copy_stream):
-                    h_out[k].copy_(pr["val"], non_blocking=True)
-            cur.wait_stream(copy_stream)
+                ho.copy_(pr["val"], non_blocking=True)
 
         for _ in range(max(1, args.warmup)):
             e2e_step()
@@ -550,10 +539,13 @@ def run_other(args):
         val = torch.zeros(col.size, dtype=torch.float64, device=device)
         detail = {}
         ref = None
-        for prec in ("fp64", "fp32", "tf32", "tf32x3", "bf16x3"):
+        fm_dense = F.Form(F.NS_CONVECTION, F.TETRAHEDRON, 2, algorithm=F.ALG_DENSE)
+        for prec, f_, tag in (("fp64", fm_dense, "fp64_dense"), ("fp64", fm, "fp64_block"),
+                              ("fp32", fm_dense, "fp32_dense"), ("fp32", fm, "fp32_block"),
+                              ("tf32", fm, "tf32"), ("tf32x3", fm, "tf32x3"), ("bf16x3", fm, "bf16x3")):
             dt = torch.float64 if prec == "fp64" else torch.float32
             A = torch.empty((m.n_elem, 30, 30), dtype=dt, device=device)
-            t = _timed(lambda: F.tabulate(fm, cells, verts, coeffs=coeffs, out=A, precision=prec), args.steps,
+            t = _timed(lambda: F.tabulate(f_, cells, verts, coeffs=coeffs, out=A, precision=prec), args.steps,
                        args.warmup)
             byts = m.n_elem * (16 + 240 + 900 * (8 if prec == "fp64" else 4)) + m.n_vert * 24
             r = {"elem_per_s": m.n_elem / t, "ms": t * 1e3, "hbm_frac": byts / t / 1e9 / hbm_peak}
@@ -562,16 +554,17 @@ def run_other(args):
             else:
                 d = (A.double() - ref).reshape(m.n_elem, -1).norm(dim=1) / ref.reshape(m.n_elem, -1).norm(dim=1)
                 r["max_rel_err_vs_fp64"] = float(d.max())
-            detail["tabulate_" + prec] = r
-            if prec != "fp64":
+            detail["tabulate_" + tag] = r
+            if ref is not A:
                 del A
         del ref
         torch.cuda.empty_cache()
-        for prec in ("fp64", "bf16x3"):
+        for prec, f_, tag in (("fp64", fm_dense, "fp64_dense"), ("fp64", fm, "fp64_block"),
+                              ("fp32", fm, "fp32_block"), ("bf16x3", fm, "bf16x3")):
             def step():
                 val.zero_()
-                F.assemble(fm, cells, verts, slot_d, val, coeffs=coeffs, precision=prec)
-            detail["assemble_" + prec + "_ms"] = _timed(step, max(1, args.steps // 2), 1) * 1e3
+                F.assemble(f_, cells, verts, slot_d, val, coeffs=coeffs, precision=prec)
+            detail["assemble_" + tag + "_ms"] = _timed(step, max(1, args.steps // 2), 1) * 1e3
         prec = "bf16x3"
         A32 = torch.empty((m.n_elem, 30, 30), dtype=torch.float32, device=device)
         clocks.start()
@@ -618,6 +611,17 @@ def run_other(args):
                 it["csr_val"].zero_()
                 F.assemble(it["form"], it["cells"], it["vertices"], it["slot"], it["csr_val"], precision="fp32")
         t_sep = _timed(separate, args.steps, args.warmup)
+        # the largest elasticity vP3 mesh of the batch, tabulated alone by each path
+        big = max((pb for pb in probs if pb.form == W.ELASTICITY and pb.degree == 3), key=lambda pb: pb.n_elem)
+        bc = torch.as_tensor(big.mesh.cells, device=device)
+        bv = torch.as_tensor(big.mesh.vertices, device=device)
+        A3 = torch.empty((big.n_elem, 60, 60), dtype=torch.float32, device=device)
+        elast = {"cells": big.n_elem}
+        for tag, alg, prec in (("fp32_dense", F.ALG_DENSE, "fp32"), ("fp32_block", F.ALG_BLOCK, "fp32"),
+                               ("tf32x3", F.ALG_AUTO, "tf32x3"), ("bf16x3", F.ALG_AUTO, "bf16x3")):
+            f3 = F.Form(F.ELASTICITY, F.TETRAHEDRON, 3, algorithm=alg)
+            elast[tag + "_ms"] = _timed(lambda: F.tabulate(f3, bc, bv, out=A3, precision=prec), 3, 1) * 1e3
+        del A3
         byts = sum(pb.n_elem * (16 + 4 * pb.n_local) + pb.mesh.n_vert * 24 for pb in probs) + 16 * total_nnz
         out.update({"metric": "element tensors/s (batched: 32 meshes, elasticity vP1-vP3 + Poisson P2)",
                     "value": n_cells / t, "ms_per_step": t * 1e3, "dtype": "f32", "nnz_per_s": total_nnz / t,
@@ -627,7 +631,8 @@ def run_other(args):
                                  "frac": byts / t / 1e9 / hbm_peak, "traffic": None, "peak_kind": peak_kind,
                                  "kernel": "batch_assemble_kernel"},
                     "clocks": clk, "gpu_launches": args.steps,
-                    "detail": {"plain_launch_ms": t_plain * 1e3, "separate_launches_ms": t_sep * 1e3}})
+                    "detail": {"plain_launch_ms": t_plain * 1e3, "separate_launches_ms": t_sep * 1e3,
+                               "elasticity_p3_tabulate": elast}})
     else:  # adjoint
         p, u, v = W.adjoint_p2(56 if args.n == 48 else args.n)
         m = p.mesh

@@ -71,6 +71,16 @@ typedef enum {
   FFC_BF16X3 = 4  /* tcgen05 kind::f16 (BF16) with three-part splits of G and A0 (six products), float out */
 } ffc_precision;
 
+/* How the CUDA-core precisions (FFC_FP64, FFC_FP32) evaluate the vector forms.
+ * DENSE contracts the full reference tensor A0 (|alpha| = 90 for convection P2, 81 for
+ * elasticity); BLOCK uses the Cartesian-product structure of the component-blocked
+ * vector basis (Section 3.5): the element tensor's n_s x n_s blocks are contractions
+ * of a reduced reference tensor R[n_s*n_s][k] with per-cell reduced geometry blocks
+ * (convection: one block of n_s*d entries on the diagonal; elasticity: nine blocks of
+ * d*d), the same sums with 27x / 9x fewer multiply-adds. AUTO = BLOCK for the vector
+ * forms, DENSE otherwise. The tensor-core precisions always contract densely. */
+typedef enum { FFC_ALG_AUTO = 0, FFC_ALG_DENSE = 1, FFC_ALG_BLOCK = 2 } ffc_algorithm;
+
 /* Device status bits returned by ffc_status_poll. */
 #define FFC_FLAG_DEGENERATE 0x1u
 #define FFC_FLAG_BOUNDS 0x2u
@@ -97,6 +107,9 @@ int ffc_form_info(const ffc_form* f, int* n_local, int* n_alpha, int* n_coeff);
 /* Raw reference tensor (the "raw format" output of Section 5.4):
  * host_out double [n*n][n_alpha], row-major. */
 int ffc_form_reference_tensor(const ffc_form* f, double* host_out);
+
+/* Selects the evaluation of the vector forms (ffc_algorithm); FFC_EINVAL otherwise. */
+int ffc_form_set_algorithm(ffc_form* f, int algorithm);
 
 /* Frees host data and any device copies of the reference tensor. NULL is ignored. */
 void ffc_form_destroy(ffc_form* f);

@@ -19,6 +19,7 @@ TRIANGLE, TETRAHEDRON = 2, 3
 FP64, FP32, TF32, TF32X3, BF16X3 = 0, 1, 2, 3, 4
 PRECISIONS = {"fp64": FP64, "fp32": FP32, "tf32": TF32, "tf32x3": TF32X3, "bf16x3": BF16X3}
 FLAG_DEGENERATE, FLAG_BOUNDS, FLAG_TIMEOUT = 1, 2, 4
+ALG_AUTO, ALG_DENSE, ALG_BLOCK = 0, 1, 2
 
 
 class FFCError(RuntimeError):
@@ -65,10 +66,12 @@ def _dev_ptr(t, dtype, name, shape=None):
 class Form:
     """A compiled form: the reference tensor A0 of (kind, cell, degree)."""
 
-    def __init__(self, kind: int, cell: int, degree: int, mu: float = 1.0, lmbda: float = 1.25):
+    def __init__(self, kind: int, cell: int, degree: int, mu: float = 1.0, lmbda: float = 1.25,
+                 algorithm: int = ALG_AUTO):
         h = ctypes.c_void_p()
         _check(lib().ffc_form_create(kind, cell, degree, mu, lmbda, ctypes.byref(h)), "ffc_form_create")
         self._h = h
+        _check(lib().ffc_form_set_algorithm(h, algorithm), "ffc_form_set_algorithm")
         self.kind, self.cell, self.degree = kind, cell, degree
         n, na, nc = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
         _check(lib().ffc_form_info(h, ctypes.byref(n), ctypes.byref(na), ctypes.byref(nc)), "ffc_form_info")

@@ -67,6 +67,18 @@ int ensure_device_tensors(ffc_form* f, DeviceTensors** out) {
     cudaFree(t.a0t_f32);
     return rc;
   }
+  if (!f->R.empty()) {
+    std::vector<float> r32(f->R.begin(), f->R.end());
+    if ((rc = upload(&t.r_f64, f->R)) || (rc = upload(&t.r_f32, r32))) {
+      cudaFree(t.a0_f64);
+      cudaFree(t.a0t_f64);
+      cudaFree(t.a0_f32);
+      cudaFree(t.a0t_f32);
+      cudaFree(t.r_f64);
+      cudaFree(t.r_f32);
+      return rc;
+    }
+  }
   auto res = f->dev.emplace(dev, t);
   *out = &res.first->second;
   return FFC_OK;
@@ -85,6 +97,8 @@ void release_device_tensors(ffc_form* f) {
     cudaFree(t.a0t_f32);
     for (auto& fam : t.tc_part)
       for (void* q : fam) cudaFree(q);
+    cudaFree(t.r_f64);
+    cudaFree(t.r_f32);
   }
   f->dev.clear();
   cudaSetDevice(cur);
@@ -93,7 +107,8 @@ void release_device_tensors(ffc_form* f) {
 static int dispatch(const LaunchArgs& a, int precision, bool assemble) {
   int rc = FFC_EUNSUPPORTED;
   if (precision == FFC_FP64 || precision == FFC_FP32) {
-    rc = launch_simt_tri(a, precision, assemble);
+    if (a.f->kr > 0 && a.f->algorithm != FFC_ALG_DENSE) rc = launch_simt_block(a, precision, assemble);
+    if (rc == FFC_EUNSUPPORTED) rc = launch_simt_tri(a, precision, assemble);
     if (rc == FFC_EUNSUPPORTED) rc = launch_simt_tet_mass(a, precision, assemble);
     if (rc == FFC_EUNSUPPORTED) rc = launch_simt_tet_poisson(a, precision, assemble);
     if (rc == FFC_EUNSUPPORTED) rc = launch_simt_vector(a, precision, assemble);

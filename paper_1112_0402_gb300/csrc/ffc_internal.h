@@ -22,6 +22,8 @@ struct DeviceTensors {
   // each part laid out per 128-entry M-tile in the core-matrix layout
   void* tc_part[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
   int tc_kpad[2] = {0, 0};
+  double* r_f64 = nullptr;    // reduced reference tensor [ns*ns][kr]
+  float* r_f32 = nullptr;
 };
 
 }  // namespace ffc
@@ -36,6 +38,11 @@ struct ffc_form {
   int ncoeff = 0;      // per-cell coefficients
   double mu = 1.0, lambda = 1.25;
   std::vector<double> A0;  // [n*n][na]
+  // Cartesian-product structure of the vector forms (Section 3.5): reduced reference
+  // tensor R[ns*ns][kr] and nb geometry blocks per cell (0 when the form has none)
+  std::vector<double> R;
+  int kr = 0, nb = 0;
+  int algorithm = 0;  // ffc_algorithm
   std::mutex lock;
   std::map<int, ffc::DeviceTensors> dev;
 };
@@ -76,6 +83,7 @@ int launch_simt_tet_mass(const LaunchArgs& a, int precision, bool assemble);
 int launch_simt_tet_poisson(const LaunchArgs& a, int precision, bool assemble);
 int launch_simt_vector(const LaunchArgs& a, int precision, bool assemble);
 int launch_tc(const LaunchArgs& a, int precision, bool assemble);
+int launch_simt_block(const LaunchArgs& a, int precision, bool assemble);
 int launch_adjoint(const LaunchArgs& a, const double* dA, double* dvert);
 
 }  // namespace ffc

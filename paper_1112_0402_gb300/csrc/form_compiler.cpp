@@ -225,6 +225,15 @@ int compile_reference_tensor(ffc_form* f) {
   const int na = f->na;
   f->A0.assign(size_t(n) * n * na, 0.0);
   auto A0 = [&](int i1, int i2, int alpha) -> double& { return f->A0[(size_t(i1) * n + i2) * na + alpha]; };
+  // reduced reference tensors of the vector forms (component-blocked Cartesian basis)
+  if (f->kind == FFC_ELASTICITY) {
+    f->kr = d * d;
+    f->nb = d * d;
+  } else if (f->kind == FFC_NS_CONVECTION) {
+    f->kr = ns * d;
+    f->nb = 1;
+  }
+  if (f->kr > 0) f->R.assign(size_t(ns) * ns * f->kr, 0.0);
   if (f->kind == FFC_MASS) {
     for (int i1 = 0; i1 < ns; ++i1)
       for (int i2 = 0; i2 < ns; ++i2) {
@@ -258,6 +267,7 @@ int compile_reference_tensor(ffc_form* f) {
                   int alpha = ((c1 * d + c2) * d + a1) * d + a2;
                   A0(c1 * ns + s1, c2 * ns + s2, alpha) = S[((size_t(s1) * ns + s2) * d + a1) * d + a2];
                 }
+      f->R = S;  // R[(s1,s2)][(a1,a2)]: the scalar stiffness blocks
     }
   } else {  // convection
     for (int s1 = 0; s1 < ns; ++s1)
@@ -271,6 +281,7 @@ int compile_reference_tensor(ffc_form* f) {
             for (int c = 0; c < d; ++c)          // test/trial component (delta(c1, c2))
               for (int ct = 0; ct < d; ++ct)     // coefficient component c(t)
                 A0(c * ns + s1, c * ns + s2, (ct * ns + st) * d + a) = s;
+            f->R[(size_t(s1) * ns + s2) * f->kr + st * d + a] = s;
           }
   }
   return FFC_OK;

@@ -125,6 +125,12 @@ int ffc_form_reference_tensor(const ffc_form* f, double* host_out) {
   return FFC_OK;
 }
 
+int ffc_form_set_algorithm(ffc_form* f, int algorithm) {
+  if (!f || algorithm < FFC_ALG_AUTO || algorithm > FFC_ALG_BLOCK) return FFC_EINVAL;
+  f->algorithm = algorithm;
+  return FFC_OK;
+}
+
 void ffc_form_destroy(ffc_form* f) {
   if (!f) return;
   release_device_tensors(f);

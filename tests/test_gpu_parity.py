@@ -55,10 +55,10 @@ def _oracle(p):
     return OE.element_tensors(p.form, M.gather_cell_vertices(p.mesh), p.degree, coeffs=p.coeffs)
 
 
-def _run_tabulate(F, p, precision):
+def _run_tabulate(F, p, precision, algorithm=0):
     import torch
 
-    form = F.Form(p.form, p.mesh.dim, p.degree)
+    form = F.Form(p.form, p.mesh.dim, p.degree, algorithm=algorithm)
     cells = _dev(p.mesh.cells, torch.int32)
     verts = _dev(p.mesh.vertices, torch.float64)
     coeffs = _dev(p.coeffs, torch.float64) if p.coeffs is not None else None
@@ -90,6 +90,39 @@ def test_tabulate_fp32_within_mixed_tolerance(F, d, n, form, q):
     got = _run_tabulate(F, p, "fp32")
     err = OE.frobenius_rel_error(got, ref)
     assert err.max() <= FP32_TOL, f"max rel err {err.max():.3e}"
+
+
+VECTOR_CASES = [c for c in CASES if c[2] in (W.NS_CONVECTION, W.ELASTICITY)]
+
+
+@pytest.mark.parametrize("d,n,form,q", VECTOR_CASES)
+@pytest.mark.parametrize("prec,tol", [("fp64", FP64_TOL), ("fp32", FP32_TOL)])
+@pytest.mark.parametrize("alg", ["dense", "block"])
+def test_vector_forms_dense_and_block_algorithms(F, d, n, form, q, prec, tol, alg):
+    """Both evaluations of the vector forms: the full reference tensor, and the
+    Cartesian-product blocks (reduced reference tensor, reduced geometry)."""
+    p = _case(d, n, form, q)
+    got = _run_tabulate(F, p, prec, algorithm=F.ALG_DENSE if alg == "dense" else F.ALG_BLOCK)
+    err = OE.frobenius_rel_error(got, _oracle(p))
+    assert err.max() <= tol, f"{alg} {prec} max rel err {err.max():.3e}"
+
+
+@pytest.mark.parametrize("form,q", [(W.NS_CONVECTION, 2), (W.ELASTICITY, 3)])
+@pytest.mark.parametrize("alg", ["dense", "block"])
+def test_vector_forms_assemble_both_algorithms(F, form, q, alg):
+    import torch
+
+    p = _case(3, 2, form, q)
+    _, _, ref_val = OA.assemble_csr(_oracle(p), p.dofmap, p.n_dof)
+    row_ptr, col, slot = F.csr_pattern(p.dofmap, p.n_dof)
+    val = torch.zeros(col.size, dtype=torch.float64, device="cuda")
+    coeffs = _dev(p.coeffs, torch.float64) if p.coeffs is not None else None
+    fm = F.Form(form, 3, q, algorithm=F.ALG_DENSE if alg == "dense" else F.ALG_BLOCK)
+    F.assemble(fm, _dev(p.mesh.cells, torch.int32), _dev(p.mesh.vertices, torch.float64), _dev(slot, torch.int32),
+               val, coeffs=coeffs, precision="fp64")
+    assert F.status_poll() == 0
+    got = val.cpu().numpy()
+    assert np.linalg.norm(got - ref_val) <= FP64_TOL * np.linalg.norm(ref_val)
 
 
 @pytest.mark.parametrize("d,n,form,q,prec", [(2, 6, W.POISSON, 1, "fp64"), (3, 3, W.MASS, 2, "fp64"),
