@@ -7,7 +7,8 @@ forms with scalar Lagrange P1..P4 -- eight (form, degree) problems.
 
 One step = for each of the eight problems: zero the CSR values and run the fused
 assembly (geometry G_K -> contraction A0:G_K -> atomic scatter into CSR through the
-precomputed slots), i.e. Algorithm 2 with the tensor representation. The headline
+precomputed slots), i.e. Algorithm 2 with the tensor representation. The zeroing runs on
+a second stream ahead of the assemblies; the step's time covers both. The headline
 `value` is element tensors computed and inserted per second over the whole step
 (8 x 663,552 per step); `nnz_per_s` is the assembled CSR entries per second.
 
@@ -53,6 +54,7 @@ def parse_args():
                     help="tet_scalar is the headline; the others print their own line")
     ap.add_argument("--precision", default="fp32", help="contraction arithmetic of the headline step")
     ap.add_argument("--n", type=int, default=48, help="hexes per axis")
+    ap.add_argument("--scale", type=float, default=1.0, help="batched workload: mesh size scale")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-detail", action="store_true")
@@ -151,13 +153,28 @@ def build_workload(F, n, device):
 
 
 def assemble_step(F, ctx, precision, events=None):
+    """Zero every CSR matrix and assemble it. The zeroing (bandwidth bound) runs on a side
+    stream, ahead of the assemblies (atomic-throughput bound) that wait for their matrix."""
+    import torch
+
+    main = torch.cuda.current_stream()
+    side = ctx.setdefault("side_stream", torch.cuda.Stream())
+    side.wait_stream(main)  # the previous step's assemblies are done with these values
+    zeroed = []
+    with torch.cuda.stream(side):
+        for pr in ctx["problems"]:
+            pr["val"].zero_()
+            ev = torch.cuda.Event()
+            ev.record(side)
+            zeroed.append(ev)
     for k, pr in enumerate(ctx["problems"]):
+        main.wait_event(zeroed[k])
         if events is not None:
-            events[k][0].record()
-        pr["val"].zero_()
+            events[k][0].record(main)
         F.assemble(pr["F"], ctx["cells"], ctx["verts"], pr["slot"], pr["val"], precision=precision)
         if events is not None:
-            events[k][1].record()
+            events[k][1].record(main)
+    main.wait_stream(side)
 
 
 def alg_bytes_assemble(ctx, pr):
@@ -170,6 +187,13 @@ def alg_bytes_assemble(ctx, pr):
 def alg_bytes_tabulate(ctx, n_local, out_bytes):
     m = ctx["mesh"]
     return m.n_elem * 16 + m.n_vert * 24 + m.n_elem * n_local * n_local * out_bytes
+
+
+# DRAM bytes (read + write) per launch of the fused P4 assemblies at 663,552 cells, from one
+# `ncu --set full` capture of these kernels at 24^3 x 6 = 82,944 cells scaled by the cell
+# count (x8; slots, CSR values and cells all grow with it). Only valid for the FP32 SIMT
+# assembly kernels as captured; other kernels report null.
+CAPTURED_TRAFFIC_GB = {("mass", 4, "fp32"): 1.597 * 8, ("poisson", 4, "fp32"): 1.479 * 8}
 
 
 def measured_peaks():
@@ -384,7 +408,10 @@ def main():
                        "l2": "inputs larger than L2: the step streams ~20 GB (CSR values, slots) per pass",
                        "parallelism": f"replicas x{world}"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                         "frac": achieved / hbm_peak, "traffic": None, "peak_kind": peak_kind,
+                         "frac": achieved / hbm_peak, "peak_kind": peak_kind,
+                         "traffic": CAPTURED_TRAFFIC_GB.get((FORM_NAME[dpr["form"]], dpr["q"], args.precision)),
+                         "traffic_unit": "GB per launch (ncu, scaled from 82,944 cells)",
+                         "algorithmic_gb": alg_bytes_assemble(ctx, dpr) / 1e9,
                          "kernel": f"assemble {FORM_NAME[dpr['form']]} P{dpr['q']} ({args.precision})",
                          "launch_ms": per_launch[dom] * 1e3},
             "per_launch_ms": {f"{FORM_NAME[p['form']]}_p{p['q']}": round(per_launch[k] * 1e3, 4)
@@ -585,7 +612,7 @@ def run_other(args):
                     "cpu_baseline": {"value": rate, "unit": "elem/s", "cores": cores, "kind": "oracle",
                                      "sample": f"{S} cells"}, "detail": detail})
     elif args.workload == "batched":
-        probs = W.batched()
+        probs = W.batched(scale=args.scale)
         items = []
         total_nnz = 0
         for pb in probs:
@@ -626,7 +653,8 @@ def run_other(args):
         out.update({"metric": "element tensors/s (batched: 32 meshes, elasticity vP1-vP3 + Poisson P2)",
                     "value": n_cells / t, "ms_per_step": t * 1e3, "dtype": "f32", "nnz_per_s": total_nnz / t,
                     "config": {"workload": "batched", "meshes": len(probs), "cells": n_cells, "nnz": total_nnz,
-                               "tile_cells_per_group": ke, "graph": True},
+                               "tile_cells_per_group": ke, "threads_per_block": b.threads_per_block,
+                               "graph": True},
                     "roofline": {"bound": "hbm", "achieved": byts / t / 1e9, "peak": hbm_peak, "unit": "GB/s",
                                  "frac": byts / t / 1e9 / hbm_peak, "traffic": None, "peak_kind": peak_kind,
                                  "kernel": "batch_assemble_kernel"},

@@ -61,8 +61,11 @@ typedef enum {
 
 typedef enum { FFC_TRIANGLE = 2, FFC_TETRAHEDRON = 3 } ffc_cell; /* value = spatial dimension d */
 
-/* Arithmetic of the contraction A0 : G. Geometry (J, det J, J^{-1}, G) is always
- * computed in FP64; FP64 is also the CSR accumulation type of ffc_assemble. */
+/* Arithmetic of the contraction A0 : G. J, det J and J^{-1} are always FP64; G_K is
+ * FP64 for the CUDA-core precisions and FP32 (from the FP64 J^{-1}, det J) for the
+ * tensor-core ones, which round it to their operand parts. FP64 is the CSR accumulation
+ * type of ffc_assemble. Tensor-core precisions are built for tetrahedra: convection P2,
+ * elasticity P1-P3, Poisson P2-P4, mass P3-P4 (others return FFC_EUNSUPPORTED). */
 typedef enum {
   FFC_FP64 = 0,   /* FP64 contraction, A_K stored as double */
   FFC_FP32 = 1,   /* FP32 G and A0, FP32 accumulation on CUDA cores, A_K stored as float */
@@ -197,13 +200,15 @@ typedef struct {
 
 /* zero_csr != 0: every run first zeroes each item's csr_val (a fresh assembly). */
 int ffc_batch_create(const ffc_batch_item* items, int n_items, int zero_csr, ffc_batch** out);
-/* Times the three tile variants (16, 32, 64 cells per thread group and tile) on the
- * caller's data, keeps the fastest and returns it; leaves every csr_val zeroed. */
-int ffc_batch_tune(ffc_batch* b, void* stream, int* cells_per_tile_group);
+/* Times the six tile variants (256 or 512 threads per block x 16, 32 or 64 cells per
+ * thread group and tile) on the caller's data, keeps the fastest and returns it (either
+ * output pointer may be NULL); leaves every csr_val zeroed. */
+int ffc_batch_tune(ffc_batch* b, void* stream, int* cells_per_tile_group, int* threads_per_block);
 /* One persistent launch (use_graph = 0), or the same work captured once into a CUDA
  * graph on `stream` and replayed (use_graph != 0). */
 int ffc_batch_run(ffc_batch* b, int use_graph, void* stream);
-int ffc_batch_info(const ffc_batch* b, int* n_items, long long* total_tiles, int* cells_per_tile_group);
+int ffc_batch_info(const ffc_batch* b, int* n_items, long long* total_tiles, int* cells_per_tile_group,
+                   int* threads_per_block);
 void ffc_batch_destroy(ffc_batch* b);
 
 /*

@@ -35,10 +35,10 @@ SIGNATURES = {
     "ffc_tabulate_static": (ctypes.c_int, [c_vp, ctypes.c_int64, c_vp, c_vp, ctypes.c_int64, c_vp, c_vp,
                                            ctypes.c_int, c_vp, c_u32p]),
     "ffc_batch_create": (ctypes.c_int, [c_vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(c_vp)]),
-    "ffc_batch_tune": (ctypes.c_int, [c_vp, c_vp, ctypes.POINTER(ctypes.c_int)]),
+    "ffc_batch_tune": (ctypes.c_int, [c_vp, c_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     "ffc_batch_run": (ctypes.c_int, [c_vp, ctypes.c_int, c_vp]),
     "ffc_batch_info": (ctypes.c_int, [c_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_longlong),
-                                      ctypes.POINTER(ctypes.c_int)]),
+                                      ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     "ffc_batch_destroy": (None, [c_vp]),
     "ffc_status_poll": (ctypes.c_int, [c_vp, c_u32p]),
     "ffc_status_string": (ctypes.c_char_p, [ctypes.c_int]),

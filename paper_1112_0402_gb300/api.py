@@ -213,18 +213,21 @@ class Batch:
         self._h = h
 
     def tune(self, stream=None) -> int:
-        c = ctypes.c_int()
-        _check(lib().ffc_batch_tune(self._h, _stream(stream), ctypes.byref(c)), "ffc_batch_tune")
+        """Picks the fastest tile variant; returns its cells per thread group and tile."""
+        c, b = ctypes.c_int(), ctypes.c_int()
+        _check(lib().ffc_batch_tune(self._h, _stream(stream), ctypes.byref(c), ctypes.byref(b)), "ffc_batch_tune")
+        self.threads_per_block = b.value
         return c.value
 
     def run(self, graph: bool = False, stream=None) -> None:
         _check(lib().ffc_batch_run(self._h, int(graph), _stream(stream)), "ffc_batch_run")
 
     def info(self):
-        n, tiles, ke = ctypes.c_int(), ctypes.c_longlong(), ctypes.c_int()
-        _check(lib().ffc_batch_info(self._h, ctypes.byref(n), ctypes.byref(tiles), ctypes.byref(ke)),
-               "ffc_batch_info")
-        return {"items": n.value, "tiles": tiles.value, "cells_per_tile_group": ke.value}
+        n, tiles, ke, blk = ctypes.c_int(), ctypes.c_longlong(), ctypes.c_int(), ctypes.c_int()
+        _check(lib().ffc_batch_info(self._h, ctypes.byref(n), ctypes.byref(tiles), ctypes.byref(ke),
+                                    ctypes.byref(blk)), "ffc_batch_info")
+        return {"items": n.value, "tiles": tiles.value, "cells_per_tile_group": ke.value,
+                "threads_per_block": blk.value}
 
     def close(self) -> None:
         if getattr(self, "_h", None):

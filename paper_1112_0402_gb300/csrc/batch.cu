@@ -7,10 +7,11 @@
 // the persistent kernel takes the next tile index from one global atomic counter
 // (no CTA ever waits for another), finds its problem by binary search over the
 // tables' first-tile indices, loads that form's reference-tensor rows and runs the
-// shared CUDA-core tile body: FP64 geometry, FP32 contraction, FP64 atomic scatter.
+// shared CUDA-core tile body: FP64 geometry, FP32 contraction, FP64 atomic scatter
+// (elasticity through the block-structured contraction, the other forms densely).
 //
-// The tile variant (cells per thread group per tile: 16, 32 or 64) is chosen by
-// timing all three on the caller's data (ffc_batch_tune). A run can be captured
+// The tile variant (256 or 512 threads per block x 16, 32 or 64 cells per thread group
+// and tile) is chosen by timing all six on the caller's data (ffc_batch_tune). A run can be captured
 // once into a CUDA graph (queue reset, optional CSR zeroing, kernel) and replayed.
 #include <cuda_runtime.h>
 
@@ -21,13 +22,16 @@
 #include <vector>
 
 #include "ffc_internal.h"
+#include "simt_block.cuh"
 #include "simt_kernels.cuh"
 
 namespace ffc {
 namespace {
 
-constexpr int BATCH_BLOCK = 256;
-constexpr int KE_VARIANTS[3] = {16, 32, 64};
+// Tile variants the autotuner times: block size x cells per thread group and tile.
+constexpr int N_VARIANTS = 6;
+constexpr int VARIANT_BLOCK[N_VARIANTS] = {256, 256, 256, 512, 512, 512};
+constexpr int VARIANT_KE[N_VARIANTS] = {16, 32, 64, 16, 32, 64};
 
 // Forms the batched kernel carries, by code.
 enum : int { CODE_ELAST_P1 = 0, CODE_ELAST_P2, CODE_ELAST_P3, CODE_POISSON_P1, CODE_POISSON_P2, CODE_MASS_P1,
@@ -42,8 +46,12 @@ template <> struct CodeForm<CODE_POISSON_P1> { static constexpr int FORM = FFC_P
 template <> struct CodeForm<CODE_POISSON_P2> { static constexpr int FORM = FFC_POISSON, Q = 2; };
 template <> struct CodeForm<CODE_MASS_P1> { static constexpr int FORM = FFC_MASS, Q = 1; };
 
-template <int CODE, int KE>
-using CfgOf = SimtCfg<3, CodeForm<CODE>::FORM, CodeForm<CODE>::Q, float, BATCH_BLOCK, KE>;
+template <int CODE, int BLK, int KE>
+using CfgOf = SimtCfg<3, CodeForm<CODE>::FORM, CodeForm<CODE>::Q, float, BLK, KE>;
+template <int CODE, int BLK, int KE>
+using BlockCfgOf = BlockCfg<3, CodeForm<CODE>::FORM, CodeForm<CODE>::Q, float, BLK, KE>;
+template <int CODE>
+constexpr bool kBlock = CodeForm<CODE>::FORM == FFC_ELASTICITY;
 
 struct WorkItem {
   int code;
@@ -52,16 +60,24 @@ struct WorkItem {
   SimtParams p;
 };
 
-template <int CODE, int KE>
+template <int CODE, int BLK, int KE>
 __device__ __forceinline__ void run_tile(const SimtParams& p, long long tile, unsigned char* smem) {
-  using C = CfgOf<CODE, KE>;
-  float a0r[C::REG_A0 ? C::R : 1][C::REG_A0 ? C::NA : 1];
-  load_a0_rows<C, float>(p.a0, threadIdx.x, a0r);
-  simt_tile<C, 3, CodeForm<CODE>::FORM, CodeForm<CODE>::Q, float, true>(p, tile, smem, a0r);
+  constexpr int FORM = CodeForm<CODE>::FORM, Q = CodeForm<CODE>::Q;
+  if constexpr (kBlock<CODE>) {
+    using C = BlockCfgOf<CODE, BLK, KE>;
+    BlockRows<C, float> rows;
+    block_rows_init<C, 3, FORM, float>(p.a0, rows, smem);
+    block_tile<C, 3, FORM, Q, float, true>(p, tile, smem, rows);
+  } else {
+    using C = CfgOf<CODE, BLK, KE>;
+    float a0r[C::REG_A0 ? C::R : 1][C::REG_A0 ? C::NA : 1];
+    load_a0_rows<C, float>(p.a0, threadIdx.x, a0r);
+    simt_tile<C, 3, FORM, Q, float, true>(p, tile, smem, a0r);
+  }
 }
 
-template <int KE>
-__global__ void __launch_bounds__(BATCH_BLOCK, 2)
+template <int BLK, int KE>
+__global__ void __launch_bounds__(BLK, BLK >= 512 ? 1 : 2)
     batch_assemble_kernel(const WorkItem* __restrict__ items, int n_items, long long total_tiles,
                           unsigned long long* queue) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -82,12 +98,12 @@ __global__ void __launch_bounds__(BATCH_BLOCK, 2)
     const SimtParams p = w.p;
     const long long local = tile - w.tile_begin;
     switch (w.code) {
-      case CODE_ELAST_P1: run_tile<CODE_ELAST_P1, KE>(p, local, smem); break;
-      case CODE_ELAST_P2: run_tile<CODE_ELAST_P2, KE>(p, local, smem); break;
-      case CODE_ELAST_P3: run_tile<CODE_ELAST_P3, KE>(p, local, smem); break;
-      case CODE_POISSON_P1: run_tile<CODE_POISSON_P1, KE>(p, local, smem); break;
-      case CODE_POISSON_P2: run_tile<CODE_POISSON_P2, KE>(p, local, smem); break;
-      case CODE_MASS_P1: run_tile<CODE_MASS_P1, KE>(p, local, smem); break;
+      case CODE_ELAST_P1: run_tile<CODE_ELAST_P1, BLK, KE>(p, local, smem); break;
+      case CODE_ELAST_P2: run_tile<CODE_ELAST_P2, BLK, KE>(p, local, smem); break;
+      case CODE_ELAST_P3: run_tile<CODE_ELAST_P3, BLK, KE>(p, local, smem); break;
+      case CODE_POISSON_P1: run_tile<CODE_POISSON_P1, BLK, KE>(p, local, smem); break;
+      case CODE_POISSON_P2: run_tile<CODE_POISSON_P2, BLK, KE>(p, local, smem); break;
+      case CODE_MASS_P1: run_tile<CODE_MASS_P1, BLK, KE>(p, local, smem); break;
       default: break;
     }
   }
@@ -98,31 +114,41 @@ struct CodeInfo {
   int cells_per_tile;
   size_t smem;
   bool reg_a0;
+  bool block;  // reads the reduced reference tensor
 };
 
-template <int CODE, int KE>
+template <int CODE, int BLK, int KE>
 CodeInfo info_of() {
-  using C = CfgOf<CODE, KE>;
-  return {C::E, C::SMEM, C::REG_A0};
+  if constexpr (kBlock<CODE>) {
+    using C = BlockCfgOf<CODE, BLK, KE>;
+    return {C::E, C::SMEM, false, true};
+  } else {
+    using C = CfgOf<CODE, BLK, KE>;
+    return {C::E, C::SMEM, C::REG_A0, false};
+  }
 }
 
-template <int KE>
+template <int V>
 CodeInfo code_info(int code) {
+  constexpr int BLK = VARIANT_BLOCK[V], KE = VARIANT_KE[V];
   switch (code) {
-    case CODE_ELAST_P1: return info_of<CODE_ELAST_P1, KE>();
-    case CODE_ELAST_P2: return info_of<CODE_ELAST_P2, KE>();
-    case CODE_ELAST_P3: return info_of<CODE_ELAST_P3, KE>();
-    case CODE_POISSON_P1: return info_of<CODE_POISSON_P1, KE>();
-    case CODE_POISSON_P2: return info_of<CODE_POISSON_P2, KE>();
-    default: return info_of<CODE_MASS_P1, KE>();
+    case CODE_ELAST_P1: return info_of<CODE_ELAST_P1, BLK, KE>();
+    case CODE_ELAST_P2: return info_of<CODE_ELAST_P2, BLK, KE>();
+    case CODE_ELAST_P3: return info_of<CODE_ELAST_P3, BLK, KE>();
+    case CODE_POISSON_P1: return info_of<CODE_POISSON_P1, BLK, KE>();
+    case CODE_POISSON_P2: return info_of<CODE_POISSON_P2, BLK, KE>();
+    default: return info_of<CODE_MASS_P1, BLK, KE>();
   }
 }
 
 CodeInfo code_info_variant(int variant, int code) {
   switch (variant) {
-    case 0: return code_info<KE_VARIANTS[0]>(code);
-    case 1: return code_info<KE_VARIANTS[1]>(code);
-    default: return code_info<KE_VARIANTS[2]>(code);
+    case 0: return code_info<0>(code);
+    case 1: return code_info<1>(code);
+    case 2: return code_info<2>(code);
+    case 3: return code_info<3>(code);
+    case 4: return code_info<4>(code);
+    default: return code_info<5>(code);
   }
 }
 
@@ -145,10 +171,10 @@ struct ffc_batch {
   int zero_csr = 1;
   int variant = 1;
   int sms = 0;
-  int grid[3] = {0, 0, 0};
-  ffc::WorkItem* d_items[3] = {nullptr, nullptr, nullptr};
-  long long total_tiles[3] = {0, 0, 0};
-  size_t smem[3] = {0, 0, 0};
+  int grid[ffc::N_VARIANTS] = {};
+  ffc::WorkItem* d_items[ffc::N_VARIANTS] = {};
+  long long total_tiles[ffc::N_VARIANTS] = {};
+  size_t smem[ffc::N_VARIANTS] = {};
   unsigned long long* d_queue = nullptr;
   cudaGraphExec_t graph = nullptr;
   int graph_variant = -1;
@@ -177,7 +203,8 @@ int build_table(ffc_batch* b, int variant) {
     p.vertices = it.vertices;
     p.n_vert = it.n_vert;
     p.coeffs = it.coeffs;
-    p.a0 = ci.reg_a0 ? (const void*)b->tensors[k]->a0_f32 : (const void*)b->tensors[k]->a0t_f32;
+    p.a0 = ci.block ? (const void*)b->tensors[k]->r_f32
+                    : ci.reg_a0 ? (const void*)b->tensors[k]->a0_f32 : (const void*)b->tensors[k]->a0t_f32;
     p.out = nullptr;
     p.slot = it.slot;
     p.csr_val = it.csr_val;
@@ -199,9 +226,10 @@ int build_table(ffc_batch* b, int variant) {
   return FFC_OK;
 }
 
-template <int KE>
-int launch_variant(ffc_batch* b, int variant, cudaStream_t s) {
-  auto kern = batch_assemble_kernel<KE>;
+template <int V>
+int launch_variant(ffc_batch* b, cudaStream_t s) {
+  constexpr int variant = V, BLK = VARIANT_BLOCK[V], KE = VARIANT_KE[V];
+  auto kern = batch_assemble_kernel<BLK, KE>;
   static bool attr = false;
   if (!attr) {
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024) != cudaSuccess)
@@ -211,11 +239,11 @@ int launch_variant(ffc_batch* b, int variant, cudaStream_t s) {
   if (b->smem[variant] > 96 * 1024) return FFC_EUNSUPPORTED;
   if (b->grid[variant] == 0) {
     int per_sm = 1;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, BATCH_BLOCK, b->smem[variant]) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, BLK, b->smem[variant]) != cudaSuccess)
       return FFC_ECUDA;
     b->grid[variant] = b->sms * std::max(1, per_sm);
   }
-  kern<<<b->grid[variant], BATCH_BLOCK, b->smem[variant], s>>>(b->d_items[variant], int(b->items.size()),
+  kern<<<b->grid[variant], BLK, b->smem[variant], s>>>(b->d_items[variant], int(b->items.size()),
                                                                   b->total_tiles[variant], b->d_queue);
   const cudaError_t e = cudaPeekAtLastError();
   if (e != cudaSuccess) set_error(std::string("batch kernel launch: ") + cudaGetErrorString(e));
@@ -228,9 +256,12 @@ int enqueue(ffc_batch* b, int variant, cudaStream_t s) {
       if (cudaMemsetAsync(it.csr_val, 0, size_t(it.nnz) * sizeof(double), s) != cudaSuccess) return FFC_ECUDA;
   if (cudaMemsetAsync(b->d_queue, 0, sizeof(unsigned long long), s) != cudaSuccess) return FFC_ECUDA;
   switch (variant) {
-    case 0: return launch_variant<KE_VARIANTS[0]>(b, 0, s);
-    case 1: return launch_variant<KE_VARIANTS[1]>(b, 1, s);
-    default: return launch_variant<KE_VARIANTS[2]>(b, 2, s);
+    case 0: return launch_variant<0>(b, s);
+    case 1: return launch_variant<1>(b, s);
+    case 2: return launch_variant<2>(b, s);
+    case 3: return launch_variant<3>(b, s);
+    case 4: return launch_variant<4>(b, s);
+    default: return launch_variant<5>(b, s);
   }
 }
 
@@ -281,7 +312,7 @@ int ffc_batch_create(const ffc_batch_item* items, int n_items, int zero_csr, ffc
     delete b;
     return FFC_ENOMEM;
   }
-  for (int v = 0; v < 3; ++v) {
+  for (int v = 0; v < N_VARIANTS; ++v) {
     int rc = build_table(b, v);
     if (rc != FFC_OK) {
       ffc_batch_destroy(b);
@@ -292,14 +323,14 @@ int ffc_batch_create(const ffc_batch_item* items, int n_items, int zero_csr, ffc
   return FFC_OK;
 }
 
-int ffc_batch_tune(ffc_batch* b, void* stream, int* cells_per_tile_group) {
+int ffc_batch_tune(ffc_batch* b, void* stream, int* cells_per_tile_group, int* threads_per_block) {
   if (!b) return FFC_EINVAL;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return FFC_ECUDA;
   float best = 1e30f;
   int best_v = b->variant;
-  for (int v = 0; v < 3; ++v) {
+  for (int v = 0; v < N_VARIANTS; ++v) {
     int rc = enqueue(b, v, s);  // warm-up
     if (rc != FFC_OK) continue;
     cudaEventRecord(e0, s);
@@ -322,7 +353,8 @@ int ffc_batch_tune(ffc_batch* b, void* stream, int* cells_per_tile_group) {
   // leave the matrices zeroed: tuning accumulated into them
   for (const auto& it : b->items)
     if (cudaMemsetAsync(it.csr_val, 0, size_t(it.nnz) * sizeof(double), s) != cudaSuccess) return FFC_ECUDA;
-  if (cells_per_tile_group) *cells_per_tile_group = KE_VARIANTS[b->variant];
+  if (cells_per_tile_group) *cells_per_tile_group = VARIANT_KE[b->variant];
+  if (threads_per_block) *threads_per_block = VARIANT_BLOCK[b->variant];
   return cudaStreamSynchronize(s) == cudaSuccess ? FFC_OK : FFC_ECUDA;
 }
 
@@ -366,11 +398,13 @@ int ffc_batch_run(ffc_batch* b, int use_graph, void* stream) {
   return e == cudaSuccess ? FFC_OK : FFC_ECUDA;
 }
 
-int ffc_batch_info(const ffc_batch* b, int* n_items, long long* total_tiles, int* cells_per_tile_group) {
+int ffc_batch_info(const ffc_batch* b, int* n_items, long long* total_tiles, int* cells_per_tile_group,
+                   int* threads_per_block) {
   if (!b) return FFC_EINVAL;
   if (n_items) *n_items = int(b->items.size());
   if (total_tiles) *total_tiles = b->total_tiles[b->variant];
-  if (cells_per_tile_group) *cells_per_tile_group = KE_VARIANTS[b->variant];
+  if (cells_per_tile_group) *cells_per_tile_group = VARIANT_KE[b->variant];
+  if (threads_per_block) *threads_per_block = VARIANT_BLOCK[b->variant];
   return FFC_OK;
 }
 
