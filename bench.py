@@ -193,6 +193,7 @@ def alg_bytes_tabulate(ctx, n_local, out_bytes):
 # `ncu --set full` capture of these kernels at 24^3 x 6 = 82,944 cells scaled by the cell
 # count (x8; slots, CSR values and cells all grow with it). Only valid for the FP32 SIMT
 # assembly kernels as captured; other kernels report null.
+FP64_NOMINAL_TFLOPS = 1.25  # GB300 FP64 (CUDA cores), nominal
 CAPTURED_TRAFFIC_GB = {("mass", 4, "fp32"): 1.597 * 8, ("poisson", 4, "fp32"): 1.479 * 8}
 
 
@@ -413,7 +414,8 @@ def main():
                          "traffic_unit": "GB per launch (ncu, scaled from 82,944 cells)",
                          "algorithmic_gb": alg_bytes_assemble(ctx, dpr) / 1e9,
                          "kernel": f"assemble {FORM_NAME[dpr['form']]} P{dpr['q']} ({args.precision})",
-                         "launch_ms": per_launch[dom] * 1e3},
+                         "launch_ms": per_launch[dom] * 1e3,
+                         "fp64_atomics_per_s": n_elem * dpr["n_local"] ** 2 / per_launch[dom]},
             "per_launch_ms": {f"{FORM_NAME[p['form']]}_p{p['q']}": round(per_launch[k] * 1e3, 4)
                               for k, p in enumerate(ctx["problems"])},
             "clocks": clk, "gpu_launches": P * args.steps, "e2e": e2e, "cpu_baseline": cpu, "detail": detail,
@@ -679,7 +681,9 @@ def run_other(args):
         clk = clocks.stop()
         assert F.status_poll() == 0
         byts = m.n_elem * (16 + 800 + 12 * 8) + m.n_vert * 24 * 2
-        flops = m.n_elem * (2 * 100 * 9 + 300)
+        # executed FP64 flops per cell: 6 symmetric combinations x 100 entries (FMA = 2),
+        # plus about 240 for J^{-1}, det J and the chain rule
+        flops = m.n_elem * (2 * 100 * 6 + 240)
         cpu_rate, S = None, 0
         if not args.no_cpu_baseline:
             import multiprocessing as mp
@@ -695,8 +699,9 @@ def run_other(args):
         out.update({"metric": "element adjoints/s (P2 Poisson dL/dvertices, 56^3x6 tets)",
                     "value": m.n_elem / t, "ms_per_step": t * 1e3, "dtype": "f64",
                     "config": {"workload": "adjoint_p2", "cells": m.n_elem, "vertices": m.n_vert},
-                    "roofline": {"bound": "alu", "achieved": flops / t / 1e12, "peak": None, "unit": "TFLOP/s",
-                                 "frac": None, "traffic": None,
+                    "roofline": {"bound": "alu", "achieved": flops / t / 1e12, "peak": FP64_NOMINAL_TFLOPS,
+                                 "unit": "TFLOP/s", "frac": flops / t / 1e12 / FP64_NOMINAL_TFLOPS,
+                                 "peak_kind": "nominal GB300 FP64", "traffic": None,
                                  "hbm_gbs": byts / t / 1e9, "hbm_frac": byts / t / 1e9 / hbm_peak,
                                  "kernel": "poisson_adjoint_kernel<3,2>"},
                     "clocks": clk, "gpu_launches": args.steps,

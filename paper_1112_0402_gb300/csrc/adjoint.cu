@@ -10,10 +10,11 @@
 // x_{c+1} - x_0, so dL/dx_{c+1} += dL/dJ[:, c] and dL/dx_0 -= sum_c dL/dJ[:, c]; the
 // vertex gradients are accumulated with FP64 atomic adds.
 //
-// A warp takes 32 cells: for each, the lanes stride over the n^2 entries (coalesced
-// reads of dA) keeping |alpha| = d^2 partial sums against the transposed reference
-// tensor held in shared memory, and reduce them with warp shuffles; lane k keeps cell
-// k's Gbar. Then all 32 lanes run the geometry chain rule, one cell each. FP64.
+// One thread per cell. Only the symmetric part of Gbar enters (c = Gbar : K K^T with
+// K K^T symmetric, and Gbar + Gbar^T), so each thread accumulates the d(d+1)/2
+// combinations against the correspondingly combined reference tensor, held in shared
+// memory and read as a broadcast (all lanes at the same entry i); no cross-lane
+// reductions. Then it runs the geometry chain rule and scatters with atomics. FP64.
 #include <cuda_runtime.h>
 
 #include "ffc_internal.h"
@@ -22,110 +23,114 @@
 namespace ffc {
 namespace {
 
-constexpr int WARPS = 8;
+constexpr int THREADS = 256;
+
+// Index of the symmetric pair (a, b), a <= b: diagonal pairs first, then a < b.
+template <int D>
+__host__ __device__ constexpr int sym_index(int a, int b) {
+  return a == b ? a : (D == 2 ? 2 : (a == 0 ? (b == 1 ? 3 : 4) : 5));
+}
 
 template <int D, int Q>
-__global__ void __launch_bounds__(WARPS * 32) poisson_adjoint_kernel(const int32_t* __restrict__ cells,
-                                                                     const double* __restrict__ vertices,
-                                                                     long long n_vert, const double* __restrict__ a0t,
-                                                                     const double* __restrict__ dA, double* dvert,
-                                                                     long long n_elem, unsigned* status) {
+__global__ void __launch_bounds__(THREADS) poisson_adjoint_kernel(const int32_t* __restrict__ cells,
+                                                                 const double* __restrict__ vertices,
+                                                                 long long n_vert, const double* __restrict__ a0t,
+                                                                 const double* __restrict__ dA, double* dvert,
+                                                                 long long n_elem, unsigned* status) {
   constexpr int N = nscalar(D, Q);
   constexpr int NN = N * N;
-  constexpr int NA = D * D;
-  extern __shared__ double a0s[];  // [NA][NN]
-  for (int k = threadIdx.x; k < NA * NN; k += blockDim.x) a0s[k] = a0t[k];
+  constexpr int NP = D * (D + 1) / 2;
+  // symmetric combinations of the reference tensor, one row per entry i:
+  // P[i][aa] = A0[i][(a,a)], P[i][ab] = A0[i][(a,b)] + A0[i][(b,a)] (a < b)
+  extern __shared__ double a0s[];  // [NN][NP]
+  for (int k = threadIdx.x; k < NN * NP; k += blockDim.x) {
+    const int i = k / NP, pidx = k % NP;
+    int a = 0, b = 0;
+#pragma unroll
+    for (int x = 0; x < D; ++x)
+#pragma unroll
+      for (int y = x; y < D; ++y)
+        if (sym_index<D>(x, y) == pidx) {
+          a = x;
+          b = y;
+        }
+    a0s[k] = (a == b) ? a0t[(a * D + a) * NN + i] : a0t[(a * D + b) * NN + i] + a0t[(b * D + a) * NN + i];
+  }
   __syncthreads();
-  const int lane = threadIdx.x & 31;
-  const long long warp_global = (long long)blockIdx.x * WARPS + (threadIdx.x >> 5);
-  const long long n_warps = (long long)gridDim.x * WARPS;
-  // each warp takes 32 consecutive cells: the lanes reduce Gbar for one cell at a
-  // time (lane k keeps cell k's sums), then every lane runs the chain rule of its cell
-  for (long long base = warp_global * 32; base < n_elem; base += n_warps * 32) {
-    double mine[NA];
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n_elem;
+       e += (long long)gridDim.x * blockDim.x) {
+    // gp[aa] = Gbar[a][a], gp[ab] = Gbar[a][b] + Gbar[b][a]
+    double gp[NP];
 #pragma unroll
-    for (int a = 0; a < NA; ++a) mine[a] = 0.0;
-    const int count = (n_elem - base) < 32 ? int(n_elem - base) : 32;
-#pragma unroll 1
-    for (int k = 0; k < count; ++k) {
-      double gb[NA];
+    for (int k = 0; k < NP; ++k) gp[k] = 0.0;
+    const double* row = dA + e * NN;
+#pragma unroll 4
+    for (int i = 0; i < NN; ++i) {
+      const double g = __ldg(row + i);
 #pragma unroll
-      for (int a = 0; a < NA; ++a) gb[a] = 0.0;
-      const double* row = dA + (base + k) * NN;
-      for (int i = lane; i < NN; i += 32) {
-        const double g = __ldg(row + i);
-#pragma unroll
-        for (int a = 0; a < NA; ++a) gb[a] = fma(a0s[a * NN + i], g, gb[a]);
-      }
-#pragma unroll
-      for (int a = 0; a < NA; ++a) {
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) gb[a] += __shfl_xor_sync(0xffffffffu, gb[a], off);
-        if (lane == k) mine[a] = gb[a];
-      }
+      for (int k = 0; k < NP; ++k) gp[k] = fma(a0s[i * NP + k], g, gp[k]);
     }
-    if (lane < count) {
-      const long long e = base + lane;
-      double gb[NA];
+    double K[D][D], s;
+    bool degenerate, bad_index;
+    cell_geometry<D>(cells, vertices, n_vert, e, K, s, degenerate, bad_index);
+    if (degenerate) atomicOr(status, FFC_FLAG_DEGENERATE);
+    if (bad_index) {
+      atomicOr(status, FFC_FLAG_BOUNDS);
+      continue;
+    }
+    double M[D][D];  // K K^T
 #pragma unroll
-      for (int a = 0; a < NA; ++a) gb[a] = mine[a];
-      double K[D][D], s;
-      bool degenerate, bad_index;
-      cell_geometry<D>(cells, vertices, n_vert, e, K, s, degenerate, bad_index);
-      if (degenerate) atomicOr(status, FFC_FLAG_DEGENERATE);
-      if (bad_index) atomicOr(status, FFC_FLAG_BOUNDS);
-      double M[D][D];  // K K^T
+    for (int a = 0; a < D; ++a)
 #pragma unroll
-      for (int a = 0; a < D; ++a)
+      for (int b = 0; b < D; ++b) {
+        double t = 0.0;
 #pragma unroll
-        for (int b = 0; b < D; ++b) {
-          double t = 0.0;
-#pragma unroll
-          for (int k = 0; k < D; ++k) t += K[a][k] * K[b][k];
-          M[a][b] = t;
-        }
-      double c = 0.0, S[D][D];
-#pragma unroll
-      for (int a = 0; a < D; ++a)
-#pragma unroll
-        for (int b = 0; b < D; ++b) {
-          c += gb[a * D + b] * M[a][b];
-          S[a][b] = gb[a * D + b] + gb[b * D + a];
-        }
-      // T = S M ; dJ = s (c K^T - K^T T)
-      double T[D][D];
-#pragma unroll
-      for (int a = 0; a < D; ++a)
-#pragma unroll
-        for (int b = 0; b < D; ++b) {
-          double t = 0.0;
-#pragma unroll
-          for (int k = 0; k < D; ++k) t += S[a][k] * M[k][b];
-          T[a][b] = t;
-        }
-      double dJ[D][D];
-#pragma unroll
-      for (int r = 0; r < D; ++r)
-#pragma unroll
-        for (int col = 0; col < D; ++col) {
-          double t = 0.0;
-#pragma unroll
-          for (int k = 0; k < D; ++k) t += K[k][r] * T[k][col];
-          dJ[r][col] = s * (c * K[col][r] - t);
-        }
-      int id[D + 1];
-#pragma unroll
-      for (int j = 0; j <= D; ++j) id[j] = __ldg(cells + e * (D + 1) + j);
-#pragma unroll
-      for (int r = 0; r < D && !bad_index; ++r) {
-        double sum = 0.0;
-#pragma unroll
-        for (int col = 0; col < D; ++col) {
-          atomicAdd(dvert + (long long)id[col + 1] * D + r, dJ[r][col]);
-          sum += dJ[r][col];
-        }
-        atomicAdd(dvert + (long long)id[0] * D + r, -sum);
+        for (int k = 0; k < D; ++k) t += K[a][k] * K[b][k];
+        M[a][b] = t;
       }
+    // S = Gbar + Gbar^T, c = Gbar : M (M symmetric)
+    double S[D][D], c = 0.0;
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+#pragma unroll
+      for (int b = 0; b < D; ++b) {
+        const double v = gp[sym_index<D>(a < b ? a : b, a < b ? b : a)];
+        S[a][b] = (a == b) ? 2.0 * v : v;
+        if (a <= b) c += v * M[a][b];
+      }
+    // T = S M ; dJ = s (c K^T - K^T T)
+    double T[D][D];
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+#pragma unroll
+      for (int b = 0; b < D; ++b) {
+        double t = 0.0;
+#pragma unroll
+        for (int k = 0; k < D; ++k) t += S[a][k] * M[k][b];
+        T[a][b] = t;
+      }
+    double dJ[D][D];
+#pragma unroll
+    for (int r = 0; r < D; ++r)
+#pragma unroll
+      for (int col = 0; col < D; ++col) {
+        double t = 0.0;
+#pragma unroll
+        for (int k = 0; k < D; ++k) t += K[k][r] * T[k][col];
+        dJ[r][col] = s * (c * K[col][r] - t);
+      }
+    int id[D + 1];
+#pragma unroll
+    for (int j = 0; j <= D; ++j) id[j] = __ldg(cells + e * (D + 1) + j);
+#pragma unroll
+    for (int r = 0; r < D; ++r) {
+      double sum = 0.0;
+#pragma unroll
+      for (int col = 0; col < D; ++col) {
+        atomicAdd(dvert + (long long)id[col + 1] * D + r, dJ[r][col]);
+        sum += dJ[r][col];
+      }
+      atomicAdd(dvert + (long long)id[0] * D + r, -sum);
     }
   }
 }
@@ -133,7 +138,7 @@ __global__ void __launch_bounds__(WARPS * 32) poisson_adjoint_kernel(const int32
 template <int D, int Q>
 int run(const LaunchArgs& a, const double* dA, double* dvert) {
   constexpr int N = nscalar(D, Q);
-  constexpr size_t SMEM = size_t(D * D) * N * N * sizeof(double);
+  constexpr size_t SMEM = size_t(D * (D + 1) / 2) * N * N * sizeof(double);
   auto kern = poisson_adjoint_kernel<D, Q>;
   static int sms = 0, per_sm = 1;
   if (sms == 0) {
@@ -143,14 +148,14 @@ int run(const LaunchArgs& a, const double* dA, double* dvert) {
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, WARPS * 32, SMEM) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, THREADS, SMEM) != cudaSuccess)
       return FFC_ECUDA;
     if (per_sm < 1) per_sm = 1;
   }
   long long grid = (long long)sms * per_sm;
-  const long long need = (a.n_elem + 32 * WARPS - 1) / (32 * WARPS);
+  const long long need = (a.n_elem + THREADS - 1) / THREADS;
   if (grid > need) grid = need;
-  kern<<<unsigned(grid), WARPS * 32, SMEM, static_cast<cudaStream_t>(a.stream)>>>(
+  kern<<<unsigned(grid), THREADS, SMEM, static_cast<cudaStream_t>(a.stream)>>>(
       a.cells, a.vertices, a.n_vert, a.t->a0t_f64, dA, dvert, a.n_elem, a.status);
   return cudaPeekAtLastError() == cudaSuccess ? FFC_OK : FFC_ECUDA;
 }

@@ -167,12 +167,34 @@ __device__ __forceinline__ void block_tile(const SimtParams& p, long long tile, 
       for (int k = C::KR; k < C::KRP; ++k) g[b * C::KRP + k] = T(0);
   }
   __syncthreads();
-  // ---- contraction per owned entry (thread groups beyond EG idle)
+  // ---- contraction per owned entry (thread groups beyond EG idle); in assembly the
+  // slots of the next cell are loaded while this cell's atomics issue
+  int slot_next[ASSEMBLE ? C::R : 1];
+  if constexpr (ASSEMBLE) {
+    const long long e = e0 + eg;
+#pragma unroll
+    for (int r = 0; r < C::R; ++r) {
+      const int i = ti + r * C::NTI;
+      slot_next[r] = (eg < C::EG && e < p.n_elem && i < C::NN && br.boff[r] >= 0) ? __ldg(p.slot + e * C::NN + i)
+                                                                                  : -1;
+    }
+  }
 #pragma unroll 1
   for (int kc = 0; kc < C::KE && eg < C::EG; ++kc) {
     const int el = eg + kc * C::EG;
     const long long e = e0 + el;
     if (e >= p.n_elem) break;
+    int slot_cur[ASSEMBLE ? C::R : 1];
+    if constexpr (ASSEMBLE) {
+      const long long en = e + C::EG;
+      const bool more = (kc + 1 < C::KE) && (en < p.n_elem);
+#pragma unroll
+      for (int r = 0; r < C::R; ++r) {
+        const int i = ti + r * C::NTI;
+        slot_cur[r] = slot_next[r];
+        slot_next[r] = (more && i < C::NN && br.boff[r] >= 0) ? __ldg(p.slot + en * C::NN + i) : -1;
+      }
+    }
     const T* g = Gs + size_t(el) * C::NB * C::KRP;
 #pragma unroll
     for (int r = 0; r < C::R; ++r) {
@@ -193,7 +215,7 @@ __device__ __forceinline__ void block_tile(const SimtParams& p, long long tile, 
       const long long o = e * C::NN + i;
       if constexpr (ASSEMBLE) {
         if (br.boff[r] >= 0) {  // structural zeros add nothing
-          const int s = __ldg(p.slot + o);
+          const int s = slot_cur[r];
           if (s >= 0 && s < p.nnz) atomicAdd(p.csr_val + s, double(acc));
           else atomicOr(p.status, FFC_FLAG_BOUNDS);
         }
