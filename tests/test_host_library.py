@@ -170,3 +170,24 @@ def test_csr_pattern_rejects_out_of_range_dofs():
     with pytest.raises(F.FFCError) as e:
         F.csr_pattern(dm, 5)
     assert e.value.code == -6
+
+
+def test_algorithm_and_batch_arguments_are_validated_on_the_host():
+    import ctypes
+
+    import paper_1112_0402_gb300 as F
+    from paper_1112_0402_gb300 import _capi
+
+    L = _lib()
+    f = F.Form(F.ELASTICITY, F.TETRAHEDRON, 2, algorithm=F.ALG_BLOCK)
+    assert L.ffc_form_set_algorithm(f.handle, 7) == -1
+    assert L.ffc_form_set_algorithm(None, 0) == -1
+    items = (_capi.BatchItem * 1)()
+    items[0].form = f.handle
+    items[0].n_elem = 10  # null device pointers: rejected before any device work
+    out = ctypes.c_void_p()
+    assert L.ffc_batch_create(items, 1, 1, ctypes.byref(out)) == -1
+    g = F.Form(F.POISSON, F.TETRAHEDRON, 4)  # a form the batched kernel does not carry
+    items[0].form = g.handle
+    assert L.ffc_batch_create(items, 1, 1, ctypes.byref(out)) == -5
+    assert L.ffc_batch_create(None, 0, 1, ctypes.byref(out)) == -1
