@@ -62,3 +62,10 @@ def csr_matvec(row_ptr: np.ndarray, col: np.ndarray, val: np.ndarray, x: np.ndar
     y = np.zeros(row_ptr.size - 1)
     np.add.at(y, rows, val * x[col])
     return y
+
+
+def assemble_vector(b_K: np.ndarray, dofmap: np.ndarray, n_dof: int) -> np.ndarray:
+    """Algorithm 2 for a linear form: b[iota(K,i)] += b^K[i]."""
+    b = np.zeros(n_dof)
+    np.add.at(b, dofmap.reshape(-1), np.asarray(b_K, dtype=np.float64).reshape(-1))
+    return b

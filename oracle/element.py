@@ -9,6 +9,8 @@ integrands of the four test cases of Section 3.3:
   elasticity  2 mu eps(phi_i1) : eps(phi_i2) + lambda div phi_i1 div phi_i2
               (Section 3.3 writes the eps:eps term; the lambda term and the 2 mu
               scaling are the standard isotropic form with mu = 1, lambda = 1.25)
+  source      the linear form v * f, f = sum_t f_t phi_t (L = v*f*dx of the Poisson
+              example in Section 5.5): a rank-1 element tensor b^K_i = int phi_i f
 
 Row index i1 is the test function v, column index i2 the trial function u.
 Vector spaces use component-blocked local numbering i = c*n_s + s with
@@ -27,11 +29,11 @@ import numpy as np
 
 from . import basis, quadrature
 
-MASS, POISSON, NS_CONVECTION, ELASTICITY = 0, 1, 2, 3
+MASS, POISSON, NS_CONVECTION, ELASTICITY, SOURCE = 0, 1, 2, 3, 4
 
 
 def integrand_degree(form: int, q: int) -> int:
-    if form == MASS:
+    if form in (MASS, SOURCE):
         return 2 * q
     if form in (POISSON, ELASTICITY):
         return max(0, 2 * q - 2)
@@ -75,14 +77,15 @@ def _vectorise(d: int, phi: np.ndarray, grad: np.ndarray | None):
 def element_tensors(form: int, verts: np.ndarray, q: int, coeffs: np.ndarray | None = None,
                     mu: float = 1.0, lmbda: float = 1.25, extra_points: int = 0,
                     chunk: int | None = None) -> np.ndarray:
-    """Element tensors [E, n, n] in float64 for cells verts [E, d+1, d]."""
+    """Element tensors [E, n, n] (bilinear forms) or [E, n] (the source form) in float64
+    for cells verts [E, d+1, d]."""
     verts = np.asarray(verts, dtype=np.float64)
     E, dp1, d = verts.shape
     p = integrand_degree(form, q)
     w, phi, dphi = _scalar_tables(d, q, p, extra_points)
     ns = phi.shape[1]
-    n = ns if form in (MASS, POISSON) else d * ns
-    out = np.empty((E, n, n))
+    n = ns if form in (MASS, POISSON, SOURCE) else d * ns
+    out = np.empty((E, n)) if form == SOURCE else np.empty((E, n, n))
     if chunk is None:
         per_elem = w.size * n * d * d * 8 * 4
         chunk = max(1, min(E, int(64e6 // max(per_elem, 1))))
@@ -92,6 +95,10 @@ def element_tensors(form: int, verts: np.ndarray, q: int, coeffs: np.ndarray | N
         if form == MASS:
             local = np.einsum("q,qi,qj->ij", w, phi, phi, optimize=True)
             out[s:s + chunk] = vol[:, None, None] * local[None]
+            continue
+        if form == SOURCE:
+            f = np.einsum("et,qt->eq", np.asarray(coeffs[s:s + chunk], dtype=np.float64), phi, optimize=True)
+            out[s:s + chunk] = vol[:, None] * np.einsum("q,qi,eq->ei", w, phi, f, optimize=True)
             continue
         grad = np.einsum("qij,ejb->eqib", dphi, grad_lam)  # [e, q, ns, d]
         if form == POISSON:

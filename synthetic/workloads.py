@@ -25,8 +25,9 @@ import numpy as np
 from .dofmap import scalar_dofmap, vector_dofmap
 from .mesh import SimplexMesh, unit_cube_tets, unit_square_triangles
 
-MASS, POISSON, NS_CONVECTION, ELASTICITY = 0, 1, 2, 3
-FORM_NAMES = {MASS: "mass", POISSON: "poisson", NS_CONVECTION: "ns_convection", ELASTICITY: "elasticity"}
+MASS, POISSON, NS_CONVECTION, ELASTICITY, SOURCE = 0, 1, 2, 3, 4
+FORM_NAMES = {MASS: "mass", POISSON: "poisson", NS_CONVECTION: "ns_convection", ELASTICITY: "elasticity",
+              SOURCE: "source"}
 ELASTICITY_MU = 1.0
 ELASTICITY_LAMBDA = 1.25
 
@@ -65,7 +66,7 @@ def make_problem(mesh: SimplexMesh, form: int, degree: int, seed: int = 0) -> Fo
         dm, nd = sdm, nds
     coeffs = None
     extra = {}
-    if form == NS_CONVECTION:
+    if form in (NS_CONVECTION, SOURCE):
         rng = np.random.default_rng([seed, 101])
         w = rng.standard_normal(nd)
         coeffs = np.ascontiguousarray(w[dm])

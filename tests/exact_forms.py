@@ -185,6 +185,17 @@ def element_tensor(form: int, verts, q: int, w=None, mu=Fraction(1), lmbda=Fract
     raise ValueError(form)
 
 
+def load_vector(verts, q: int, f):
+    """Exact b^K_i = int_K psi_i f with f = sum_t f_t psi_t (rational vertices and f_t)."""
+    d = len(verts) - 1
+    _, _, det = _affine(verts)
+    psi = _basis(d, q)
+    fp = {}
+    for t, ft in enumerate(f):
+        fp = padd(fp, psi[t], Fraction(ft))
+    return [det * pint(pmul(p, fp)) for p in psi]
+
+
 def reference_tensor_poisson(d: int, q: int):
     """A0[i1][i2][a1][a2] = int_{K0} d_a1 Psi_i1 d_a2 Psi_i2 dX, exact."""
     psi = _basis(d, q)

@@ -4,7 +4,7 @@ import numpy as np
 import pytest
 
 from oracle import assemble, element, shape
-from oracle.element import ELASTICITY, MASS, NS_CONVECTION, POISSON
+from oracle.element import ELASTICITY, MASS, NS_CONVECTION, POISSON, SOURCE
 from synthetic import mesh as M
 from synthetic import workloads as W
 
@@ -120,3 +120,25 @@ def test_shape_gradient_matches_central_differences(q):
             assert abs(fd - grad[k, c]) < 1e-6 * max(1.0, abs(grad).max())
     # translation invariance: the gradient sums to zero over all vertices
     assert np.abs(grad.sum(axis=0)).max() < 1e-10 * np.abs(grad).max()
+
+
+@pytest.mark.parametrize("d,n,q", [(2, 4, 1), (2, 3, 2), (3, 2, 1), (3, 2, 2), (3, 1, 3), (3, 1, 4)])
+def test_global_load_vector_reproduces_polynomial_integrals(d, n, q):
+    # b_i = int psi_i f; with f interpolated exactly (degree <= q), b . 1 = int f and
+    # b . X = int x f for the nodal vector X of a linear x (q >= 1 reproduces it)
+    p = _problem(d, n, SOURCE, q)
+    for f, x_f in ((lambda x: 1.0 + 0 * x[..., 0], 1 / 2),
+                   (lambda x: x[..., 0], 1 / 3)):
+        p.coeffs = np.ascontiguousarray(_nodal(p, f)[p.dofmap])
+        b = assemble.assemble_vector(_tensors(p), p.dofmap, p.n_dof)
+        assert abs(b.sum() - (1.0 if x_f == 1 / 2 else 1 / 2)) < 1e-13
+        X = _nodal(p, lambda x: x[..., 0])
+        assert abs(b @ X - x_f) < 1e-13
+    # loop form of Algorithm 2 for a vector
+    ref = np.zeros(p.n_dof)
+    bK = _tensors(p)
+    for e in range(p.n_elem):
+        for i in range(p.n_local):
+            ref[p.dofmap[e, i]] += bK[e, i]
+    assert np.array_equal(assemble.assemble_vector(bK, p.dofmap, p.n_dof), ref) or \
+        np.abs(assemble.assemble_vector(bK, p.dofmap, p.n_dof) - ref).max() < 1e-15

@@ -272,3 +272,28 @@ def test_negative_orientation_uses_absolute_determinant():
         B = element.element_tensors(form, vf, q)
         perm = [basis.lattice(3, q).index(tuple(k[[0, 2, 1, 3]])) for k in np.array(basis.lattice(3, q))]
         assert np.allclose(B, A[:, perm][:, :, perm], rtol=1e-13, atol=1e-15)
+
+
+# ---------------------------------------------------------------- linear form (source)
+@pytest.mark.parametrize("q", [1, 2, 3])
+@pytest.mark.parametrize("t", range(len(RATIONAL_TETS)))
+def test_source_vector_vs_exact_rational(q, t):
+    verts = [tuple(Fraction(c) for c in v) for v in RATIONAL_TETS[t]]
+    n = n_local(3, q)
+    f = [Fraction((5 * i) % 9 - 4, 7) for i in range(n)]
+    ref = np.array(X.load_vector(verts, q, f), dtype=float)
+    vf = np.array([[float(c) for c in v] for v in verts])[None]
+    b = element.element_tensors(element.SOURCE, vf, q, coeffs=np.array([[float(x) for x in f]]))[0]
+    assert np.abs(b - ref).max() <= 1e-14 * np.abs(ref).max()
+
+
+def test_source_vector_closed_forms():
+    v = random_simplices(3, 10)
+    vol = np.abs(np.einsum("ei,ei->e", v[:, 1] - v[:, 0], np.cross(v[:, 2] - v[:, 0], v[:, 3] - v[:, 0]))) / 6
+    b = element.element_tensors(element.SOURCE, v, 1, coeffs=np.ones((10, 4)))
+    assert np.allclose(b, vol[:, None] / 4, rtol=1e-14)  # int lambda_i = |K| / (d+1)
+    rng = np.random.default_rng(2)
+    f = rng.standard_normal((10, 20))
+    b = element.element_tensors(element.SOURCE, v, 3, coeffs=f)
+    M = element.element_tensors(MASS, v, 3)
+    assert np.allclose(b, np.einsum("eij,ej->ei", M, f), rtol=1e-12, atol=1e-15)  # b = M f
