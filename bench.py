@@ -50,7 +50,7 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["tet_scalar", "ns_vp2", "batched", "adjoint"], default="tet_scalar",
+    ap.add_argument("--workload", choices=["tet_scalar", "ns_vp2", "batched", "adjoint", "source"], default="tet_scalar",
                     help="tet_scalar is the headline; the others print their own line")
     ap.add_argument("--precision", default="fp32", help="contraction arithmetic of the headline step")
     ap.add_argument("--n", type=int, default=48, help="hexes per axis")
@@ -663,6 +663,68 @@ def run_other(args):
                     "clocks": clk, "gpu_launches": args.steps,
                     "detail": {"plain_launch_ms": t_plain * 1e3, "separate_launches_ms": t_sep * 1e3,
                                "elasticity_p3_tabulate": elast}})
+    elif args.workload == "source":
+        # the linear form L = v f dx (P4, 48^3 x 6 tets) assembled into a global vector
+        m = W.tet_scalar_mesh(args.n)
+        p = W.make_problem(m, W.SOURCE, 4, seed=2)
+        n = p.n_local
+        cells = torch.as_tensor(m.cells, device=device)
+        verts = torch.as_tensor(m.vertices, device=device)
+        coeffs = torch.as_tensor(p.coeffs, device=device)
+        dm = torch.as_tensor(p.dofmap, device=device)
+        fm = F.Form(F.SOURCE, F.TETRAHEDRON, 4)
+        b = torch.zeros(p.n_dof, dtype=torch.float64, device=device)
+
+        def step(prec):
+            b.zero_()
+            F.assemble(fm, cells, verts, dm, b, coeffs=coeffs, precision=prec)
+
+        detail = {}
+        for prec in ("fp64", "fp32"):
+            dt = torch.float64 if prec == "fp64" else torch.float32
+            A = torch.empty((m.n_elem, n), dtype=dt, device=device)
+            detail["tabulate_" + prec + "_ms"] = _timed(
+                lambda: F.tabulate(fm, cells, verts, coeffs=coeffs, out=A, precision=prec), args.steps,
+                args.warmup) * 1e3
+            del A
+        detail["assemble_fp64_ms"] = _timed(lambda: step("fp64"), args.steps, args.warmup) * 1e3
+        # the assembly kernel alone, on the launching stream (the zeroing is a separate launch)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * args.steps)]
+        for _ in range(args.warmup):
+            step("fp32")
+        torch.cuda.synchronize()
+        clocks.start()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record()
+        for k in range(args.steps):
+            b.zero_()
+            ev[2 * k].record()
+            F.assemble(fm, cells, verts, dm, b, coeffs=coeffs, precision="fp32")
+            ev[2 * k + 1].record()
+        t1.record()
+        torch.cuda.synchronize()
+        clk = clocks.stop()
+        assert F.status_poll() == 0
+        t = t0.elapsed_time(t1) / 1e3 / args.steps
+        t_k = sum(ev[2 * k].elapsed_time(ev[2 * k + 1]) for k in range(args.steps)) / 1e3 / args.steps
+        # algorithmic bytes of one assembly: cells, vertices, f on each cell, dof map, and
+        # the global vector read and written once
+        byts = m.n_elem * (16 + 8 * n + 4 * n) + m.n_vert * 24 + 16 * p.n_dof
+        detail["fp64_flops_per_s"] = 2.0 * n * n * m.n_elem / (detail["assemble_fp64_ms"] / 1e3)
+        rate, S = (None, 0) if args.no_cpu_baseline else _oracle_rate(W.SOURCE, 4, M.gather_cell_vertices(m),
+                                                                       p.coeffs, cores)
+        out.update({"metric": "element vectors/s (source form P4, 48^3x6 tets, zero + assemble into b)",
+                    "value": m.n_elem / t, "ms_per_step": t * 1e3, "dtype": "f32",
+                    "config": {"workload": "source_p4", "cells": m.n_elem, "n_dof": p.n_dof,
+                               "l2": "inputs 0.29 GB per step > L2"},
+                    "roofline": {"bound": "hbm", "achieved": byts / t_k / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                                 "frac": byts / t_k / 1e9 / hbm_peak, "traffic": None, "peak_kind": peak_kind,
+                                 "kernel": "simt_tabulate_kernel<3,SOURCE,4,float,assemble>",
+                                 "kernel_ms": t_k * 1e3},
+                    "clocks": clk, "gpu_launches": 2 * args.steps,
+                    "cpu_baseline": {"value": rate, "unit": "elem/s", "cores": cores, "kind": "oracle",
+                                     "sample": f"{S} cells"}, "detail": detail})
     else:  # adjoint
         p, u, v = W.adjoint_p2(56 if args.n == 48 else args.n)
         m = p.mesh

@@ -1,11 +1,11 @@
 /*
  * ffc_gb300.h -- C ABI of the GB300 (sm_103a) tensor-representation library.
  *
- * The library evaluates element tensors of bilinear variational forms on affine
- * simplices by the tensor representation A^K_i = A0_{i alpha} G_K^alpha
+ * The library evaluates element tensors of bilinear (and linear) variational forms
+ * on affine simplices by the tensor representation A^K_i = A0_{i alpha} G_K^alpha
  * (Kirby & Logg, "A Compiler for Variational Forms", Section 3.2, eq.
- * (tensorproduct)) and adds them into a global CSR matrix through the
- * local-to-global dof map (Section 2.2, Algorithm 2).
+ * (tensorproduct)) and adds them into a global CSR matrix (or, for a linear form,
+ * a global vector) through the local-to-global dof map (Section 2.2, Algorithm 2).
  *
  * Conventions shared by every entry point
  *  - Return value: FFC_OK (0) or a negative ffc_status. Argument checks happen
@@ -21,7 +21,8 @@
  *    multi-index (vertices, then edges 01,02,03,12,13,23, faces, interior).
  *    Vector spaces are component blocked: i = c*n_scalar + s.
  *  - Element tensor layout: A_K[e][i1][i2], i1 = test (row), i2 = trial (column),
- *    the dense row-major block of Section 5.5 ("block[]").
+ *    the dense row-major block of Section 5.5 ("block[]"). A linear form (rank 1)
+ *    has A_K[e][i], i = test index: every "n*n" below reads "n" for it.
  *  - Geometry: J = [x_1 - x_0, ..., x_d - x_0] from the cell's vertices in the
  *    given order; G_K uses |det J| (negatively oriented cells are allowed).
  *  - Device-side problems (a degenerate cell, a CSR slot out of range) do not
@@ -51,12 +52,15 @@ typedef enum {
   FFC_ETIMEOUT = -7       /* status word: a bounded device wait gave up */
 } ffc_status;
 
-/* Forms of Section 3.3 of the paper. */
+/* Forms of Section 3.3 of the paper, and the linear form L(v) = int v f dx of
+ * Section 2.1 (the right-hand side of the Poisson specification in Section 5.5). */
 typedef enum {
   FFC_MASS = 0,           /* int v u dx                         (test case 1) */
   FFC_POISSON = 1,        /* int grad v . grad u dx             (test case 2) */
   FFC_NS_CONVECTION = 2,  /* int v . (w . grad) u dx, w given   (test case 3) */
-  FFC_ELASTICITY = 3      /* int 2 mu eps(v):eps(u) + lambda div v div u dx (test case 4) */
+  FFC_ELASTICITY = 3,     /* int 2 mu eps(v):eps(u) + lambda div v div u dx (test case 4) */
+  FFC_SOURCE = 4          /* int v f dx, f = sum_t f_t phi_t given per cell (rank 1):
+                           * A0[i][t] = int_{K0} Psi_i Psi_t, G_K[t] = |det J| f_t */
 } ffc_form_kind;
 
 typedef enum { FFC_TRIANGLE = 2, FFC_TETRAHEDRON = 3 } ffc_cell; /* value = spatial dimension d */
@@ -65,7 +69,8 @@ typedef enum { FFC_TRIANGLE = 2, FFC_TETRAHEDRON = 3 } ffc_cell; /* value = spat
  * FP64 for the CUDA-core precisions and FP32 (from the FP64 J^{-1}, det J) for the
  * tensor-core ones, which round it to their operand parts. FP64 is the CSR accumulation
  * type of ffc_assemble. Tensor-core precisions are built for tetrahedra: convection P2,
- * elasticity P1-P3, Poisson P2-P4, mass P3-P4 (others return FFC_EUNSUPPORTED). */
+ * elasticity P1-P3, Poisson P2-P4, mass P3-P4 (others, and every linear form, return
+ * FFC_EUNSUPPORTED). */
 typedef enum {
   FFC_FP64 = 0,   /* FP64 contraction, A_K stored as double */
   FFC_FP32 = 1,   /* FP32 G and A0, FP32 accumulation on CUDA cores, A_K stored as float */
@@ -95,7 +100,8 @@ typedef enum { FFC_ALG_AUTO = 0, FFC_ALG_DENSE = 1, FFC_ALG_BLOCK = 2 } ffc_algo
  * once, in FP64, by collapsed Gauss-Jacobi quadrature on the reference simplex
  * (Section 5.3 and Section 6), exact for the integrand degree.
  *   form   ffc_form_kind; cell ffc_cell; degree q of the Lagrange space (1..4;
- *          the convection form takes 1..2, elasticity 1..3, vector forms need tets).
+ *          the convection form takes 1..2, elasticity 1..3, vector forms need tets;
+ *          the source form's coefficient f lives in the same space as v).
  *   mu, lambda  elasticity parameters (ignored by the other forms).
  *   out    receives a new handle; release with ffc_form_destroy.
  * Returns FFC_EINVAL / FFC_EUNSUPPORTED / FFC_ENOMEM. Host-only: no device memory
@@ -104,11 +110,16 @@ typedef enum { FFC_ALG_AUTO = 0, FFC_ALG_DENSE = 1, FFC_ALG_BLOCK = 2 } ffc_algo
 int ffc_form_create(int form, int cell, int degree, double mu, double lambda, ffc_form** out);
 
 /* n_local = n (local dofs per cell), n_alpha = |alpha| (entries of G_K),
- * n_coeff = per-cell coefficients the form reads (30 for vector-P2 convection, else 0). */
+ * n_coeff = per-cell coefficients the form reads (30 for vector-P2 convection, n for
+ * the source form, else 0). */
 int ffc_form_info(const ffc_form* f, int* n_local, int* n_alpha, int* n_coeff);
 
+/* Rank of the form's tensor (Section 3.1): 2 for a bilinear form (element matrix),
+ * 1 for a linear form (element vector). */
+int ffc_form_rank(const ffc_form* f, int* rank);
+
 /* Raw reference tensor (the "raw format" output of Section 5.4):
- * host_out double [n*n][n_alpha], row-major. */
+ * host_out double [n^rank][n_alpha], row-major. */
 int ffc_form_reference_tensor(const ffc_form* f, double* host_out);
 
 /* Selects the evaluation of the vector forms (ffc_algorithm); FFC_EINVAL otherwise. */
@@ -124,8 +135,9 @@ void ffc_form_destroy(ffc_form* f);
  *   cells     device int32 [n_elem][d+1] vertex ids (local vertex order as given)
  *   vertices  device double [n_vert][d]
  *   coeffs    device double [n_elem][n_coeff] (convection: w on each cell, component
- *             blocked like the basis), NULL when n_coeff == 0
- *   A_K       device [n_elem][n][n], double for FFC_FP64, float otherwise
+ *             blocked like the basis; source: f on each cell), NULL when n_coeff == 0
+ *   A_K       device [n_elem][n][n] ([n_elem][n] for a linear form), double for
+ *             FFC_FP64, float otherwise
  *   precision ffc_precision
  * n_elem == 0 launches nothing and returns FFC_OK. A vertex id outside
  * [0, n_vert) is replaced by 0 and sets FFC_FLAG_BOUNDS (never read out of range).
@@ -156,6 +168,9 @@ int ffc_csr_pattern(int64_t n_elem, int n_local, const int32_t* dofmap, int64_t 
  *   csr_val[slot[e][i1][i2]] += A^K[i1][i2]     (FP64 atomic adds).
  *   slot     device int32 [n_elem][n][n] from ffc_csr_pattern
  *   csr_val  device double [nnz], accumulated into (zero it first for a fresh matrix)
+ * A linear form is added into a global vector the same way, b[slot[e][i]] += b^K[i]:
+ * `slot` is then the dof map itself (device int32 [n_elem][n]), `csr_val` the vector
+ * b and `nnz` its length (the number of global dofs).
  * Slots >= nnz are skipped and set FFC_FLAG_BOUNDS. Summation order of the atomic
  * adds is not deterministic (results agree to rounding).
  */

@@ -22,6 +22,7 @@ SIGNATURES = {
                                        ctypes.POINTER(c_vp)]),
     "ffc_form_info": (ctypes.c_int, [c_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                      ctypes.POINTER(ctypes.c_int)]),
+    "ffc_form_rank": (ctypes.c_int, [c_vp, ctypes.POINTER(ctypes.c_int)]),
     "ffc_form_reference_tensor": (ctypes.c_int, [c_vp, c_vp]),
     "ffc_form_set_algorithm": (ctypes.c_int, [c_vp, ctypes.c_int]),
     "ffc_form_destroy": (None, [c_vp]),

@@ -5,6 +5,13 @@ library's CUDA kernels). PyTorch provides device memory and streams.
     A_K = tabulate(form, cells, vertices)                 # [n_elem, n, n] on the GPU
     row_ptr, col, slot = csr_pattern(dofmap, n_dof)       # host, setup
     assemble(form, cells, vertices, slot_dev, csr_val)    # csr_val[slot] += A^K
+
+A linear form (SOURCE, rank 1) has element vectors [n_elem, n]; its assembly adds
+them into a global vector, with the dof map in place of the slots:
+
+    L = Form(SOURCE, TETRAHEDRON, 2)
+    b = torch.zeros(n_dof, dtype=torch.float64, device="cuda")
+    assemble(L, cells, vertices, dofmap_dev, b, coeffs=f_on_cells)
 """
 from __future__ import annotations
 
@@ -14,7 +21,7 @@ import numpy as np
 
 from ._capi import lib
 
-MASS, POISSON, NS_CONVECTION, ELASTICITY = 0, 1, 2, 3
+MASS, POISSON, NS_CONVECTION, ELASTICITY, SOURCE = 0, 1, 2, 3, 4
 TRIANGLE, TETRAHEDRON = 2, 3
 FP64, FP32, TF32, TF32X3, BF16X3 = 0, 1, 2, 3, 4
 PRECISIONS = {"fp64": FP64, "fp32": FP32, "tf32": TF32, "tf32x3": TF32X3, "bf16x3": BF16X3}
@@ -76,6 +83,14 @@ class Form:
         n, na, nc = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
         _check(lib().ffc_form_info(h, ctypes.byref(n), ctypes.byref(na), ctypes.byref(nc)), "ffc_form_info")
         self.n_local, self.n_alpha, self.n_coeff = n.value, na.value, nc.value
+        r = ctypes.c_int()
+        _check(lib().ffc_form_rank(h, ctypes.byref(r)), "ffc_form_rank")
+        self.rank = r.value
+
+    @property
+    def tensor_shape(self) -> tuple:
+        """Shape of one element tensor: (n, n), or (n,) for a linear form."""
+        return (self.n_local,) * self.rank
 
     @property
     def handle(self):
@@ -86,7 +101,7 @@ class Form:
         return self.cell
 
     def reference_tensor(self) -> np.ndarray:
-        out = np.empty((self.n_local * self.n_local, self.n_alpha), dtype=np.float64)
+        out = np.empty((self.n_local ** self.rank, self.n_alpha), dtype=np.float64)
         _check(lib().ffc_form_reference_tensor(self._h, out.ctypes.data_as(ctypes.c_void_p)),
                "ffc_form_reference_tensor")
         return out
@@ -104,19 +119,20 @@ class Form:
 
 
 def tabulate(form: Form, cells, vertices, coeffs=None, precision="fp64", out=None, stream=None):
-    """Element tensors [n_elem, n, n] (float64 for fp64, float32 otherwise)."""
+    """Element tensors [n_elem, n, n] ([n_elem, n] for a linear form; float64 for fp64,
+    float32 otherwise)."""
     import torch
 
     p = _prec(precision)
     n_elem = cells.shape[0]
-    n = form.n_local
+    shp = (n_elem,) + form.tensor_shape
     dt = torch.float64 if p == FP64 else torch.float32
     if out is None:
-        out = torch.empty((n_elem, n, n), dtype=dt, device=vertices.device)
+        out = torch.empty(shp, dtype=dt, device=vertices.device)
     c = _dev_ptr(cells, torch.int32, "cells", (n_elem, form.dim + 1))
     v = _dev_ptr(vertices, torch.float64, "vertices")
     w = _dev_ptr(coeffs, torch.float64, "coeffs", (n_elem, form.n_coeff)) if form.n_coeff else None
-    o = _dev_ptr(out, dt, "out", (n_elem, n, n))
+    o = _dev_ptr(out, dt, "out", shp)
     _check(lib().ffc_tabulate(form.handle, n_elem, c, v, vertices.shape[0], w, o, p, _stream(stream)),
            "ffc_tabulate")
     return out
@@ -140,16 +156,16 @@ def csr_pattern(dofmap: np.ndarray, n_dof: int, with_slots: bool = True):
 
 
 def assemble(form: Form, cells, vertices, slot, csr_val, coeffs=None, precision="fp64", stream=None):
-    """csr_val[slot[e, i1, i2]] += A^K[e, i1, i2] for all cells (accumulates)."""
+    """csr_val[slot[e, i1, i2]] += A^K[e, i1, i2] for all cells (accumulates). For a
+    linear form ``slot`` is the dof map [n_elem, n] and ``csr_val`` the global vector."""
     import torch
 
     p = _prec(precision)
     n_elem = cells.shape[0]
-    n = form.n_local
     c = _dev_ptr(cells, torch.int32, "cells", (n_elem, form.dim + 1))
     v = _dev_ptr(vertices, torch.float64, "vertices")
     w = _dev_ptr(coeffs, torch.float64, "coeffs", (n_elem, form.n_coeff)) if form.n_coeff else None
-    s = _dev_ptr(slot, torch.int32, "slot", (n_elem, n, n))
+    s = _dev_ptr(slot, torch.int32, "slot", (n_elem,) + form.tensor_shape)
     val = _dev_ptr(csr_val, torch.float64, "csr_val")
     _check(lib().ffc_assemble(form.handle, n_elem, c, v, vertices.shape[0], w, s, val, csr_val.numel(), p,
                               _stream(stream)), "ffc_assemble")

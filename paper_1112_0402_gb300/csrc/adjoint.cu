@@ -12,9 +12,10 @@
 //
 // One thread per cell. Only the symmetric part of Gbar enters (c = Gbar : K K^T with
 // K K^T symmetric, and Gbar + Gbar^T), so each thread accumulates the d(d+1)/2
-// combinations against the correspondingly combined reference tensor, held in shared
-// memory and read as a broadcast (all lanes at the same entry i); no cross-lane
-// reductions. Then it runs the geometry chain rule and scatters with atomics. FP64.
+// combinations against the reference tensor in the kernels' symmetric layout (columns
+// (a,a) and (a,b) + (b,a)), held in shared memory and read as a broadcast (all lanes at
+// the same entry i); no cross-lane reductions. Then it runs the geometry chain rule
+// and scatters with atomics. FP64.
 #include <cuda_runtime.h>
 
 #include "ffc_internal.h"
@@ -25,12 +26,6 @@ namespace {
 
 constexpr int THREADS = 256;
 
-// Index of the symmetric pair (a, b), a <= b: diagonal pairs first, then a < b.
-template <int D>
-__host__ __device__ constexpr int sym_index(int a, int b) {
-  return a == b ? a : (D == 2 ? 2 : (a == 0 ? (b == 1 ? 3 : 4) : 5));
-}
-
 template <int D, int Q>
 __global__ void __launch_bounds__(THREADS) poisson_adjoint_kernel(const int32_t* __restrict__ cells,
                                                                  const double* __restrict__ vertices,
@@ -40,21 +35,12 @@ __global__ void __launch_bounds__(THREADS) poisson_adjoint_kernel(const int32_t*
   constexpr int N = nscalar(D, Q);
   constexpr int NN = N * N;
   constexpr int NP = D * (D + 1) / 2;
-  // symmetric combinations of the reference tensor, one row per entry i:
+  // the reference tensor in the symmetric layout, one row per entry i:
   // P[i][aa] = A0[i][(a,a)], P[i][ab] = A0[i][(a,b)] + A0[i][(b,a)] (a < b)
   extern __shared__ double a0s[];  // [NN][NP]
   for (int k = threadIdx.x; k < NN * NP; k += blockDim.x) {
     const int i = k / NP, pidx = k % NP;
-    int a = 0, b = 0;
-#pragma unroll
-    for (int x = 0; x < D; ++x)
-#pragma unroll
-      for (int y = x; y < D; ++y)
-        if (sym_index<D>(x, y) == pidx) {
-          a = x;
-          b = y;
-        }
-    a0s[k] = (a == b) ? a0t[(a * D + a) * NN + i] : a0t[(a * D + b) * NN + i] + a0t[(b * D + a) * NN + i];
+    a0s[k] = a0t[pidx * NN + i];
   }
   __syncthreads();
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n_elem;
@@ -94,7 +80,7 @@ __global__ void __launch_bounds__(THREADS) poisson_adjoint_kernel(const int32_t*
     for (int a = 0; a < D; ++a)
 #pragma unroll
       for (int b = 0; b < D; ++b) {
-        const double v = gp[sym_index<D>(a < b ? a : b, a < b ? b : a)];
+        const double v = gp[sym_pair_index<D>(a < b ? a : b, a < b ? b : a)];
         S[a][b] = (a == b) ? 2.0 * v : v;
         if (a <= b) c += v * M[a][b];
       }

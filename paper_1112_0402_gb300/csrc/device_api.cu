@@ -52,8 +52,8 @@ int ensure_device_tensors(ffc_form* f, DeviceTensors** out) {
     *out = &it->second;
     return FFC_OK;
   }
-  const size_t nn = size_t(f->n) * f->n, na = f->na;
-  std::vector<double> rows(f->A0), cols(nn * na);
+  const size_t nn = f->n_entries(), na = size_t(f->kernel_na());
+  std::vector<double> rows(f->kernel_a0()), cols(nn * na);
   for (size_t i = 0; i < nn; ++i)
     for (size_t a = 0; a < na; ++a) cols[a * nn + i] = rows[i * na + a];
   std::vector<float> rows32(rows.begin(), rows.end()), cols32(cols.begin(), cols.end());
@@ -112,6 +112,7 @@ static int dispatch(const LaunchArgs& a, int precision, bool assemble) {
     if (rc == FFC_EUNSUPPORTED) rc = launch_simt_tet_mass(a, precision, assemble);
     if (rc == FFC_EUNSUPPORTED) rc = launch_simt_tet_poisson(a, precision, assemble);
     if (rc == FFC_EUNSUPPORTED) rc = launch_simt_vector(a, precision, assemble);
+    if (rc == FFC_EUNSUPPORTED) rc = launch_simt_source(a, precision, assemble);
   } else if (precision == FFC_TF32 || precision == FFC_TF32X3 || precision == FFC_BF16X3) {
     rc = launch_tc(a, precision, assemble);
   }

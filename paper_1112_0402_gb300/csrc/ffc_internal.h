@@ -36,8 +36,14 @@ struct ffc_form {
   int n = 0;           // local dofs (ns or d*ns)
   int na = 0;          // |alpha|
   int ncoeff = 0;      // per-cell coefficients
+  int rank = 2;        // 2: element matrix [n][n]; 1: element vector [n]
   double mu = 1.0, lambda = 1.25;
   std::vector<double> A0;  // [n*n][na]
+  // the CUDA-core kernels' layout of A0 where it differs (the Poisson form: G_K is
+  // symmetric, so A0 is stored once per pair a1 <= a2 with the (a1, a2) and (a2, a1)
+  // columns summed, nak = d(d+1)/2); empty otherwise
+  std::vector<double> A0k;
+  int nak = 0;
   // Cartesian-product structure of the vector forms (Section 3.5): reduced reference
   // tensor R[ns*ns][kr] and nb geometry blocks per cell (0 when the form has none)
   std::vector<double> R;
@@ -45,6 +51,10 @@ struct ffc_form {
   int algorithm = 0;  // ffc_algorithm
   std::mutex lock;
   std::map<int, ffc::DeviceTensors> dev;
+  // entries of one element tensor (rows of A0)
+  size_t n_entries() const { return rank == 2 ? size_t(n) * n : size_t(n); }
+  const std::vector<double>& kernel_a0() const { return A0k.empty() ? A0 : A0k; }
+  int kernel_na() const { return A0k.empty() ? na : nak; }
 };
 
 namespace ffc {
@@ -52,6 +62,9 @@ namespace ffc {
 // Host form compiler (reference tensor by collapsed Gauss-Jacobi quadrature).
 int compile_reference_tensor(ffc_form* f);
 int n_scalar_local(int d, int q);
+// column of the symmetric pair (a, b) in the Poisson kernel layout: diagonal pairs
+// 0..d-1, then (0,1) [, (0,2), (1,2)]; the device code uses the same numbering
+int sym_pair(int d, int a, int b);
 
 // Error text for ffc_last_error.
 void set_error(const std::string& msg);
@@ -82,6 +95,7 @@ int launch_simt_tri(const LaunchArgs& a, int precision, bool assemble);
 int launch_simt_tet_mass(const LaunchArgs& a, int precision, bool assemble);
 int launch_simt_tet_poisson(const LaunchArgs& a, int precision, bool assemble);
 int launch_simt_vector(const LaunchArgs& a, int precision, bool assemble);
+int launch_simt_source(const LaunchArgs& a, int precision, bool assemble);
 int launch_tc(const LaunchArgs& a, int precision, bool assemble);
 int launch_simt_block(const LaunchArgs& a, int precision, bool assemble);
 int launch_adjoint(const LaunchArgs& a, const double* dA, double* dvert);

@@ -13,9 +13,13 @@
 // geometry tensors G_K computed on the device (K = J^{-1}, det = |det J|):
 //   mass        alpha = 0                     A0 = int Psi_i1 Psi_i2             G = det
 //   Poisson     alpha = a1*d + a2             A0 = int d_a1 Psi_i1 d_a2 Psi_i2   G = det sum_b K[a1][b] K[a2][b]
+//               (the CUDA-core kernels use the symmetry of G, Section 3.5: one column per
+//               pair a1 <= a2, diagonal pairs first, the two off-diagonal columns summed)
 //   convection  alpha = t*d + a  (t = coefficient dof, component c(t))
 //               A0 = int Phi_i1[b] Phi_t[c(t)] d_a Phi_i2[b]                     G = det K[a][c(t)] w_t
 //               (eq. (navierstokes) with alpha_1 = c(alpha_2) for a component-blocked basis)
+//   source      (rank 1, i = test index) alpha = t (coefficient dof)
+//               A0 = int Psi_i Psi_t                                             G = det f_t
 //   elasticity  alpha = ((b1*d + b2)*d + a1)*d + a2
 //               A0 = delta(c(i1), b1) delta(c(i2), b2) int d_a1 Psi_s1 d_a2 Psi_s2
 //               G  = det (mu delta(b1,b2) (K K^T)[a1][a2] + mu K[a1][b2] K[a2][b1]
@@ -29,6 +33,12 @@
 #include "ffc_internal.h"
 
 namespace ffc {
+
+int sym_pair(int d, int a, int b) {
+  if (a > b) std::swap(a, b);
+  if (a == b) return a;
+  return d == 2 ? 2 : (a == 0 ? (b == 1 ? 3 : 4) : 5);
+}
 
 int n_scalar_local(int d, int q) {
   int num = 1;
@@ -199,7 +209,8 @@ int compile_reference_tensor(ffc_form* f) {
   if (int(lat.size()) != ns) return FFC_EINVAL;
   int p;
   switch (f->kind) {
-    case FFC_MASS: p = 2 * q; break;
+    case FFC_MASS:
+    case FFC_SOURCE: p = 2 * q; break;
     case FFC_POISSON:
     case FFC_ELASTICITY: p = std::max(0, 2 * q - 2); break;
     case FFC_NS_CONVECTION: p = 3 * q - 1; break;
@@ -223,7 +234,16 @@ int compile_reference_tensor(ffc_form* f) {
     }
   }
   const int na = f->na;
-  f->A0.assign(size_t(n) * n * na, 0.0);
+  f->A0.assign(f->n_entries() * na, 0.0);
+  if (f->kind == FFC_SOURCE) {
+    for (int i = 0; i < ns; ++i)
+      for (int t = 0; t < ns; ++t) {
+        double s = 0.0;
+        for (int iq = 0; iq < N; ++iq) s += W[iq] * psi[size_t(iq) * ns + i] * psi[size_t(iq) * ns + t];
+        f->A0[size_t(i) * na + t] = s;
+      }
+    return FFC_OK;
+  }
   auto A0 = [&](int i1, int i2, int alpha) -> double& { return f->A0[(size_t(i1) * n + i2) * na + alpha]; };
   // reduced reference tensors of the vector forms (component-blocked Cartesian basis)
   if (f->kind == FFC_ELASTICITY) {
@@ -257,6 +277,15 @@ int compile_reference_tensor(ffc_form* f) {
       for (int s1 = 0; s1 < ns; ++s1)
         for (int s2 = 0; s2 < ns; ++s2)
           for (int a = 0; a < d * d; ++a) A0(s1, s2, a) = S[(size_t(s1) * ns + s2) * d * d + a];
+      f->nak = d * (d + 1) / 2;
+      f->A0k.assign(size_t(n) * n * f->nak, 0.0);
+      for (size_t i = 0; i < size_t(n) * n; ++i)
+        for (int a1 = 0; a1 < d; ++a1)
+          for (int a2 = a1; a2 < d; ++a2) {
+            const double* row = &f->A0[i * na];
+            const double v = (a1 == a2) ? row[a1 * d + a1] : row[a1 * d + a2] + row[a2 * d + a1];
+            f->A0k[i * f->nak + sym_pair(d, a1, a2)] = v;
+          }
     } else {
       for (int c1 = 0; c1 < d; ++c1)
         for (int s1 = 0; s1 < ns; ++s1)

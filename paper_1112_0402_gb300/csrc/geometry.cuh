@@ -15,17 +15,26 @@ constexpr int nlocal(int form, int d, int q) {
 }
 constexpr int nalpha(int form, int d, int q) {
   return form == FFC_MASS ? 1
+       : form == FFC_SOURCE ? nscalar(d, q)
        : form == FFC_POISSON ? d * d
        : form == FFC_NS_CONVECTION ? nlocal(form, d, q) * d
        : d * d * d * d;
 }
 
-// Gathers the cell's vertices and computes K = J^{-1} and |det J|.
+// Column layout of the CUDA-core kernels' reference tensor: the Poisson G_K is
+// symmetric, so it is kept once per pair a1 <= a2 (Section 3.5: symmetry means fewer
+// operations), d(d+1)/2 columns: diagonal pairs first, then (0,1) [, (0,2), (1,2)].
+constexpr int nalpha_k(int form, int d, int q) { return form == FFC_POISSON ? d * (d + 1) / 2 : nalpha(form, d, q); }
 template <int D>
-__device__ __forceinline__ void cell_geometry(const int32_t* __restrict__ cells, const double* __restrict__ vertices,
-                                              int64_t n_vert, int64_t e, double K[D][D], double& det_abs,
-                                              bool& degenerate, bool& bad_index) {
-  double x[D + 1][D];
+__host__ __device__ constexpr int sym_pair_index(int a, int b) {
+  return a == b ? a : (D == 2 ? 2 : (a == 0 ? (b == 1 ? 3 : 4) : 5));
+}
+
+// Gathers the cell's vertex coordinates; an out-of-range vertex id is reported and
+// replaced by vertex 0 (never read out of bounds).
+template <int D>
+__device__ __forceinline__ void gather_vertices(const int32_t* __restrict__ cells, const double* __restrict__ vertices,
+                                                int64_t n_vert, int64_t e, double x[D + 1][D], bool& bad_index) {
   int id[D + 1];
   if constexpr (D == 3) {
     const int4 c = __ldg(reinterpret_cast<const int4*>(cells) + e);
@@ -40,7 +49,6 @@ __device__ __forceinline__ void cell_geometry(const int32_t* __restrict__ cells,
   bad_index = false;
 #pragma unroll
   for (int j = 0; j <= D; ++j) {
-    // an out-of-range vertex id is reported and replaced by vertex 0 (never read out of bounds)
     if (id[j] < 0 || id[j] >= n_vert) {
       bad_index = true;
       id[j] = 0;
@@ -48,6 +56,15 @@ __device__ __forceinline__ void cell_geometry(const int32_t* __restrict__ cells,
 #pragma unroll
     for (int r = 0; r < D; ++r) x[j][r] = __ldg(vertices + int64_t(id[j]) * D + r);
   }
+}
+
+// Gathers the cell's vertices and computes K = J^{-1} and |det J|.
+template <int D>
+__device__ __forceinline__ void cell_geometry(const int32_t* __restrict__ cells, const double* __restrict__ vertices,
+                                              int64_t n_vert, int64_t e, double K[D][D], double& det_abs,
+                                              bool& degenerate, bool& bad_index) {
+  double x[D + 1][D];
+  gather_vertices<D>(cells, vertices, n_vert, e, x, bad_index);
   double J[D][D];
 #pragma unroll
   for (int r = 0; r < D; ++r)
@@ -94,6 +111,50 @@ __device__ __forceinline__ void cell_geometry(const int32_t* __restrict__ cells,
 #pragma unroll
   for (int r = 1; r < D; ++r) hd *= h;
   degenerate = !(det_abs > 1e-14 * hd);
+}
+
+// |det J| alone (forms whose geometry tensor needs no J^{-1}: the source form). The
+// degeneracy test is the one of cell_geometry, |det J| <= 1e-14 h_max^d, evaluated
+// squared (det^2 <= 1e-28 h_max^{2d}) so it needs neither a square root nor a division.
+template <int D>
+__device__ __forceinline__ void cell_det(const int32_t* __restrict__ cells, const double* __restrict__ vertices,
+                                         int64_t n_vert, int64_t e, double& det_abs, bool& degenerate,
+                                         bool& bad_index) {
+  double x[D + 1][D];
+  gather_vertices<D>(cells, vertices, n_vert, e, x, bad_index);
+  double J[D][D];
+#pragma unroll
+  for (int r = 0; r < D; ++r)
+#pragma unroll
+    for (int c = 0; c < D; ++c) J[r][c] = x[c + 1][r] - x[0][r];
+  double det;
+  if constexpr (D == 3) {
+    det = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) + J[0][1] * (J[1][2] * J[2][0] - J[1][0] * J[2][2]) +
+          J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+  } else {
+    det = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+  }
+  det_abs = fabs(det);
+  // edges: the columns of J (from vertex 0) and their differences
+  double h2 = 0.0;
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    double s = 0.0;
+#pragma unroll
+    for (int r = 0; r < D; ++r) s += J[r][i] * J[r][i];
+    h2 = fmax(h2, s);
+#pragma unroll
+    for (int j = i + 1; j < D; ++j) {
+      double t = 0.0;
+#pragma unroll
+      for (int r = 0; r < D; ++r) t += (J[r][j] - J[r][i]) * (J[r][j] - J[r][i]);
+      h2 = fmax(h2, t);
+    }
+  }
+  double h2d = h2;
+#pragma unroll
+  for (int r = 1; r < D; ++r) h2d *= h2;
+  degenerate = !(det * det > 1e-28 * h2d);
 }
 
 // Geometry tensor of the form, written as G[alpha] (alpha layouts documented in
@@ -147,6 +208,30 @@ __device__ __forceinline__ void geometry_tensor(const double K[D][D], double det
             if (b1 == b2) g += mu * KK[a1][a2];
             store(((b1 * D + b2) * D + a1) * D + a2, det * g);
           }
+  }
+}
+
+}  // namespace ffc
+
+namespace ffc {
+
+// G_K in the CUDA-core kernels' layout (nalpha_k entries): the symmetric Poisson G once
+// per pair a1 <= a2, every other form as geometry_tensor.
+template <int D, int FORM, int Q, typename Store>
+__device__ __forceinline__ void geometry_tensor_k(const double K[D][D], double det, const double* w, double mu,
+                                                  double lambda, Store&& store) {
+  if constexpr (FORM == FFC_POISSON) {
+#pragma unroll
+    for (int a1 = 0; a1 < D; ++a1)
+#pragma unroll
+      for (int a2 = a1; a2 < D; ++a2) {
+        double s = 0.0;
+#pragma unroll
+        for (int b = 0; b < D; ++b) s += K[a1][b] * K[a2][b];
+        store(sym_pair_index<D>(a1, a2), det * s);
+      }
+  } else {
+    geometry_tensor<D, FORM, Q>(K, det, w, mu, lambda, store);
   }
 }
 

@@ -69,7 +69,7 @@ const char* ffc_status_string(int s) {
 int ffc_form_create(int form, int cell, int degree, double mu, double lambda, ffc_form** out) {
   if (!out) return FFC_EINVAL;
   *out = nullptr;
-  if (form < FFC_MASS || form > FFC_ELASTICITY) { set_error("unknown form"); return FFC_EINVAL; }
+  if (form < FFC_MASS || form > FFC_SOURCE) { set_error("unknown form"); return FFC_EINVAL; }
   if (cell != FFC_TRIANGLE && cell != FFC_TETRAHEDRON) { set_error("unknown cell"); return FFC_EINVAL; }
   if (degree < 1 || degree > 4) { set_error("degree must be 1..4"); return FFC_EINVAL; }
   if (form == FFC_NS_CONVECTION && (cell != FFC_TETRAHEDRON || degree > 2)) {
@@ -93,8 +93,10 @@ int ffc_form_create(int form, int cell, int degree, double mu, double lambda, ff
     case FFC_POISSON: f->na = f->d * f->d; break;
     case FFC_NS_CONVECTION: f->na = f->n * f->d; break;
     case FFC_ELASTICITY: f->na = f->d * f->d * f->d * f->d; break;
+    case FFC_SOURCE: f->na = f->n; break;
   }
-  f->ncoeff = (form == FFC_NS_CONVECTION) ? f->n : 0;
+  f->ncoeff = (form == FFC_NS_CONVECTION || form == FFC_SOURCE) ? f->n : 0;
+  f->rank = (form == FFC_SOURCE) ? 1 : 2;
   f->mu = mu;
   f->lambda = lambda;
   int rc;
@@ -116,6 +118,12 @@ int ffc_form_info(const ffc_form* f, int* n_local, int* n_alpha, int* n_coeff) {
   if (n_local) *n_local = f->n;
   if (n_alpha) *n_alpha = f->na;
   if (n_coeff) *n_coeff = f->ncoeff;
+  return FFC_OK;
+}
+
+int ffc_form_rank(const ffc_form* f, int* rank) {
+  if (!f || !rank) return FFC_EINVAL;
+  *rank = f->rank;
   return FFC_OK;
 }
 

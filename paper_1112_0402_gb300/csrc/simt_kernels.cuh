@@ -29,7 +29,7 @@ template <int D, int FORM, int Q, typename T, int BLOCK = 0, int KE_T = 0>
 struct SimtCfg {
   static constexpr int N = nlocal(FORM, D, Q);
   static constexpr int NN = N * N;
-  static constexpr int NA = nalpha(FORM, D, Q);
+  static constexpr int NA = nalpha_k(FORM, D, Q);
   static constexpr int VEC = 16 / int(sizeof(T));
   static constexpr int NAP = (NA + VEC - 1) / VEC * VEC;
   static constexpr int RMAX_THREADS = BLOCK > 0 ? BLOCK : 512;
@@ -113,7 +113,7 @@ __device__ __forceinline__ void simt_tile(const SimtParams& p, long long tile, u
         cell_geometry<D>(p.cells, p.vertices, p.n_vert, e, K, det, degenerate, bad_index);
         if (degenerate) atomicOr(p.status, FFC_FLAG_DEGENERATE);
         if (bad_index) atomicOr(p.status, FFC_FLAG_BOUNDS);
-        geometry_tensor<D, FORM, Q>(K, det, Ws + el * C::NCOEF, p.mu, p.lambda,
+        geometry_tensor_k<D, FORM, Q>(K, det, Ws + el * C::NCOEF, p.mu, p.lambda,
                                     [&](int a, double v) { g[a] = T(v); });
       } else {
 #pragma unroll 1

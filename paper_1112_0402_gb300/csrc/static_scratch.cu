@@ -82,7 +82,7 @@ extern "C" int ffc_tabulate_static(const ffc_form* f, int64_t n_elem, const int3
     set_error("ffc_tabulate_static: invalid argument (precision must be FFC_FP64 or FFC_FP32)");
     return FFC_EINVAL;
   }
-  const size_t nn = size_t(f->n) * f->n, na = size_t(f->na);
+  const size_t nn = f->n_entries(), na = size_t(f->kernel_na());
   const size_t need = nn * na * (2 * sizeof(double) + 2 * sizeof(float)) + 4 * 256;
   if (need > kStaticA0Bytes) {
     set_error("ffc_tabulate_static: the reference tensor needs " + std::to_string(need) +
@@ -113,7 +113,7 @@ extern "C" int ffc_tabulate_static(const ffc_form* f, int64_t n_elem, const int3
   t.a0t_f32 = reinterpret_cast<float*>(p);
   cudaError_t e = cudaMemsetAsync(status, 0, sizeof(uint32_t), s);
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(t.a0_f64, f->A0.data(), nn * na * sizeof(double), cudaMemcpyHostToDevice, s);
+    e = cudaMemcpyAsync(t.a0_f64, f->kernel_a0().data(), nn * na * sizeof(double), cudaMemcpyHostToDevice, s);
   if (e != cudaSuccess) {
     set_error(std::string("ffc_tabulate_static: ") + cudaGetErrorString(e));
     return FFC_ECUDA;
@@ -125,6 +125,7 @@ extern "C" int ffc_tabulate_static(const ffc_form* f, int64_t n_elem, const int3
   if (rc == FFC_EUNSUPPORTED) rc = launch_simt_tet_mass(a, precision, false);
   if (rc == FFC_EUNSUPPORTED) rc = launch_simt_tet_poisson(a, precision, false);
   if (rc == FFC_EUNSUPPORTED) rc = launch_simt_vector(a, precision, false);
+  if (rc == FFC_EUNSUPPORTED) rc = launch_simt_source(a, precision, false);
   if (rc != FFC_OK) return rc;
   if (host_flags) {
     e = cudaMemcpyAsync(host_flags, status, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);

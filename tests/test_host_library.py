@@ -191,3 +191,19 @@ def test_algorithm_and_batch_arguments_are_validated_on_the_host():
     items[0].form = g.handle
     assert L.ffc_batch_create(items, 1, 1, ctypes.byref(out)) == -5
     assert L.ffc_batch_create(None, 0, 1, ctypes.byref(out)) == -1
+
+
+@pytest.mark.parametrize("d,q", [(2, 1), (2, 4), (3, 1), (3, 2), (3, 3)])
+def test_source_form_is_rank_one_with_the_mass_reference_tensor(d, q):
+    import paper_1112_0402_gb300 as F
+
+    f = F.Form(F.SOURCE, d, q)
+    exact = np.array(X.reference_tensor_mass(d, q), dtype=float)
+    n = exact.shape[0]
+    assert (f.rank, f.n_local, f.n_alpha, f.n_coeff) == (1, n, n, n)
+    A0 = f.reference_tensor()
+    assert A0.shape == (n, n)  # A0[i][t] = int Psi_i Psi_t
+    assert np.abs(A0 - exact).max() <= 4e-15 * np.abs(exact).max()
+    assert F.Form(F.MASS, d, q).rank == 2
+    with pytest.raises(F.FFCError):
+        F.Form(5, d, q)
