@@ -65,10 +65,11 @@ typedef enum {
 
 typedef enum { FFC_TRIANGLE = 2, FFC_TETRAHEDRON = 3 } ffc_cell; /* value = spatial dimension d */
 
-/* Arithmetic of the contraction A0 : G. J, det J and J^{-1} are always FP64; G_K is
- * FP64 for the CUDA-core precisions and FP32 (from the FP64 J^{-1}, det J) for the
- * tensor-core ones, which round it to their operand parts. FP64 is the CSR accumulation
- * type of ffc_assemble. Tensor-core precisions are built for tetrahedra: convection P2,
+/* Arithmetic of the contraction A0 : G. J, det J and J^{-1} are always FP64. G_K is
+ * formed from them in FP64 and rounded once for the dense CUDA-core contraction, and in
+ * the contraction's own type for the block algorithm (FFC_ALG_BLOCK: FP32 products for
+ * FFC_FP32) and in FP32 for the tensor-core precisions, which round it to their operand
+ * parts. FP64 is the CSR accumulation type of ffc_assemble. Tensor-core precisions are built for tetrahedra: convection P2,
  * elasticity P1-P3, Poisson P2-P4, mass P3-P4 (others, and every linear form, return
  * FFC_EUNSUPPORTED). */
 typedef enum {

@@ -58,6 +58,43 @@ __device__ __forceinline__ void gather_vertices(const int32_t* __restrict__ cell
   }
 }
 
+// The degeneracy test |det J| <= 1e-14 h_max^d (h_max the longest edge), evaluated as
+// det^2 <= 1e-28 h_max^{2d}: no square root, no division. The edges are J's columns
+// (x_j - x_0) and their differences (x_j - x_i); their squared lengths are formed in
+// FP32 from J, since a threshold needs no more (on GB300 every FP64 instruction is
+// scarce), and the comparison is made in FP64 against the FP64 determinant.
+template <int D>
+__device__ __forceinline__ bool degenerate_test(const double J[D][D], double det) {
+  float Jf[D][D];
+#pragma unroll
+  for (int r = 0; r < D; ++r)
+#pragma unroll
+    for (int c = 0; c < D; ++c) Jf[r][c] = float(J[r][c]);
+  float h2 = 0.f;
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    float s = 0.f;
+#pragma unroll
+    for (int r = 0; r < D; ++r) s = fmaf(Jf[r][i], Jf[r][i], s);
+    h2 = fmaxf(h2, s);
+#pragma unroll
+    for (int j = i + 1; j < D; ++j) {
+      float t = 0.f;
+#pragma unroll
+      for (int r = 0; r < D; ++r) {
+        const float dd = Jf[r][j] - Jf[r][i];
+        t = fmaf(dd, dd, t);
+      }
+      h2 = fmaxf(h2, t);
+    }
+  }
+  const double h2_64 = double(h2);
+  double h2d = h2_64;
+#pragma unroll
+  for (int r = 1; r < D; ++r) h2d *= h2_64;
+  return !(det * det > 1e-28 * h2d);
+}
+
 // Gathers the cell's vertices and computes K = J^{-1} and |det J|.
 template <int D>
 __device__ __forceinline__ void cell_geometry(const int32_t* __restrict__ cells, const double* __restrict__ vertices,
@@ -96,26 +133,11 @@ __device__ __forceinline__ void cell_geometry(const int32_t* __restrict__ cells,
     K[1][1] = J[0][0] * inv;
   }
   det_abs = fabs(det);
-  double h2 = 0.0;
-#pragma unroll
-  for (int i = 0; i <= D; ++i)
-#pragma unroll
-    for (int j = i + 1; j <= D; ++j) {
-      double s = 0.0;
-#pragma unroll
-      for (int r = 0; r < D; ++r) s += (x[i][r] - x[j][r]) * (x[i][r] - x[j][r]);
-      h2 = fmax(h2, s);
-    }
-  const double h = sqrt(h2);
-  double hd = h;
-#pragma unroll
-  for (int r = 1; r < D; ++r) hd *= h;
-  degenerate = !(det_abs > 1e-14 * hd);
+  degenerate = degenerate_test<D>(J, det);
 }
 
-// |det J| alone (forms whose geometry tensor needs no J^{-1}: the source form). The
-// degeneracy test is the one of cell_geometry, |det J| <= 1e-14 h_max^d, evaluated
-// squared (det^2 <= 1e-28 h_max^{2d}) so it needs neither a square root nor a division.
+// |det J| alone (forms whose geometry tensor needs no J^{-1}: the source form), with the
+// same degeneracy test as cell_geometry.
 template <int D>
 __device__ __forceinline__ void cell_det(const int32_t* __restrict__ cells, const double* __restrict__ vertices,
                                          int64_t n_vert, int64_t e, double& det_abs, bool& degenerate,
@@ -135,26 +157,7 @@ __device__ __forceinline__ void cell_det(const int32_t* __restrict__ cells, cons
     det = J[0][0] * J[1][1] - J[0][1] * J[1][0];
   }
   det_abs = fabs(det);
-  // edges: the columns of J (from vertex 0) and their differences
-  double h2 = 0.0;
-#pragma unroll
-  for (int i = 0; i < D; ++i) {
-    double s = 0.0;
-#pragma unroll
-    for (int r = 0; r < D; ++r) s += J[r][i] * J[r][i];
-    h2 = fmax(h2, s);
-#pragma unroll
-    for (int j = i + 1; j < D; ++j) {
-      double t = 0.0;
-#pragma unroll
-      for (int r = 0; r < D; ++r) t += (J[r][j] - J[r][i]) * (J[r][j] - J[r][i]);
-      h2 = fmax(h2, t);
-    }
-  }
-  double h2d = h2;
-#pragma unroll
-  for (int r = 1; r < D; ++r) h2d *= h2;
-  degenerate = !(det * det > 1e-28 * h2d);
+  degenerate = degenerate_test<D>(J, det);
 }
 
 // Geometry tensor of the form, written as G[alpha] (alpha layouts documented in

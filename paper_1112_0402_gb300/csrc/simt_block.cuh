@@ -16,9 +16,15 @@
 //               + mu K[a1][c2] K[a2][c1] + lambda K[a1][c1] K[a2][c2]).
 // This is the same value as the dense A0 : G_K contraction (identical sums), with
 // 27x (convection) and 9x (elasticity) fewer multiply-adds and a reference tensor small
-// enough for registers. Thread layout as in the dense SIMT kernel: thread t owns
-// entries i = t mod NTI + r*NTI of the cells of its group, so stores are coalesced;
-// structurally zero entries are stored as 0 (tabulate) or skipped (assembly).
+// enough for registers.
+//
+// Thread layout ("pair major"): a thread owns a pair (s1, s2) and keeps its reduced row
+// R[(s1,s2)] in registers; per cell it contracts that row with each of the cell's nb
+// geometry blocks (16-byte shared-memory loads, the same address across the warp) and
+// writes the d*d entries ((c1,s1),(c2,s2)) of the element tensor. Consecutive threads
+// hold consecutive s2, so each store instruction covers runs of n_s consecutive
+// entries. The convection form's one block goes to the d diagonal positions; the
+// structurally zero off-diagonal blocks are stored as 0 (tabulate) or skipped (assembly).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -31,8 +37,9 @@
 
 namespace ffc {
 
-// BLOCK = 0: block size from n^2; BLOCK > 0: fixed block size shared with other forms
-// (batched kernel). KE_T: cells per thread group and tile (0 = 128).
+// BLOCK = 0: thread count from the number of pairs; BLOCK > 0: fixed block size shared
+// with other forms (batched kernel). KE_T > 0: cells per thread group and tile (tiles
+// are capped at 128 cells); 0 = 128 cells per tile.
 template <int D, int FORM, int Q, typename T, int BLOCK = 0, int KE_T = 0>
 struct BlockCfg {
   static constexpr int NS = nscalar(D, Q);
@@ -42,72 +49,66 @@ struct BlockCfg {
   static constexpr int NB = FORM == FFC_NS_CONVECTION ? 1 : D * D;
   static constexpr int VEC = 16 / int(sizeof(T));
   static constexpr int KRP = (KR + VEC - 1) / VEC * VEC;
-  static constexpr int RMAX_THREADS = BLOCK > 0 ? BLOCK : 512;
-  static constexpr int R = (NN + RMAX_THREADS - 1) / RMAX_THREADS;
-  static constexpr int NTI = (NN + R - 1) / R;
-  static constexpr int EG = BLOCK > 0 ? BLOCK / NTI : (NTI >= 256 ? 1 : 256 / NTI);
-  static constexpr int NT = BLOCK > 0 ? BLOCK : NTI * EG;
-  static constexpr bool REG_R = R * KR * int(sizeof(T)) / 4 <= (BLOCK > 0 ? (BLOCK >= 512 ? 80 : 32) : 96);
-  static constexpr int KE = ((KE_T > 0 ? KE_T : 128) + EG - 1) / EG;  // 128 cells: 4 warps share the geometry
-  static constexpr int E = EG * KE;
+  static constexpr int NP2 = NS * NS;  // pairs (s1, s2)
+  // about 256 threads: whole groups of NP2 threads, rounded up to whole warps
+  static constexpr int NT0 = NP2 >= 256 ? NP2 : NP2 * (256 / NP2);
+  static constexpr int NT = BLOCK > 0 ? BLOCK : (NT0 + 31) / 32 * 32;
+  static constexpr int GRP = NT >= NP2 ? NT / NP2 : 1;  // thread groups; a tile's cells are dealt to them
+  static constexpr int PPT = (NP2 + NT - 1) / NT;       // pairs per thread
+  static constexpr bool REG_R = PPT * KR * int(sizeof(T)) / 4 <= 64;
+  static constexpr int E_DEF = (FORM == FFC_NS_CONVECTION && sizeof(T) == 8) ? 64 : 128;
+  static constexpr int E = KE_T > 0 ? (KE_T * GRP < 128 ? KE_T * GRP : 128) : E_DEF;  // cells per tile
   static constexpr int NCOEF = FORM == FFC_NS_CONVECTION ? N : 0;
   static constexpr size_t G_BYTES = size_t(E) * NB * KRP * sizeof(T);
-  static constexpr size_t R_BYTES = REG_R ? 0 : size_t(NS) * NS * KRP * sizeof(T);
-  static constexpr size_t SMEM = G_BYTES + R_BYTES + size_t(E) * NCOEF * sizeof(double);
+  static constexpr size_t R_BYTES = REG_R ? 0 : size_t(NP2) * KRP * sizeof(T);
+  static constexpr size_t W_BYTES = size_t(E) * NCOEF * sizeof(double);
+  static constexpr size_t SMEM = G_BYTES + R_BYTES + W_BYTES;
 };
 
 template <class C, typename T>
 struct BlockRows {
-  int row[C::R];   // reduced row (s1, s2) of each owned entry
-  int boff[C::R];  // offset of its geometry block in a cell's blocks; -1: structurally zero
-  T rr[C::REG_R ? C::R : 1][C::REG_R ? C::KR : 1];
+  T rr[C::REG_R ? C::PPT : 1][C::REG_R ? C::KR : 1];  // reduced rows of the thread's pairs
 };
 
-// Per-thread entry decoding and the reduced reference tensor (registers, or shared memory
-// behind the geometry blocks; the first barrier of block_tile orders those stores).
+// The thread's pairs: pair slot j holds pp = t mod NP2 (NT >= NP2, group t / NP2) or
+// pp = t + j*NT (NT < NP2, one group). -1: no pair.
+template <class C>
+__device__ __forceinline__ int pair_of(int t, int j) {
+  if constexpr (C::NT >= C::NP2) return (j == 0 && t < C::GRP * C::NP2) ? t % C::NP2 : -1;
+  else return (t + j * C::NT < C::NP2) ? t + j * C::NT : -1;
+}
+
+// The reduced reference tensor rows (registers, or shared memory behind the geometry
+// blocks; the first barrier of block_tile orders those stores).
 template <class C, int D, int FORM, typename T>
 __device__ __forceinline__ void block_rows_init(const void* r, BlockRows<C, T>& b, unsigned char* smem) {
   const int t = threadIdx.x;
-  const int ti = t % C::NTI;
   const T* Rg = static_cast<const T*>(r);
-#pragma unroll
-  for (int k = 0; k < C::R; ++k) {
-    const int i = ti + k * C::NTI;
-    b.row[k] = 0;
-    b.boff[k] = -1;
-    if (i < C::NN) {
-      const int i1 = i / C::N, i2 = i % C::N;
-      const int c1 = i1 / C::NS, s1 = i1 % C::NS, c2 = i2 / C::NS, s2 = i2 % C::NS;
-      b.row[k] = s1 * C::NS + s2;
-      if constexpr (FORM == FFC_NS_CONVECTION) b.boff[k] = (c1 == c2) ? 0 : -1;
-      else b.boff[k] = (c1 * D + c2) * C::KRP;
-    }
-  }
   if constexpr (C::REG_R) {
 #pragma unroll
-    for (int k = 0; k < C::R; ++k)
+    for (int j = 0; j < C::PPT; ++j) {
+      const int pp = pair_of<C>(t, j);
 #pragma unroll
-      for (int j = 0; j < C::KR; ++j) b.rr[k][j] = Rg[size_t(b.row[k]) * C::KR + j];
+      for (int k = 0; k < C::KR; ++k) b.rr[j][k] = pp >= 0 ? Rg[size_t(pp) * C::KR + k] : T(0);
+    }
   } else {
     T* Rs = reinterpret_cast<T*>(smem + C::G_BYTES);
-    for (int k = t; k < C::NS * C::NS * C::KRP; k += C::NT) {
+    for (int k = t; k < C::NP2 * C::KRP; k += C::NT) {
       const int rw = k / C::KRP, kk = k % C::KRP;
       Rs[k] = kk < C::KR ? Rg[size_t(rw) * C::KR + kk] : T(0);
     }
   }
 }
 
-// One tile of E cells: reduced geometry blocks (FP64) into shared memory, then each
-// owned entry contracts its block with its reduced row. Contains block barriers.
+// One tile of E cells: reduced geometry blocks into shared memory, then each thread
+// contracts its pairs with every block of the group's cells. Contains block barriers.
 template <class C, int D, int FORM, int Q, typename T, bool ASSEMBLE>
 __device__ __forceinline__ void block_tile(const SimtParams& p, long long tile, unsigned char* smem,
                                            const BlockRows<C, T>& br) {
   T* Gs = reinterpret_cast<T*>(smem);                                       // [E][NB][KRP]
-  const T* Rs = reinterpret_cast<const T*>(smem + C::G_BYTES);              // [NS*NS][KRP]
+  const T* Rs = reinterpret_cast<const T*>(smem + C::G_BYTES);              // [NP2][KRP]
   double* Ws = reinterpret_cast<double*>(smem + C::G_BYTES + C::R_BYTES);   // [E][NCOEF]
   const int t = threadIdx.x;
-  const int ti = t % C::NTI;
-  const int eg = t / C::NTI;
   const long long e0 = tile * C::E;
   if constexpr (C::NCOEF > 0) {
     const long long lim = (p.n_elem - e0) * C::NCOEF;
@@ -115,7 +116,7 @@ __device__ __forceinline__ void block_tile(const SimtParams& p, long long tile, 
     for (int k = t; k < C::E * C::NCOEF; k += C::NT) Ws[k] = (k < lim) ? __ldg(src + k) : 0.0;
   }
   __syncthreads();
-  // ---- reduced geometry blocks of the tile's cells (FP64)
+  // ---- reduced geometry blocks of the tile's cells (J^{-1}, det J in FP64)
   for (int el = t; el < C::E; el += C::NT) {
     const long long e = e0 + el;
     T* g = Gs + size_t(el) * C::NB * C::KRP;
@@ -127,28 +128,42 @@ __device__ __forceinline__ void block_tile(const SimtParams& p, long long tile, 
       if (degenerate) atomicOr(p.status, FFC_FLAG_DEGENERATE);
       if (bad_index) atomicOr(p.status, FFC_FLAG_BOUNDS);
     }
+    // the reduced geometry blocks are products of J^{-1} and det J with the coefficients;
+    // for an FP32 contraction they are formed in FP32 (they are rounded to FP32 anyway),
+    // for FP64 in FP64
+    using GT = T;
+    GT Kt[D][D], dett = GT(det);
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+#pragma unroll
+      for (int b = 0; b < D; ++b) Kt[a][b] = GT(K[a][b]);
     if constexpr (FORM == FFC_NS_CONVECTION) {
       const double* w = Ws + el * C::NCOEF;
 #pragma unroll
-      for (int st = 0; st < C::NS; ++st)
+      for (int st = 0; st < C::NS; ++st) {
+        GT wc[D];
+#pragma unroll
+        for (int c = 0; c < D; ++c) wc[c] = GT(w[c * C::NS + st]);
 #pragma unroll
         for (int a = 0; a < D; ++a) {
-          double h = 0.0;
+          GT h = GT(0);
 #pragma unroll
-          for (int c = 0; c < D; ++c) h += K[a][c] * w[c * C::NS + st];
-          g[st * D + a] = live ? T(det * h) : T(0);
+          for (int c = 0; c < D; ++c) h = fma(Kt[a][c], wc[c], h);
+          g[st * D + a] = live ? dett * h : T(0);
         }
+      }
     } else {
-      double KK[D][D];
+      GT KK[D][D];
 #pragma unroll
       for (int a1 = 0; a1 < D; ++a1)
 #pragma unroll
         for (int a2 = 0; a2 < D; ++a2) {
-          double sum = 0.0;
+          GT sum = GT(0);
 #pragma unroll
-          for (int b = 0; b < D; ++b) sum += K[a1][b] * K[a2][b];
+          for (int b = 0; b < D; ++b) sum = fma(Kt[a1][b], Kt[a2][b], sum);
           KK[a1][a2] = sum;
         }
+      const GT mu = GT(p.mu), lambda = GT(p.lambda);
 #pragma unroll
       for (int c1 = 0; c1 < D; ++c1)
 #pragma unroll
@@ -157,9 +172,9 @@ __device__ __forceinline__ void block_tile(const SimtParams& p, long long tile, 
           for (int a1 = 0; a1 < D; ++a1)
 #pragma unroll
             for (int a2 = 0; a2 < D; ++a2) {
-              double v = p.mu * K[a1][c2] * K[a2][c1] + p.lambda * K[a1][c1] * K[a2][c2];
-              if (c1 == c2) v += p.mu * KK[a1][a2];
-              g[(c1 * D + c2) * C::KRP + a1 * D + a2] = live ? T(det * v) : T(0);
+              GT v = mu * Kt[a1][c2] * Kt[a2][c1] + lambda * Kt[a1][c1] * Kt[a2][c2];
+              if (c1 == c2) v += mu * KK[a1][a2];
+              g[(c1 * D + c2) * C::KRP + a1 * D + a2] = live ? dett * v : T(0);
             }
     }
 #pragma unroll
@@ -167,60 +182,85 @@ __device__ __forceinline__ void block_tile(const SimtParams& p, long long tile, 
       for (int k = C::KR; k < C::KRP; ++k) g[b * C::KRP + k] = T(0);
   }
   __syncthreads();
-  // ---- contraction per owned entry (thread groups beyond EG idle); in assembly the
-  // slots of the next cell are loaded while this cell's atomics issue
-  int slot_next[ASSEMBLE ? C::R : 1];
-  if constexpr (ASSEMBLE) {
-    const long long e = e0 + eg;
+  // ---- contraction: pair slots x the group's cells x blocks
+  using V = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+  const int grp = C::NT >= C::NP2 ? t / C::NP2 : 0;
+  const long long left = p.n_elem - e0;
+  const int nc = int(left < C::E ? left : C::E);
 #pragma unroll
-    for (int r = 0; r < C::R; ++r) {
-      const int i = ti + r * C::NTI;
-      slot_next[r] = (eg < C::EG && e < p.n_elem && i < C::NN && br.boff[r] >= 0) ? __ldg(p.slot + e * C::NN + i)
-                                                                                  : -1;
-    }
-  }
-#pragma unroll 1
-  for (int kc = 0; kc < C::KE && eg < C::EG; ++kc) {
-    const int el = eg + kc * C::EG;
-    const long long e = e0 + el;
-    if (e >= p.n_elem) break;
-    int slot_cur[ASSEMBLE ? C::R : 1];
+  for (int j = 0; j < C::PPT; ++j) {
+    const int pp = pair_of<C>(t, j);
+    if (pp < 0) continue;
+    const int s1 = pp / C::NS, s2 = pp % C::NS;
+    const T* rrow = Rs + size_t(pp) * C::KRP;
+    // positions of the d*d entries ((c1,s1),(c2,s2)) in the cell's element tensor
+    int pos[D * D];
+#pragma unroll
+    for (int c1 = 0; c1 < D; ++c1)
+#pragma unroll
+      for (int c2 = 0; c2 < D; ++c2) pos[c1 * D + c2] = (c1 * C::NS + s1) * C::N + c2 * C::NS + s2;
+    constexpr bool DIAG = FORM == FFC_NS_CONVECTION;  // one block, on the diagonal
+    // assembly: the slots of the next cell are loaded while this cell's atomics issue
+    int sl_next[ASSEMBLE ? D * D : 1];
     if constexpr (ASSEMBLE) {
-      const long long en = e + C::EG;
-      const bool more = (kc + 1 < C::KE) && (en < p.n_elem);
 #pragma unroll
-      for (int r = 0; r < C::R; ++r) {
-        const int i = ti + r * C::NTI;
-        slot_cur[r] = slot_next[r];
-        slot_next[r] = (more && i < C::NN && br.boff[r] >= 0) ? __ldg(p.slot + en * C::NN + i) : -1;
-      }
+      for (int b = 0; b < D * D; ++b)
+        sl_next[b] = (grp < nc && (!DIAG || b % (D + 1) == 0)) ? __ldg(p.slot + (e0 + grp) * C::NN + pos[b]) : -1;
     }
-    const T* g = Gs + size_t(el) * C::NB * C::KRP;
+#pragma unroll 1
+    for (int el = grp; el < nc; el += C::GRP) {
+      const long long e = e0 + el;
+      int sl[ASSEMBLE ? D * D : 1];
+      if constexpr (ASSEMBLE) {
+        const int en = el + C::GRP;
 #pragma unroll
-    for (int r = 0; r < C::R; ++r) {
-      const int i = ti + r * C::NTI;
-      if (i >= C::NN) continue;
-      T acc = T(0);
-      if (br.boff[r] >= 0) {
-        const T* gb = g + br.boff[r];
-        if constexpr (C::REG_R) {
-#pragma unroll
-          for (int k = 0; k < C::KR; ++k) acc = fma(gb[k], br.rr[r][k], acc);
-        } else {
-          const T* rw = Rs + size_t(br.row[r]) * C::KRP;
-#pragma unroll
-          for (int k = 0; k < C::KR; ++k) acc = fma(gb[k], rw[k], acc);
+        for (int b = 0; b < D * D; ++b) {
+          sl[b] = sl_next[b];
+          sl_next[b] = (en < nc && (!DIAG || b % (D + 1) == 0)) ? __ldg(p.slot + (e0 + en) * C::NN + pos[b]) : -1;
         }
       }
-      const long long o = e * C::NN + i;
-      if constexpr (ASSEMBLE) {
-        if (br.boff[r] >= 0) {  // structural zeros add nothing
-          const int s = slot_cur[r];
-          if (s >= 0 && s < p.nnz) atomicAdd(p.csr_val + s, double(acc));
-          else atomicOr(p.status, FFC_FLAG_BOUNDS);
+      const V* gv = reinterpret_cast<const V*>(Gs + size_t(el) * C::NB * C::KRP);
+      T val[C::NB];
+#pragma unroll
+      for (int b = 0; b < C::NB; ++b) {
+        T acc = T(0);
+#pragma unroll
+        for (int kv = 0; kv < C::KRP / C::VEC; ++kv) {
+          const V x = gv[b * (C::KRP / C::VEC) + kv];
+          T xs[C::VEC];
+          if constexpr (sizeof(T) == 4) {
+            xs[0] = x.x;
+            xs[1] = x.y;
+            xs[2] = x.z;
+            xs[3] = x.w;
+          } else {
+            xs[0] = x.x;
+            xs[1] = x.y;
+          }
+#pragma unroll
+          for (int q = 0; q < C::VEC; ++q) {
+            const int k = kv * C::VEC + q;
+            if (k < C::KR) {
+              if constexpr (C::REG_R) acc = fma(xs[q], br.rr[j][k < C::KR ? k : 0], acc);
+              else acc = fma(xs[q], rrow[k], acc);
+            }
+          }
         }
-      } else {
-        __stcs(static_cast<T*>(p.out) + o, acc);
+        val[b] = acc;
+      }
+#pragma unroll
+      for (int b = 0; b < D * D; ++b) {
+        const bool nonzero = !DIAG || b % (D + 1) == 0;
+        const T v = DIAG ? (nonzero ? val[0] : T(0)) : val[DIAG ? 0 : b];
+        if constexpr (ASSEMBLE) {
+          if (nonzero) {  // structural zeros add nothing
+            const int sv = sl[b];
+            if (sv >= 0 && sv < p.nnz) atomicAdd(p.csr_val + sv, double(v));
+            else atomicOr(p.status, FFC_FLAG_BOUNDS);
+          }
+        } else {
+          __stcs(static_cast<T*>(p.out) + e * C::NN + pos[b], v);
+        }
       }
     }
   }

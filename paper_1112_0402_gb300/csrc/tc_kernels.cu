@@ -186,6 +186,17 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
   for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
 }
 
+// The same load without its wait (several loads in flight, then one tmem_wait_ld),
+// straight into the caller's registers: they must not be read before tmem_wait_ld().
+__device__ __forceinline__ void tmem_ld16_issue(uint32_t taddr, uint32_t* r) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
 __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
@@ -383,17 +394,24 @@ __global__ void __launch_bounds__(THREADS, 1) tc_tabulate_kernel(TcParams p) {
 }
 
 // ---------------------------------------------------------------------------------
-// Warp-specialized version. Warps 0..7 produce the B tile (G) and drain the
-// accumulator; warp 8 lane 0 issues the bulk copies of the A0 tiles and the MMAs.
+// Warp-specialized version. Three roles:
+//   warps 0..3  producers: the geometry of the NEXT cell tile (FP64 J^{-1}, det, then
+//               G_K in FP32, one cell per thread) is computed into registers while the
+//               MMAs of the current tile still read the B buffer; once the control warp
+//               reports the buffer free (b_empty), the split parts are written to it;
+//   warps 4..7  drainers: TMEM lane quarter (warp mod 4) x all 128 cell columns, stores
+//               or atomics of the element tensor entries;
+//   warp 8      control: lane 0 issues the bulk copies of the A0 tiles and the MMAs.
 // The accumulator is double-buffered in TMEM (2 x 128 columns) so the MMA chain of
-// M-tile m+1 runs while the epilogue stores M-tile m; the A0 tiles are double-
-// buffered in shared memory when two stages fit. Barriers:
+// M-tile m+1 runs while the drainers store M-tile m; the A0 tiles are double-buffered
+// in shared memory when two stages fit. Barriers:
 //   a_full[s]   bulk copy of stage s landed (expect_tx)       a_empty[s]  MMAs reading stage s done
-//   acc_full[b] MMAs into TMEM buffer b done                   acc_empty[b] epilogue drained buffer b
-//   b_full      B tile of the current cell tile written by the epilogue warps
+//   acc_full[b] MMAs into TMEM buffer b done                   acc_empty[b] drainers emptied buffer b
+//   b_full      B tile of the current cell tile written        b_empty     MMAs reading B done
 // ---------------------------------------------------------------------------------
-constexpr int EPI_WARPS = 8;
+constexpr int EPI_WARPS = 8;                 // producers (0..3) and drainers (4..7)
 constexpr int EPI_THREADS = EPI_WARPS * 32;
+constexpr int ROLE_THREADS = EPI_THREADS / 2;  // 128: one producer thread per cell, one drainer per TMEM lane
 constexpr int WS_THREADS = EPI_THREADS + 32;
 
 template <int D, int FORM, int Q, int MODE>
@@ -500,12 +518,66 @@ __device__ __forceinline__ void split_f32(float x, typename Split<MODE>::Store (
   }
 }
 
+// Writes one cell's G row (operand B row `row`) as its split parts, one 16-byte core-matrix
+// row per store: a warp's 32 rows are four 128-byte core-matrix blocks, conflict free.
+template <class C, int MODE>
+__device__ __forceinline__ void write_b_row(unsigned char* Bs, int row, const float (&g32)[C::NA]) {
+  using S = Split<MODE>;
+#pragma unroll
+  for (int kc = 0; kc < C::KC; ++kc) {
+    uint32_t w[S::PARTS][4];
+#pragma unroll
+    for (int j = 0; j < S::EPC; ++j) {
+      const int k = kc * S::EPC + j;
+      typename S::Store parts[3];
+      split_f32<MODE>(k < C::NA ? g32[k < C::NA ? k : 0] : 0.f, parts);
+#pragma unroll
+      for (int qq = 0; qq < S::PARTS; ++qq) {
+        if constexpr (S::BF16) {
+          if (j & 1) w[qq][j >> 1] |= uint32_t(parts[qq]) << 16;
+          else w[qq][j >> 1] = uint32_t(parts[qq]);
+        } else {
+          w[qq][j] = uint32_t(parts[qq]);
+        }
+      }
+    }
+    const uint32_t o = core_offset(row, kc * S::EPC, C::KC, S::EPC) * S::ESIZE;
+#pragma unroll
+    for (int qq = 0; qq < S::PARTS; ++qq)
+      *reinterpret_cast<uint4*>(Bs + qq * C::B_BYTES + o) = make_uint4(w[qq][0], w[qq][1], w[qq][2], w[qq][3]);
+  }
+}
+
+// G_K of cell e in FP32 (zeros past the end), from the FP64 geometry.
+template <class C, int D, int FORM, int Q>
+__device__ __forceinline__ void cell_g32(const TcParams& p, long long e, float (&g32)[C::NA]) {
+  if (e < p.n_elem) {
+    double K[D][D], det;
+    bool degenerate, bad_index;
+    cell_geometry<D>(p.cells, p.vertices, p.n_vert, e, K, det, degenerate, bad_index);
+    if (degenerate) atomicOr(p.status, FFC_FLAG_DEGENERATE);
+    if (bad_index) atomicOr(p.status, FFC_FLAG_BOUNDS);
+    double wl[FORM == FFC_NS_CONVECTION ? C::N : 1];
+    if constexpr (FORM == FFC_NS_CONVECTION) {
+      const double* w = p.coeffs + e * C::N;
+#pragma unroll
+      for (int k = 0; k < C::N; ++k) wl[k] = __ldg(w + k);
+    }
+    geometry_tensor_f32<D, FORM, Q>(K, det, wl, p.mu, p.lambda, g32);
+  } else {
+#pragma unroll
+    for (int a = 0; a < C::NA; ++a) g32[a] = 0.f;
+  }
+}
+
 template <int D, int FORM, int Q, int MODE, bool ASSEMBLE>
 __global__ void __launch_bounds__(WS_THREADS, 1) tc_ws_kernel(TcParams p) {
   using C = TcCfg<D, FORM, Q, MODE>;
   using W = TcWsCfg<D, FORM, Q, MODE>;
   using S = Split<MODE>;
-  using Store = typename S::Store;
+  // tabulate splits the epilogue warps into producers and drainers; assembly keeps all
+  // eight on both jobs (its drain is bound by atomic latency and wants every warp)
+  constexpr bool SPLIT = !ASSEMBLE;
   extern __shared__ __align__(1024) unsigned char smem[];
   unsigned char* As = smem;                              // STAGES x PARTS x A_BYTES
   unsigned char* Bs = smem + W::STAGES * W::A_TOTAL;     // PARTS x B_BYTES
@@ -517,15 +589,16 @@ __global__ void __launch_bounds__(WS_THREADS, 1) tc_ws_kernel(TcParams p) {
   const int warp = t >> 5;
   const int lane = t & 31;
   auto bar = [&](int k) { return smem_u32(&bars[k]); };
-  // 0,1 a_full  2,3 a_empty  4,5 acc_full  6,7 acc_empty  8 b_full
+  // 0,1 a_full  2,3 a_empty  4,5 acc_full  6,7 acc_empty  8 b_full  9 b_empty
   if (t == 0) {
     for (int k = 0; k < 2; ++k) {
       mbar_init(bar(0 + k), 1);
       mbar_init(bar(2 + k), 1);
       mbar_init(bar(4 + k), 1);
-      mbar_init(bar(6 + k), EPI_THREADS);
+      mbar_init(bar(6 + k), SPLIT ? ROLE_THREADS : EPI_THREADS);
     }
-    mbar_init(bar(8), EPI_THREADS);
+    mbar_init(bar(8), SPLIT ? ROLE_THREADS : EPI_THREADS);
+    mbar_init(bar(9), 1);
     abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -593,6 +666,7 @@ __global__ void __launch_bounds__(WS_THREADS, 1) tc_ws_kernel(TcParams p) {
           }
           mma_commit(bar(4 + acc));
           mma_commit(bar(2 + stage));
+          if (SPLIT && mt == C::MT - 1) mma_commit(bar(9));  // B free once this tile's MMAs complete
           // refill: the stage the previous tile used (two stages) or this one (one stage)
           if constexpr (W::STAGES == 2) {
             if (g >= 1 && g + 1 < total) {
@@ -620,43 +694,106 @@ __global__ void __launch_bounds__(WS_THREADS, 1) tc_ws_kernel(TcParams p) {
         mbar_wait(bar(2 + int(last % W::STAGES)), ph_empty[int(last % W::STAGES)] ^ 0u);
       }
     }
-  } else {
-    // ------------------------------------------------------------ epilogue warps
+  } else if (SPLIT && warp < EPI_WARPS / 2) {
+    // ------------------------------------------------------------ producers: G_K of each tile
+    uint32_t ph_b_empty = 0;
+    bool ok = true;
+    for (long long ct = 0; ct < my_tiles && ok; ++ct) {
+      float g32[C::NA];
+      cell_g32<C, D, FORM, Q>(p, (blockIdx.x + ct * gridDim.x) * N_CELLS + t, g32);
+      // the previous tile's MMAs must be done reading B before it is overwritten
+      if (ct > 0) {
+        ok = mbar_wait_or_abort(bar(9), ph_b_empty, &abort_flag);
+        ph_b_empty ^= 1;
+        if (!ok) break;
+      }
+      write_b_row<C, MODE>(Bs, t, g32);
+      fence_proxy_async();
+      mbar_arrive(bar(8));
+    }
+    if (!ok) {
+      atomicOr(p.status, FFC_FLAG_TIMEOUT);
+      abort_flag = 1;
+    }
+  } else if (SPLIT) {
+    // ------------------------------------------------------------ drainers: TMEM -> HBM
     uint32_t ph_acc_full[2] = {0, 0};
     long long g = 0;
     bool ok = true;
-    const int q4 = warp & 3;        // TMEM lane quarter
-    const int half = warp >> 2;     // column half: cells half*64 .. half*64+63
+    const int q4 = warp & 3;  // TMEM lane quarter
+    for (long long ct = 0; ct < my_tiles && ok; ++ct) {
+      const long long e0 = (blockIdx.x + ct * gridDim.x) * N_CELLS;
+      for (int mt = 0; mt < C::MT; ++mt, ++g) {
+        const int acc = int(g & 1);
+        ok = mbar_wait_or_abort(bar(4 + acc), ph_acc_full[acc], &abort_flag);
+        ph_acc_full[acc] ^= 1;
+        if (__any_sync(0xffffffffu, !ok)) {
+          ok = false;
+          break;
+        }
+        fence_after();
+        const int i = mt * M_TILE + q4 * 32 + lane;
+        const uint32_t taddr = tmem + (uint32_t(q4 * 32) << 16) + uint32_t(acc * W::ACC_COLS);
+#pragma unroll 1
+        for (int c = 0; c < N_CELLS / 32; ++c) {
+          // 32 cell columns per step: two (four with the correction accumulator) loads in
+          // flight before one wait
+          uint32_t rv[32];
+          float v[32];
+          tmem_ld16_issue(taddr + c * 32, rv);
+          tmem_ld16_issue(taddr + c * 32 + 16, rv + 16);
+          if constexpr (S::NPROD > 1) {
+            uint32_t rw[32];
+            tmem_ld16_issue(taddr + N_CELLS + c * 32, rw);
+            tmem_ld16_issue(taddr + N_CELLS + c * 32 + 16, rw + 16);
+            tmem_wait_ld();
+#pragma unroll
+            for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(rv[j]) + __uint_as_float(rw[j]);
+          } else {
+            tmem_wait_ld();
+#pragma unroll
+            for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(rv[j]);
+          }
+          if (i < C::NN) {
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+              const long long e = e0 + c * 32 + j;
+              if (e < p.n_elem) {
+                const long long o = e * C::NN + i;
+                if constexpr (ASSEMBLE) {
+                  const int s = __ldg(p.slot + o);
+                  if (s >= 0 && s < p.nnz) atomicAdd(p.csr_val + s, double(v[j]));
+                  else atomicOr(p.status, FFC_FLAG_BOUNDS);
+                } else {
+                  __stcs(p.out + o, v[j]);
+                }
+              }
+            }
+          }
+        }
+        fence_before();
+        mbar_arrive(bar(6 + acc));
+      }
+    }
+    if (!ok) {
+      if (lane == 0) atomicOr(p.status, FFC_FLAG_TIMEOUT);
+      abort_flag = 1;
+    }
+  } else {
+    // ------------------------------------------------------------ combined epilogue (assembly)
+    // warps 0..7 write the tile's B (threads 0..127, one cell each), then drain: lane
+    // quarter warp mod 4, column half warp / 4
+    uint32_t ph_acc_full[2] = {0, 0};
+    long long g = 0;
+    bool ok = true;
+    const int q4 = warp & 3;
+    const int half = warp >> 2;
     for (long long ct = 0; ct < my_tiles && ok; ++ct) {
       const long long e0 = (blockIdx.x + ct * gridDim.x) * N_CELLS;
       if (t < N_CELLS) {
-        const long long e = e0 + t;
         float g32[C::NA];
-        if (e < p.n_elem) {
-          double K[D][D], det;
-          bool degenerate, bad_index;
-          cell_geometry<D>(p.cells, p.vertices, p.n_vert, e, K, det, degenerate, bad_index);
-          if (degenerate) atomicOr(p.status, FFC_FLAG_DEGENERATE);
-          if (bad_index) atomicOr(p.status, FFC_FLAG_BOUNDS);
-          double wl[FORM == FFC_NS_CONVECTION ? C::N : 1];
-          if constexpr (FORM == FFC_NS_CONVECTION) {
-            const double* w = p.coeffs + e * C::N;
-#pragma unroll
-            for (int k = 0; k < C::N; ++k) wl[k] = __ldg(w + k);
-          }
-          geometry_tensor_f32<D, FORM, Q>(K, det, wl, p.mu, p.lambda, g32);
-        } else {
-#pragma unroll
-          for (int a = 0; a < C::NA; ++a) g32[a] = 0.f;
-        }
-#pragma unroll
-        for (int k = 0; k < C::KPAD; ++k) {
-          Store parts[3];
-          split_f32<MODE>(k < C::NA ? g32[k] : 0.f, parts);
-          const uint32_t o = core_offset(t, k, C::KC, S::EPC);
-#pragma unroll
-          for (int qq = 0; qq < S::PARTS; ++qq) reinterpret_cast<Store*>(Bs + qq * C::B_BYTES)[o] = parts[qq];
-        }
+        cell_g32<C, D, FORM, Q>(p, e0 + t, g32);
+        write_b_row<C, MODE>(Bs, t, g32);
         fence_proxy_async();
       }
       mbar_arrive(bar(8));

@@ -178,6 +178,22 @@ def test_degenerate_cell_sets_status_flag(F):
     assert F.status_poll() == 0  # poll clears
 
 
+@pytest.mark.parametrize("form", [W.POISSON, W.MASS, W.SOURCE])
+def test_degeneracy_threshold_of_a_sliver(F, form):
+    """|det J| <= 1e-14 h_max^3 flags the cell: the sliver (0,0,0), (1,0,0), (0,1,0),
+    (1/2, 1/2, eps) has det J = eps and h_max = sqrt(2), so the threshold is
+    eps = 2.83e-14; both the full geometry (J^{-1}) and the determinant-only path."""
+    import torch
+
+    fm = F.Form(form, 3, 2)
+    cells = _dev(np.array([[0, 1, 2, 3]], np.int32), torch.int32)
+    coeffs = _dev(np.ones((1, 10)), torch.float64) if form == W.SOURCE else None
+    for eps, flagged in ((1e-12, False), (4e-14, False), (2e-14, True), (1e-15, True)):
+        verts = _dev(np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [0.5, 0.5, eps]], float), torch.float64)
+        F.tabulate(fm, cells, verts, coeffs=coeffs)
+        assert bool(F.status_poll() & F.FLAG_DEGENERATE) == flagged, eps
+
+
 def test_out_of_range_slot_is_skipped_and_flagged(F):
     import torch
 
