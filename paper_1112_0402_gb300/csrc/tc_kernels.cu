@@ -5,25 +5,21 @@
 //     D[i][e] = sum_alpha A0[i][alpha] * G[e][alpha]        (M = entries i, N = cells e)
 //
 // Orientation: the MMA's M dimension runs over element-tensor entries i (128 per
-// M-tile) and N over 128 cells, so a TMEM lane holds one entry for 128 cells.
-// In the epilogue warp w reads lanes 32w..32w+31 and, for each cell, stores 32
-// consecutive entries of that cell's row-major A_K block: coalesced 128-byte stores.
+// M-tile) and N over 128 cells, so a TMEM lane holds one entry for 128 cells; a warp's
+// tcgen05.ld column is 32 consecutive entries of one cell's row-major A_K block, stored
+// as one coalesced 128-byte write.
 //
-// Per CTA (128 threads, persistent over cell tiles):
-//   1. each thread computes one cell's geometry and G_K in FP64, splits it into
-//      1-3 parts of the MMA operand type and writes them into the B tiles
-//      (canonical K-major, no-swizzle core-matrix layout);
-//   2. per M-tile, thread 0 issues bulk TMA copies of the pre-laid-out A0 tile parts
-//      into shared memory, waits on an mbarrier, issues the tcgen05.mma chain, and
-//      commits it to a second mbarrier;
-//   3. all threads wait, tcgen05.ld the accumulator and store (or atomically add)
-//      the results.
+// A0 is pre-laid-out on the host per (M-tile, K-chunk of 32) in the canonical K-major,
+// no-swizzle core-matrix layout, so one 1-D bulk copy per operand part stages a chunk;
+// a ring of up to 8 chunk stages in shared memory keeps several copies in flight ahead
+// of the MMAs. G (operand B, 128 cells x all of K) stays resident per cell tile.
+// Warp roles, the barriers and the split-precision modes are described at the kernel.
 // Split-precision modes (x = sum of parts, products summed smallest first):
 //   TF32     x ~ t1                     1 product   (kind::tf32, K-step 8)
 //   TF32X3   x ~ t1 + t2                3 products  t2*t1, t1*t2, t1*t1
 //   BF16X3   x ~ b1 + b2 + b3           6 products  b3b1, b2b2, b1b3, b2b1, b1b2, b1b1
 //                                                   (kind::f16 with BF16, K-step 16)
-// Every part is the round-to-nearest of the FP64 remainder left by the previous parts.
+// Every part is the round-to-nearest of the remainder left by the previous parts.
 // Every mbarrier wait is bounded; on expiry the kernel sets FFC_FLAG_TIMEOUT,
 // waits (bounded) for its own work in flight, frees its TMEM and returns.
 #include <cuda_bf16.h>
@@ -43,10 +39,7 @@ namespace tc {
 
 constexpr int M_TILE = 128;   // entries per M-tile (TMEM lanes)
 constexpr int N_CELLS = 128;  // cells per tile (MMA N, TMEM columns)
-constexpr int THREADS = 128;
 constexpr uint32_t WAIT_LIMIT = 1u << 24;
-
-__host__ __device__ constexpr int kpad(int na) { return (na + 7) / 8 * 8; }
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -85,34 +78,6 @@ struct Split {
 
 __host__ __device__ __forceinline__ uint32_t core_offset(int row, int k, int kc, int epc) {
   return uint32_t(((row >> 3) * kc + k / epc) * (8 * epc) + (row & 7) * epc + (k % epc));
-}
-
-__device__ __forceinline__ uint32_t tf32_bits(double x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(float(x)));
-  return r;
-}
-
-__device__ __forceinline__ uint16_t bf16_bits(double x) {
-  return __bfloat16_as_ushort(__float2bfloat16_rn(float(x)));
-}
-
-__device__ __forceinline__ double bf16_value(uint16_t b) { return double(__uint_as_float(uint32_t(b) << 16)); }
-
-// Splits x into PARTS operand values, each the rounding of the remainder left so far.
-template <int MODE>
-__device__ __forceinline__ void split_device(double x, typename Split<MODE>::Store (&out)[3]) {
-  double r = x;
-#pragma unroll
-  for (int k = 0; k < Split<MODE>::PARTS; ++k) {
-    if constexpr (Split<MODE>::BF16) {
-      out[k] = bf16_bits(r);
-      r -= bf16_value(out[k]);
-    } else {
-      out[k] = tf32_bits(r);
-      r -= double(__uint_as_float(out[k]));
-    }
-  }
 }
 
 __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
@@ -216,212 +181,59 @@ struct TcParams {
   unsigned* status;
 };
 
+constexpr int KCH = 32;  // K per staged A0 chunk
+
 template <int D, int FORM, int Q, int MODE>
 struct TcCfg {
   using S = Split<MODE>;
   static constexpr int N = nlocal(FORM, D, Q);
   static constexpr int NN = N * N;
   static constexpr int NA = nalpha(FORM, D, Q);
-  static constexpr int KPAD = (NA + S::KSTEP - 1) / S::KSTEP * S::KSTEP;
-  static constexpr int KC = KPAD / S::EPC;
+  static constexpr int KPAD = (NA + KCH - 1) / KCH * KCH;  // a whole number of chunks
+  static constexpr int KC = KPAD / S::EPC;                 // core-matrix columns of B
+  static constexpr int NCH = KPAD / KCH;                   // A0 chunks per M-tile
+  static constexpr int KCC = KCH / S::EPC;                 // core-matrix columns per chunk
   static constexpr int MT = (NN + M_TILE - 1) / M_TILE;
-  static constexpr uint32_t A_BYTES = M_TILE * KPAD * S::ESIZE;
+  static constexpr uint32_t CH_BYTES = M_TILE * KCH * S::ESIZE;  // one part of one chunk
   static constexpr uint32_t B_BYTES = N_CELLS * KPAD * S::ESIZE;
-  static constexpr size_t SMEM = size_t(S::PARTS) * (A_BYTES + B_BYTES) + 128 + 128;
 };
 
-template <int D, int FORM, int Q, int MODE, bool ASSEMBLE>
-__global__ void __launch_bounds__(THREADS, 1) tc_tabulate_kernel(TcParams p) {
-  using C = TcCfg<D, FORM, Q, MODE>;
-  using S = Split<MODE>;
-  using Store = typename S::Store;
-  extern __shared__ __align__(1024) unsigned char smem[];
-  unsigned char* As = smem;                                   // PARTS x A_BYTES
-  unsigned char* Bs = smem + S::PARTS * C::A_BYTES;           // PARTS x B_BYTES
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + S::PARTS * (C::A_BYTES + C::B_BYTES));
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 4);
-  __shared__ int abort_flag;
-
-  const int t = threadIdx.x;
-  const int warp = t >> 5;
-  const int lane = t & 31;
-  const uint32_t bar_load = smem_u32(&bars[0]);
-  const uint32_t bar_mma = smem_u32(&bars[1]);
-
-  if (t == 0) {
-    mbar_init(bar_load, 1);
-    mbar_init(bar_mma, 1);
-    abort_flag = 0;
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                 "r"(uint32_t(N_CELLS)));
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-  }
-  fence_before();
-  __syncthreads();
-  fence_after();
-  const uint32_t tmem = *tmem_slot;
-  constexpr uint32_t IDESC = S::idesc(M_TILE, N_CELLS);
-  uint32_t ph_load = 0, ph_mma = 0;
-  bool timed_out = false;
-  int pending = 0;  // thread 0: 1 = a bulk copy may still be in flight, 2 = an MMA chain may be
-
-  const long long n_tiles = (p.n_elem + N_CELLS - 1) / N_CELLS;
-  for (long long tile = blockIdx.x; tile < n_tiles && !timed_out; tile += gridDim.x) {
-    const long long e0 = tile * N_CELLS;
-    // ---- 1. geometry tensor of cell e0 + t -> B tile row t (all parts)
-    {
-      const long long e = e0 + t;
-      double g[C::NA];
-      if (e < p.n_elem) {
-        double K[D][D], det;
-        bool degenerate, bad_index;
-        cell_geometry<D>(p.cells, p.vertices, p.n_vert, e, K, det, degenerate, bad_index);
-        if (degenerate) atomicOr(p.status, FFC_FLAG_DEGENERATE);
-        if (bad_index) atomicOr(p.status, FFC_FLAG_BOUNDS);
-        double wl[FORM == FFC_NS_CONVECTION ? C::N : 1];
-        if constexpr (FORM == FFC_NS_CONVECTION) {
-          const double* w = p.coeffs + e * C::N;
-#pragma unroll
-          for (int k = 0; k < C::N; ++k) wl[k] = __ldg(w + k);
-        }
-        geometry_tensor<D, FORM, Q>(K, det, wl, p.mu, p.lambda, [&](int a, double v) { g[a] = v; });
-      } else {
-#pragma unroll
-        for (int a = 0; a < C::NA; ++a) g[a] = 0.0;
-      }
-#pragma unroll
-      for (int k = 0; k < C::KPAD; ++k) {
-        Store parts[3];
-        split_device<MODE>(k < C::NA ? g[k] : 0.0, parts);
-        const uint32_t o = core_offset(t, k, C::KC, S::EPC);
-#pragma unroll
-        for (int q = 0; q < S::PARTS; ++q) reinterpret_cast<Store*>(Bs + q * C::B_BYTES)[o] = parts[q];
-      }
-    }
-    fence_proxy_async();
-    __syncthreads();
-
-    for (int mt = 0; mt < C::MT; ++mt) {
-      // ---- 2. stage the A0 M-tile parts and run the MMA chain
-      if (t == 0) {
-        mbar_expect_tx(bar_load, S::PARTS * C::A_BYTES);
-#pragma unroll
-        for (int q = 0; q < S::PARTS; ++q)
-          bulk_g2s(smem_u32(As + q * C::A_BYTES),
-                   static_cast<const unsigned char*>(p.a0_part[q]) + size_t(mt) * C::A_BYTES, C::A_BYTES, bar_load);
-        bool ok = mbar_wait(bar_load, ph_load);
-        if (ok) {
-          fence_after();
-          constexpr uint32_t SBO = C::KC * 128;
-#pragma unroll 1
-          for (int ks = 0; ks < C::KPAD / S::KSTEP; ++ks) {
-            const uint32_t off = ks * 256;  // one K-step = two core matrices along K
-#pragma unroll
-            for (int k = 0; k < S::NPROD; ++k) {
-              const uint64_t da = smem_desc(smem_u32(As + S::pa(k) * C::A_BYTES) + off, 128, SBO);
-              const uint64_t db = smem_desc(smem_u32(Bs + S::pb(k) * C::B_BYTES) + off, 128, SBO);
-              mma<S::BF16>(tmem, da, db, IDESC, (ks > 0 || k > 0) ? 1u : 0u);
-            }
-          }
-          mma_commit(bar_mma);
-        } else {
-          atomicOr(p.status, FFC_FLAG_TIMEOUT);
-          abort_flag = 1;
-          pending = 1;
-        }
-      }
-      ph_load ^= 1;
-      __syncthreads();
-      if (abort_flag) {
-        timed_out = true;
-        break;
-      }
-      // ---- 3. wait for the accumulator, then the epilogue
-      bool ok = mbar_wait(bar_mma, ph_mma);
-      ph_mma ^= 1;
-      if (__syncthreads_or(!ok)) {
-        if (t == 0) {
-          atomicOr(p.status, FFC_FLAG_TIMEOUT);
-          pending = 2;
-        }
-        timed_out = true;
-        break;
-      }
-      fence_after();
-      const int i = mt * M_TILE + warp * 32 + lane;
-      const uint32_t taddr = tmem + (uint32_t(warp * 32) << 16);
-#pragma unroll 1
-      for (int c = 0; c < N_CELLS / 16; ++c) {
-        float v[16];
-        tmem_ld16(taddr + c * 16, v);
-        if (i < C::NN) {
-#pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            const long long e = e0 + c * 16 + j;
-            if (e < p.n_elem) {
-              const long long o = e * C::NN + i;
-              if constexpr (ASSEMBLE) {
-                const int s = __ldg(p.slot + o);
-                if (s >= 0 && s < p.nnz) atomicAdd(p.csr_val + s, double(v[j]));
-                else atomicOr(p.status, FFC_FLAG_BOUNDS);
-              } else {
-                __stcs(p.out + o, v[j]);
-              }
-            }
-          }
-        }
-      }
-      fence_before();
-      __syncthreads();
-    }
-  }
-  if (timed_out) {
-    // give the copy or MMA chain still in flight a bounded time to land before the
-    // shared memory and TMEM are released
-    if (t == 0 && pending == 1) mbar_wait(bar_load, ph_load ^ 1);
-    if (t == 0 && pending == 2) mbar_wait(bar_mma, ph_mma ^ 1);
-    __syncthreads();
-  }
-  fence_before();
-  __syncthreads();
-  if (warp == 0) {
-    fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(uint32_t(N_CELLS)));
-  }
-}
-
 // ---------------------------------------------------------------------------------
-// Warp-specialized version. Three roles:
-//   warps 0..3  producers: the geometry of the NEXT cell tile (FP64 J^{-1}, det, then
-//               G_K in FP32, one cell per thread) is computed into registers while the
-//               MMAs of the current tile still read the B buffer; once the control warp
-//               reports the buffer free (b_empty), the split parts are written to it;
-//   warps 4..7  drainers: TMEM lane quarter (warp mod 4) x all 128 cell columns, stores
-//               or atomics of the element tensor entries;
-//   warp 8      control: lane 0 issues the bulk copies of the A0 tiles and the MMAs.
+// Warp roles:
+//   warps 0..3  producers (tabulate): the geometry of the NEXT cell tile (FP64 J^{-1},
+//               det, then G_K in FP32, one cell per thread) is computed into registers
+//               while the MMAs of the current tile still read the B buffer; once the
+//               MMA warp reports the buffer free (b_empty), the split parts are written;
+//   warps 4..7  drainers (tabulate): TMEM lane quarter (warp mod 4) x all 128 cell
+//               columns, stores of the element tensor entries;
+//               (assembly: warps 0..7 both write B and drain, atomics being latency bound)
+//   warp 8      MMA: lane 0 issues the tcgen05.mma chains, one per staged A0 chunk;
+//   warp 9      TMA: lane 0 streams the A0 chunks through the stage ring.
 // The accumulator is double-buffered in TMEM (2 x 128 columns) so the MMA chain of
-// M-tile m+1 runs while the drainers store M-tile m; the A0 tiles are double-buffered
-// in shared memory when two stages fit. Barriers:
-//   a_full[s]   bulk copy of stage s landed (expect_tx)       a_empty[s]  MMAs reading stage s done
+// M-tile m+1 runs while the drainers store M-tile m. Barriers:
+//   a_full[s]   bulk copy into stage s landed (expect_tx)     a_empty[s]  MMAs reading stage s done
 //   acc_full[b] MMAs into TMEM buffer b done                   acc_empty[b] drainers emptied buffer b
 //   b_full      B tile of the current cell tile written        b_empty     MMAs reading B done
 // ---------------------------------------------------------------------------------
 constexpr int EPI_WARPS = 8;                 // producers (0..3) and drainers (4..7)
 constexpr int EPI_THREADS = EPI_WARPS * 32;
 constexpr int ROLE_THREADS = EPI_THREADS / 2;  // 128: one producer thread per cell, one drainer per TMEM lane
-constexpr int WS_THREADS = EPI_THREADS + 32;
+constexpr int MMA_WARP = EPI_WARPS, TMA_WARP = EPI_WARPS + 1;
+constexpr int WS_THREADS = EPI_THREADS + 64;
+constexpr int MAX_STAGES = 8;
 
 template <int D, int FORM, int Q, int MODE>
 struct TcWsCfg {
   using Base = TcCfg<D, FORM, Q, MODE>;
   using S = Split<MODE>;
-  static constexpr size_t A_TOTAL = size_t(S::PARTS) * Base::A_BYTES;
+  static constexpr size_t STAGE_BYTES = size_t(S::PARTS) * Base::CH_BYTES;
   static constexpr size_t B_TOTAL = size_t(S::PARTS) * Base::B_BYTES;
-  static constexpr int STAGES = (2 * A_TOTAL + B_TOTAL + 512 <= 227 * 1024) ? 2 : 1;
-  static constexpr size_t SMEM = STAGES * A_TOTAL + B_TOTAL + 256;
+  static constexpr size_t BAR_BYTES = 512;  // 2*MAX_STAGES + 6 mbarriers and the TMEM address
+  static constexpr size_t BUDGET = 227 * 1024;
+  static constexpr int FIT = int((BUDGET - B_TOTAL - BAR_BYTES) / STAGE_BYTES);
+  static constexpr int STAGES = FIT < MAX_STAGES ? FIT : MAX_STAGES;
+  static_assert(STAGES >= 2, "A0 chunk ring needs two stages");
+  static constexpr size_t SMEM = STAGES * STAGE_BYTES + B_TOTAL + BAR_BYTES;
   // TMEM columns per accumulator buffer: main (+ correction) x 128 cells
   static constexpr int ACC_COLS = S::NPROD > 1 ? 2 * N_CELLS : N_CELLS;
   static constexpr uint32_t TMEM_COLS = 2 * ACC_COLS;
@@ -579,26 +391,29 @@ __global__ void __launch_bounds__(WS_THREADS, 1) tc_ws_kernel(TcParams p) {
   // eight on both jobs (its drain is bound by atomic latency and wants every warp)
   constexpr bool SPLIT = !ASSEMBLE;
   extern __shared__ __align__(1024) unsigned char smem[];
-  unsigned char* As = smem;                              // STAGES x PARTS x A_BYTES
-  unsigned char* Bs = smem + W::STAGES * W::A_TOTAL;     // PARTS x B_BYTES
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + W::STAGES * W::A_TOTAL + W::B_TOTAL);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 12);
+  unsigned char* As = smem;                                   // STAGES x PARTS x CH_BYTES
+  unsigned char* Bs = smem + W::STAGES * W::STAGE_BYTES;      // PARTS x B_BYTES
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + W::STAGES * W::STAGE_BYTES + W::B_TOTAL);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 24);
   __shared__ int abort_flag;
+  constexpr int BAR_A_FULL = 0, BAR_A_EMPTY = MAX_STAGES, BAR_ACC_FULL = 2 * MAX_STAGES,
+                BAR_ACC_EMPTY = BAR_ACC_FULL + 2, BAR_B_FULL = BAR_ACC_EMPTY + 2, BAR_B_EMPTY = BAR_B_FULL + 1;
 
   const int t = threadIdx.x;
   const int warp = t >> 5;
   const int lane = t & 31;
   auto bar = [&](int k) { return smem_u32(&bars[k]); };
-  // 0,1 a_full  2,3 a_empty  4,5 acc_full  6,7 acc_empty  8 b_full  9 b_empty
   if (t == 0) {
-    for (int k = 0; k < 2; ++k) {
-      mbar_init(bar(0 + k), 1);
-      mbar_init(bar(2 + k), 1);
-      mbar_init(bar(4 + k), 1);
-      mbar_init(bar(6 + k), SPLIT ? ROLE_THREADS : EPI_THREADS);
+    for (int k = 0; k < W::STAGES; ++k) {
+      mbar_init(bar(BAR_A_FULL + k), 1);
+      mbar_init(bar(BAR_A_EMPTY + k), 1);
     }
-    mbar_init(bar(8), SPLIT ? ROLE_THREADS : EPI_THREADS);
-    mbar_init(bar(9), 1);
+    for (int k = 0; k < 2; ++k) {
+      mbar_init(bar(BAR_ACC_FULL + k), 1);
+      mbar_init(bar(BAR_ACC_EMPTY + k), SPLIT ? ROLE_THREADS : EPI_THREADS);
+    }
+    mbar_init(bar(BAR_B_FULL), SPLIT ? ROLE_THREADS : EPI_THREADS);
+    mbar_init(bar(BAR_B_EMPTY), 1);
     abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -614,75 +429,81 @@ __global__ void __launch_bounds__(WS_THREADS, 1) tc_ws_kernel(TcParams p) {
   const long long n_tiles = (p.n_elem + N_CELLS - 1) / N_CELLS;
   long long my_tiles = 0;
   if (blockIdx.x < n_tiles) my_tiles = (n_tiles - 1 - blockIdx.x) / gridDim.x + 1;
+  const long long total_chunks = my_tiles * C::MT * C::NCH;  // A0 chunks this CTA consumes
 
-  if (warp == EPI_WARPS) {
-    // ------------------------------------------------------------ control: TMA + MMA
+  if (warp == TMA_WARP) {
+    // ------------------------------------------------------------ TMA: A0 chunk ring
     if (lane == 0) {
-      constexpr uint32_t IDESC = S::idesc(M_TILE, N_CELLS);
-      constexpr uint32_t SBO = C::KC * 128;
-      const long long total = my_tiles * C::MT;  // A tiles this CTA consumes
-      uint32_t ph_full[2] = {0, 0}, ph_empty[2] = {0, 0}, ph_acc_empty[2] = {0, 0}, ph_b = 0;
+      uint32_t ph_empty = 0;  // bit s: phase of a_empty[s]
       bool ok = true;
-      auto load = [&](int stage, long long g) {
-        const int mt = int(g % C::MT);
-        mbar_expect_tx(bar(0 + stage), uint32_t(W::A_TOTAL));
+      for (long long g = 0; g < total_chunks && ok; ++g) {
+        const int s = int(g % W::STAGES);
+        if (g >= W::STAGES) {
+          ok = mbar_wait_or_abort(bar(BAR_A_EMPTY + s), (ph_empty >> s) & 1u, &abort_flag);
+          ph_empty ^= 1u << s;
+          if (!ok) break;
+        }
+        const long long mc = g % (long long)(C::MT * C::NCH);  // (M-tile, chunk) of this cell tile
+        mbar_expect_tx(bar(BAR_A_FULL + s), uint32_t(W::STAGE_BYTES));
 #pragma unroll
         for (int q = 0; q < S::PARTS; ++q)
-          bulk_g2s(smem_u32(As + stage * W::A_TOTAL + q * C::A_BYTES),
-                   static_cast<const unsigned char*>(p.a0_part[q]) + size_t(mt) * C::A_BYTES, C::A_BYTES,
-                   bar(0 + stage));
-      };
-      for (int st = 0; st < W::STAGES && st < total; ++st) load(st, st);
-      long long g = 0;
+          bulk_g2s(smem_u32(As + s * W::STAGE_BYTES + q * C::CH_BYTES),
+                   static_cast<const unsigned char*>(p.a0_part[q]) + size_t(mc) * C::CH_BYTES, C::CH_BYTES,
+                   bar(BAR_A_FULL + s));
+      }
+      if (!ok) {
+        atomicOr(p.status, FFC_FLAG_TIMEOUT);
+        abort_flag = 1;
+      }
+    }
+  } else if (warp == MMA_WARP) {
+    // ------------------------------------------------------------ MMA issue
+    if (lane == 0) {
+      constexpr uint32_t IDESC = S::idesc(M_TILE, N_CELLS);
+      constexpr uint32_t SBO_A = C::KCC * 128;  // chunk: row groups of KCC core matrices
+      constexpr uint32_t SBO_B = C::KC * 128;   // B: row groups of all KC core matrices
+      constexpr int KS_PER_CH = KCH / S::KSTEP;
+      uint32_t ph_full = 0, ph_acc_empty = 0, ph_b = 0;
+      bool ok = true;
+      long long g = 0, gm = 0;  // chunks and M-tiles consumed
       for (long long ct = 0; ct < my_tiles && ok; ++ct) {
-        ok = mbar_wait_or_abort(bar(8), ph_b, &abort_flag);
+        ok = mbar_wait_or_abort(bar(BAR_B_FULL), ph_b, &abort_flag);
         ph_b ^= 1;
-        for (int mt = 0; mt < C::MT && ok; ++mt, ++g) {
-          const int stage = int(g % W::STAGES);
-          const int acc = int(g & 1);
-          ok = mbar_wait_or_abort(bar(0 + stage), ph_full[stage], &abort_flag);
-          ph_full[stage] ^= 1;
-          if (ok && g >= 2) {
-            ok = mbar_wait_or_abort(bar(6 + acc), ph_acc_empty[acc], &abort_flag);
-            ph_acc_empty[acc] ^= 1;
+        for (int mt = 0; mt < C::MT && ok; ++mt, ++gm) {
+          const int acc = int(gm & 1);
+          if (gm >= 2) {
+            ok = mbar_wait_or_abort(bar(BAR_ACC_EMPTY + acc), (ph_acc_empty >> acc) & 1u, &abort_flag);
+            ph_acc_empty ^= 1u << acc;
+            if (!ok) break;
           }
-          if (!ok) break;
-          fence_after();
           // main product (part 0 x part 0) and the correction products accumulate
           // separately; the epilogue adds them once
           const uint32_t d_main = tmem + uint32_t(acc * W::ACC_COLS);
           const uint32_t d_corr = d_main + uint32_t(N_CELLS);
-#pragma unroll 1
-          for (int ks = 0; ks < C::KPAD / S::KSTEP; ++ks) {
-            const uint32_t off = ks * 256;
+          for (int ch = 0; ch < C::NCH; ++ch, ++g) {
+            const int s = int(g % W::STAGES);
+            ok = mbar_wait_or_abort(bar(BAR_A_FULL + s), (ph_full >> s) & 1u, &abort_flag);
+            ph_full ^= 1u << s;
+            if (!ok) break;
+            fence_after();
 #pragma unroll
-            for (int k = 0; k < S::NPROD; ++k) {
-              const uint64_t da =
-                  smem_desc(smem_u32(As + stage * W::A_TOTAL + S::pa(k) * C::A_BYTES) + off, 128, SBO);
-              const uint64_t db = smem_desc(smem_u32(Bs + S::pb(k) * C::B_BYTES) + off, 128, SBO);
-              if (k == S::NPROD - 1) mma<S::BF16>(d_main, da, db, IDESC, ks > 0 ? 1u : 0u);
-              else mma<S::BF16>(d_corr, da, db, IDESC, (ks > 0 || k > 0) ? 1u : 0u);
+            for (int ksl = 0; ksl < KS_PER_CH; ++ksl) {
+              const int ks = ch * KS_PER_CH + ksl;
+#pragma unroll
+              for (int k = 0; k < S::NPROD; ++k) {
+                const uint64_t da =
+                    smem_desc(smem_u32(As + s * W::STAGE_BYTES + S::pa(k) * C::CH_BYTES) + ksl * 256, 128, SBO_A);
+                const uint64_t db = smem_desc(smem_u32(Bs + S::pb(k) * C::B_BYTES) + ks * 256, 128, SBO_B);
+                if (k == S::NPROD - 1) mma<S::BF16>(d_main, da, db, IDESC, ks > 0 ? 1u : 0u);
+                else mma<S::BF16>(d_corr, da, db, IDESC, (ks > 0 || k > 0) ? 1u : 0u);
+              }
             }
+            mma_commit(bar(BAR_A_EMPTY + s));  // the stage is free once these MMAs complete
           }
-          mma_commit(bar(4 + acc));
-          mma_commit(bar(2 + stage));
-          if (SPLIT && mt == C::MT - 1) mma_commit(bar(9));  // B free once this tile's MMAs complete
-          // refill: the stage the previous tile used (two stages) or this one (one stage)
-          if constexpr (W::STAGES == 2) {
-            if (g >= 1 && g + 1 < total) {
-              const int ps = int((g - 1) % 2);
-              ok = mbar_wait_or_abort(bar(2 + ps), ph_empty[ps], &abort_flag);
-              ph_empty[ps] ^= 1;
-              if (ok) load(ps, g + 1);
-            }
-          } else {
-            if (g + 1 < total) {
-              ok = mbar_wait_or_abort(bar(2), ph_empty[0], &abort_flag);
-              ph_empty[0] ^= 1;
-              if (ok) load(0, g + 1);
-            }
-          }
+          if (!ok) break;
+          mma_commit(bar(BAR_ACC_FULL + acc));
         }
+        if (ok && SPLIT) mma_commit(bar(BAR_B_EMPTY));  // B free once this tile's MMAs complete
       }
       if (!ok) {
         atomicOr(p.status, FFC_FLAG_TIMEOUT);
@@ -690,8 +511,8 @@ __global__ void __launch_bounds__(WS_THREADS, 1) tc_ws_kernel(TcParams p) {
       }
       // let the last MMA chain finish before TMEM is released (bounded)
       if (g > 0) {
-        const long long last = g - 1;
-        mbar_wait(bar(2 + int(last % W::STAGES)), ph_empty[int(last % W::STAGES)] ^ 0u);
+        const int s = int((g - 1) % W::STAGES);
+        mbar_wait(bar(BAR_A_EMPTY + s), ((g - 1) / W::STAGES) & 1);
       }
     }
   } else if (SPLIT && warp < EPI_WARPS / 2) {
@@ -703,13 +524,13 @@ __global__ void __launch_bounds__(WS_THREADS, 1) tc_ws_kernel(TcParams p) {
       cell_g32<C, D, FORM, Q>(p, (blockIdx.x + ct * gridDim.x) * N_CELLS + t, g32);
       // the previous tile's MMAs must be done reading B before it is overwritten
       if (ct > 0) {
-        ok = mbar_wait_or_abort(bar(9), ph_b_empty, &abort_flag);
+        ok = mbar_wait_or_abort(bar(BAR_B_EMPTY), ph_b_empty, &abort_flag);
         ph_b_empty ^= 1;
         if (!ok) break;
       }
       write_b_row<C, MODE>(Bs, t, g32);
       fence_proxy_async();
-      mbar_arrive(bar(8));
+      mbar_arrive(bar(BAR_B_FULL));
     }
     if (!ok) {
       atomicOr(p.status, FFC_FLAG_TIMEOUT);
@@ -725,7 +546,7 @@ __global__ void __launch_bounds__(WS_THREADS, 1) tc_ws_kernel(TcParams p) {
       const long long e0 = (blockIdx.x + ct * gridDim.x) * N_CELLS;
       for (int mt = 0; mt < C::MT; ++mt, ++g) {
         const int acc = int(g & 1);
-        ok = mbar_wait_or_abort(bar(4 + acc), ph_acc_full[acc], &abort_flag);
+        ok = mbar_wait_or_abort(bar(BAR_ACC_FULL + acc), ph_acc_full[acc], &abort_flag);
         ph_acc_full[acc] ^= 1;
         if (__any_sync(0xffffffffu, !ok)) {
           ok = false;
@@ -772,7 +593,7 @@ __global__ void __launch_bounds__(WS_THREADS, 1) tc_ws_kernel(TcParams p) {
           }
         }
         fence_before();
-        mbar_arrive(bar(6 + acc));
+        mbar_arrive(bar(BAR_ACC_EMPTY + acc));
       }
     }
     if (!ok) {
@@ -796,10 +617,10 @@ __global__ void __launch_bounds__(WS_THREADS, 1) tc_ws_kernel(TcParams p) {
         write_b_row<C, MODE>(Bs, t, g32);
         fence_proxy_async();
       }
-      mbar_arrive(bar(8));
+      mbar_arrive(bar(BAR_B_FULL));
       for (int mt = 0; mt < C::MT; ++mt, ++g) {
         const int acc = int(g & 1);
-        ok = mbar_wait_or_abort(bar(4 + acc), ph_acc_full[acc], &abort_flag);
+        ok = mbar_wait_or_abort(bar(BAR_ACC_FULL + acc), ph_acc_full[acc], &abort_flag);
         ph_acc_full[acc] ^= 1;
         if (__any_sync(0xffffffffu, !ok)) {
           ok = false;
@@ -836,7 +657,7 @@ __global__ void __launch_bounds__(WS_THREADS, 1) tc_ws_kernel(TcParams p) {
           }
         }
         fence_before();
-        mbar_arrive(bar(6 + acc));
+        mbar_arrive(bar(BAR_ACC_EMPTY + acc));
       }
     }
     if (!ok) {
@@ -881,13 +702,14 @@ int upload_parts(ffc_form* f, DeviceTensors* t) {
   const int fam = S::BF16 ? 1 : 0;
   std::lock_guard<std::mutex> g(f->lock);
   if (t->tc_part[fam][S::PARTS - 1] && t->tc_kpad[fam] == C::KPAD) return FFC_OK;
-  const size_t per = size_t(C::MT) * M_TILE * C::KPAD;  // elements per part
+  const size_t per = size_t(C::MT) * M_TILE * C::KPAD;  // elements per part: [MT][NCH][128 x KCH] chunks
   const int nparts = S::BF16 ? 3 : 2;                    // a family uploads all its parts once
   std::vector<std::vector<typename S::Store>> parts(nparts, std::vector<typename S::Store>(per, 0));
   for (int i = 0; i < C::NN; ++i)
     for (int k = 0; k < C::NA; ++k) {
       double r = f->A0[size_t(i) * C::NA + k];
-      const size_t o = size_t(i / M_TILE) * M_TILE * C::KPAD + core_offset(i % M_TILE, k, C::KC, S::EPC);
+      const size_t o = (size_t(i / M_TILE) * C::NCH + k / KCH) * (M_TILE * KCH) +
+                       core_offset(i % M_TILE, k % KCH, C::KCC, S::EPC);
       for (int q = 0; q < nparts; ++q) {
         if constexpr (S::BF16) {
           const uint16_t b = host_bf16_bits(r);
