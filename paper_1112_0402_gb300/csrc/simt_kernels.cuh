@@ -65,8 +65,8 @@ struct SimtParams {
 };
 
 template <typename OutT>
-__device__ __forceinline__ void put(OutT* p, double v) {
-  __stcs(p, OutT(v));
+__device__ __forceinline__ void put(OutT* p, OutT v) {
+  __stcs(p, v);
 }
 
 // Loads the thread's rows of the reference tensor into registers (register path).
@@ -172,7 +172,7 @@ __device__ __forceinline__ void simt_tile(const SimtParams& p, long long tile, u
               if (s >= 0 && s < p.nnz) atomicAdd(p.csr_val + s, double(acc[r]));
               else atomicOr(p.status, FFC_FLAG_BOUNDS);
             } else {
-              put(static_cast<OutT*>(p.out) + o, double(acc[r]));
+              put(static_cast<OutT*>(p.out) + o, acc[r]);
             }
           }
         }
@@ -217,7 +217,7 @@ __device__ __forceinline__ void simt_tile(const SimtParams& p, long long tile, u
               if (s >= 0 && s < p.nnz) atomicAdd(p.csr_val + s, double(acc[k]));
               else atomicOr(p.status, FFC_FLAG_BOUNDS);
             } else {
-              put(static_cast<OutT*>(p.out) + o, double(acc[k]));
+              put(static_cast<OutT*>(p.out) + o, acc[k]);
             }
           }
         }

@@ -188,3 +188,52 @@ def test_source_full_size_p4(F):
         assert F.status_poll() == 0
         assert abs(b.sum().item() - int_f) <= tol
         assert abs((b @ Xd).item() - int_xf) <= tol
+
+
+def _conversion_cases():
+    """Doubles that exercise FP64 -> FP32 round-to-nearest-even: a wide exponent range
+    (normal, subnormal and overflowing FP32 results), exact ties with even and odd kept
+    fractions, one unit either side of a tie, the largest finite FP32 value and its
+    rounding boundary, signed zeros, infinities, NaN."""
+    rng = np.random.default_rng(7)
+    xs = list(rng.standard_normal(3000) * 10.0 ** rng.uniform(-50, 50, 3000))
+    for _ in range(400):
+        e = int(rng.integers(897, 1151))
+        frac = int(rng.integers(0, 1 << 23))
+        for low in (0x10000000, 0x10000001, 0x0FFFFFFF, 0, 0x1FFFFFFF):
+            bits = (int(rng.integers(0, 2)) << 63) | (e << 52) | (frac << 29) | low
+            xs.append(np.array([bits], dtype=np.uint64).view(np.float64)[0])
+    fmax = float(np.finfo(np.float32).max)
+    half_ulp = 2.0 ** (127 - 24)
+    xs += [fmax, -fmax, fmax + half_ulp, fmax + half_ulp * (1 - 2 ** -30), 2.0 ** -126, 2.0 ** -126 * (1 - 2 ** -40),
+           2.0 ** -149, 2.0 ** -150, 3e-46, 0.0, -0.0, np.inf, -np.inf, np.nan, 1.0, -1.0, 1e300, -1e-300]
+    return np.array(xs, dtype=np.float64)
+
+
+def test_fp32_source_arithmetic_is_exact_ieee(F):
+    """The FP32 source kernel rounds f to FP32, multiplies in FP32 and accumulates in FP64.
+    On the reference tetrahedron (det J = 1) with f = (x, 0, 0, 0) and one cell per dof
+    block, b[4c] = f64(RN32(RN32(x) * RN32(A0[0][0]))) for every x, ties, overflow,
+    subnormal results, signed zeros, infinities and NaN included, which numpy reproduces
+    exactly in IEEE float32 arithmetic."""
+    import torch
+
+    xs = _conversion_cases()
+    n = xs.size
+    form = F.Form(F.SOURCE, F.TETRAHEDRON, 1)
+    a00 = np.float32(form.reference_tensor()[0, 0])
+    cells = torch.zeros((n, 4), dtype=torch.int32, device="cuda") + torch.arange(4, dtype=torch.int32, device="cuda")
+    verts = _dev(np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1]], float), torch.float64)
+    f = np.zeros((n, 4))
+    f[:, 0] = xs
+    dm = _dev(np.arange(4 * n, dtype=np.int32).reshape(n, 4), torch.int32)
+    b = torch.zeros(4 * n, dtype=torch.float64, device="cuda")
+    with np.errstate(over="ignore", invalid="ignore"):
+        want = (xs.astype(np.float32) * a00).astype(np.float64)
+    F.assemble(form, cells, verts, dm, b, coeffs=_dev(f, torch.float64), precision="fp32")
+    bt = F.tabulate(form, cells, verts, coeffs=_dev(f, torch.float64), precision="fp32")
+    F.status_poll()
+    got = b.cpu().numpy()[0::4]
+    assert np.array_equal(got, want, equal_nan=True)
+    with np.errstate(over="ignore", invalid="ignore"):
+        assert np.array_equal(bt.cpu().numpy()[:, 0], want.astype(np.float32), equal_nan=True)
