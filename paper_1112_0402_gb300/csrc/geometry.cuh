@@ -136,7 +136,7 @@ __device__ __forceinline__ void cell_geometry(const int32_t* __restrict__ cells,
   degenerate = degenerate_test<D>(J, det);
 }
 
-// |det J| alone (forms whose geometry tensor needs no J^{-1}: the source form), with the
+// |det J| alone (forms whose geometry tensor needs no J^{-1}: mass and source), with the
 // same degeneracy test as cell_geometry.
 template <int D>
 __device__ __forceinline__ void cell_det(const int32_t* __restrict__ cells, const double* __restrict__ vertices,

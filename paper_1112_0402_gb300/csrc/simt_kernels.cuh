@@ -40,7 +40,9 @@ struct SimtCfg {
   // register-resident reference tensor rows; a shared block size (several forms in one
   // kernel) keeps it only for small |alpha| so the kernel's register count stays low
   static constexpr bool REG_A0 = (R * NA * int(sizeof(T)) / 4) <= (BLOCK > 0 ? 32 : 96);
-  static constexpr int KE_TARGET = KE_T > 0 ? KE_T : (REG_A0 ? 64 : 16);
+  // cells per thread group and tile (register path: 64, or 32 for element tensors above
+  // 512 entries, whose single thread group per CTA spends longer between the barriers)
+  static constexpr int KE_TARGET = KE_T > 0 ? KE_T : (REG_A0 ? (R > 1 ? 32 : 64) : 16);
   static constexpr int KE = (KE_TARGET + EG - 1) / EG;
   static constexpr int E = EG * KE;
   static constexpr int NCOEF = (FORM == FFC_NS_CONVECTION) ? N : 0;
@@ -108,9 +110,13 @@ __device__ __forceinline__ void simt_tile(const SimtParams& p, long long tile, u
       const long long e = e0 + el;
       T* g = Gs + el * C::NAP;
       if (e < p.n_elem) {
-        double K[D][D], det;
+        double K[D][D] = {}, det;
         bool degenerate, bad_index;
-        cell_geometry<D>(p.cells, p.vertices, p.n_vert, e, K, det, degenerate, bad_index);
+        if constexpr (FORM == FFC_MASS) {  // G = |det J|: no inverse needed
+          cell_det<D>(p.cells, p.vertices, p.n_vert, e, det, degenerate, bad_index);
+        } else {
+          cell_geometry<D>(p.cells, p.vertices, p.n_vert, e, K, det, degenerate, bad_index);
+        }
         if (degenerate) atomicOr(p.status, FFC_FLAG_DEGENERATE);
         if (bad_index) atomicOr(p.status, FFC_FLAG_BOUNDS);
         geometry_tensor_k<D, FORM, Q>(K, det, Ws + el * C::NCOEF, p.mu, p.lambda,

@@ -364,9 +364,13 @@ __device__ __forceinline__ void write_b_row(unsigned char* Bs, int row, const fl
 template <class C, int D, int FORM, int Q>
 __device__ __forceinline__ void cell_g32(const TcParams& p, long long e, float (&g32)[C::NA]) {
   if (e < p.n_elem) {
-    double K[D][D], det;
+    double K[D][D] = {}, det;
     bool degenerate, bad_index;
-    cell_geometry<D>(p.cells, p.vertices, p.n_vert, e, K, det, degenerate, bad_index);
+    if constexpr (FORM == FFC_MASS) {  // G = |det J|: no inverse needed
+      cell_det<D>(p.cells, p.vertices, p.n_vert, e, det, degenerate, bad_index);
+    } else {
+      cell_geometry<D>(p.cells, p.vertices, p.n_vert, e, K, det, degenerate, bad_index);
+    }
     if (degenerate) atomicOr(p.status, FFC_FLAG_DEGENERATE);
     if (bad_index) atomicOr(p.status, FFC_FLAG_BOUNDS);
     double wl[FORM == FFC_NS_CONVECTION ? C::N : 1];
