@@ -65,11 +65,14 @@ typedef enum {
 
 typedef enum { FFC_TRIANGLE = 2, FFC_TETRAHEDRON = 3 } ffc_cell; /* value = spatial dimension d */
 
-/* Arithmetic of the contraction A0 : G. J, det J and J^{-1} are always FP64. G_K is
- * formed from them in FP64 and rounded once for the dense CUDA-core contraction, and in
- * the contraction's own type for the block algorithm (FFC_ALG_BLOCK: FP32 products for
- * FFC_FP32) and in FP32 for the tensor-core precisions, which round it to their operand
- * parts. FP64 is the CSR accumulation type of ffc_assemble. Tensor-core precisions are built for tetrahedra: convection P2,
+/* Arithmetic of the contraction A0 : G. J, its cofactors (adjugate) and det J are always
+ * FP64: that is where a near-degenerate cell cancels. For FFC_FP64 the inverse
+ * K = adj(J) / det J and G_K are FP64. For FFC_FP32 and the tensor-core precisions G_K
+ * is formed in FP32, the type it is rounded to anyway (the tensor cores further split it
+ * into operand parts): the dense kernels form K in FP32 from the FP64 adjugate and
+ * determinant (a well-conditioned step; cells with |det J| outside [1e-30, 1e30] divide
+ * in FP64), the block algorithm takes an FP64 K. FP64 is the CSR accumulation type of
+ * ffc_assemble. Tensor-core precisions are built for tetrahedra: convection P2,
  * elasticity P1-P3, Poisson P2-P4, mass P3-P4 (others, and every linear form, return
  * FFC_EUNSUPPORTED). */
 typedef enum {

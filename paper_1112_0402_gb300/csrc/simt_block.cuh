@@ -116,10 +116,13 @@ __device__ __forceinline__ void block_tile(const SimtParams& p, long long tile, 
     for (int k = t; k < C::E * C::NCOEF; k += C::NT) Ws[k] = (k < lim) ? __ldg(src + k) : 0.0;
   }
   __syncthreads();
-  // ---- reduced geometry blocks of the tile's cells (J^{-1}, det J in FP64)
+  // ---- reduced geometry blocks of the tile's cells
   for (int el = t; el < C::E; el += C::NT) {
     const long long e = e0 + el;
     T* g = Gs + size_t(el) * C::NB * C::KRP;
+    // J^{-1} and det J in FP64 (measured: forming J^{-1} in FP32 from the FP64 adjugate,
+    // as the dense kernels do, made this tile slower); the reduced geometry blocks, their
+    // products with the coefficients, in the contraction's type (rounded to it anyway)
     double K[D][D] = {}, det = 0.0;
     bool live = e < p.n_elem;
     if (live) {
@@ -128,9 +131,6 @@ __device__ __forceinline__ void block_tile(const SimtParams& p, long long tile, 
       if (degenerate) atomicOr(p.status, FFC_FLAG_DEGENERATE);
       if (bad_index) atomicOr(p.status, FFC_FLAG_BOUNDS);
     }
-    // the reduced geometry blocks are products of J^{-1} and det J with the coefficients;
-    // for an FP32 contraction they are formed in FP32 (they are rounded to FP32 anyway),
-    // for FP64 in FP64
     using GT = T;
     GT Kt[D][D], dett = GT(det);
 #pragma unroll

@@ -111,17 +111,24 @@ __device__ __forceinline__ void simt_tile(const SimtParams& p, long long tile, u
       const long long e = e0 + el;
       T* g = Gs + el * C::NAP;
       if (e < p.n_elem) {
-        double K[D][D] = {}, det;
         bool degenerate, bad_index;
-        if constexpr (FORM == FFC_MASS) {  // G = |det J|: no inverse needed
-          cell_det<D>(p.cells, p.vertices, p.n_vert, e, det, degenerate, bad_index);
+        if constexpr (sizeof(T) == 4 && FORM != FFC_MASS) {
+          // FP32 contraction: FP64 J, adj(J), det J; K and G_K in FP32
+          float K[D][D], det;
+          cell_geometry_f32<D>(p.cells, p.vertices, p.n_vert, e, K, det, degenerate, bad_index);
+          geometry_tensor_f32<D, FORM, Q, true>(K, det, Ws + el * C::NCOEF, p.mu, p.lambda, g);
         } else {
-          cell_geometry<D>(p.cells, p.vertices, p.n_vert, e, K, det, degenerate, bad_index);
+          double K[D][D] = {}, det;
+          if constexpr (FORM == FFC_MASS) {  // G = |det J|: no inverse needed
+            cell_det<D>(p.cells, p.vertices, p.n_vert, e, det, degenerate, bad_index);
+          } else {
+            cell_geometry<D>(p.cells, p.vertices, p.n_vert, e, K, det, degenerate, bad_index);
+          }
+          geometry_tensor_k<D, FORM, Q>(K, det, Ws + el * C::NCOEF, p.mu, p.lambda,
+                                      [&](int a, double v) { g[a] = T(v); });
         }
         if (degenerate) atomicOr(p.status, FFC_FLAG_DEGENERATE);
         if (bad_index) atomicOr(p.status, FFC_FLAG_BOUNDS);
-        geometry_tensor_k<D, FORM, Q>(K, det, Ws + el * C::NCOEF, p.mu, p.lambda,
-                                    [&](int a, double v) { g[a] = T(v); });
       } else {
 #pragma unroll 1
         for (int a = 0; a < C::NA; ++a) g[a] = T(0);

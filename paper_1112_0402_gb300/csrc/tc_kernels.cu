@@ -252,67 +252,6 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
-// G_K in FP32 from the FP64 geometry (K = J^{-1}, |det J|): the tensor-core paths
-// round G to the operand parts anyway, so only J, its inverse and determinant keep FP64.
-template <int D, int FORM, int Q>
-__device__ __forceinline__ void geometry_tensor_f32(const double Kd[D][D], double det, const double* w, double mu,
-                                                    double lambda, float* g) {
-  float K[D][D];
-#pragma unroll
-  for (int a = 0; a < D; ++a)
-#pragma unroll
-    for (int b = 0; b < D; ++b) K[a][b] = float(Kd[a][b]);
-  const float detf = float(det);
-  if constexpr (FORM == FFC_MASS) {
-    g[0] = detf;
-  } else if constexpr (FORM == FFC_POISSON) {
-#pragma unroll
-    for (int a1 = 0; a1 < D; ++a1)
-#pragma unroll
-      for (int a2 = 0; a2 < D; ++a2) {
-        float s = 0.f;
-#pragma unroll
-        for (int b = 0; b < D; ++b) s = fmaf(K[a1][b], K[a2][b], s);
-        g[a1 * D + a2] = detf * s;
-      }
-  } else if constexpr (FORM == FFC_NS_CONVECTION) {
-    constexpr int NS = nscalar(D, Q);
-#pragma unroll
-    for (int ct = 0; ct < D; ++ct)
-#pragma unroll
-      for (int st = 0; st < NS; ++st) {
-        const int t = ct * NS + st;
-        const float dw = float(det * w[t]);
-#pragma unroll
-        for (int a = 0; a < D; ++a) g[t * D + a] = dw * K[a][ct];
-      }
-  } else {
-    float KK[D][D];
-#pragma unroll
-    for (int a1 = 0; a1 < D; ++a1)
-#pragma unroll
-      for (int a2 = 0; a2 < D; ++a2) {
-        float s = 0.f;
-#pragma unroll
-        for (int b = 0; b < D; ++b) s = fmaf(K[a1][b], K[a2][b], s);
-        KK[a1][a2] = s;
-      }
-    const float muf = float(mu), lf = float(lambda);
-#pragma unroll
-    for (int b1 = 0; b1 < D; ++b1)
-#pragma unroll
-      for (int b2 = 0; b2 < D; ++b2)
-#pragma unroll
-        for (int a1 = 0; a1 < D; ++a1)
-#pragma unroll
-          for (int a2 = 0; a2 < D; ++a2) {
-            float v = muf * K[a1][b2] * K[a2][b1] + lf * K[a1][b1] * K[a2][b2];
-            if (b1 == b2) v += muf * KK[a1][a2];
-            g[((b1 * D + b2) * D + a1) * D + a2] = detf * v;
-          }
-  }
-}
-
 template <int MODE>
 __device__ __forceinline__ void split_f32(float x, typename Split<MODE>::Store (&out)[3]) {
   float r = x;
@@ -364,22 +303,19 @@ __device__ __forceinline__ void write_b_row(unsigned char* Bs, int row, const fl
 template <class C, int D, int FORM, int Q>
 __device__ __forceinline__ void cell_g32(const TcParams& p, long long e, float (&g32)[C::NA]) {
   if (e < p.n_elem) {
-    double K[D][D] = {}, det;
+    float K[D][D] = {}, det;
     bool degenerate, bad_index;
     if constexpr (FORM == FFC_MASS) {  // G = |det J|: no inverse needed
-      cell_det<D>(p.cells, p.vertices, p.n_vert, e, det, degenerate, bad_index);
+      double d64;
+      cell_det<D>(p.cells, p.vertices, p.n_vert, e, d64, degenerate, bad_index);
+      det = float(d64);
     } else {
-      cell_geometry<D>(p.cells, p.vertices, p.n_vert, e, K, det, degenerate, bad_index);
+      cell_geometry_f32<D>(p.cells, p.vertices, p.n_vert, e, K, det, degenerate, bad_index);
     }
     if (degenerate) atomicOr(p.status, FFC_FLAG_DEGENERATE);
     if (bad_index) atomicOr(p.status, FFC_FLAG_BOUNDS);
-    double wl[FORM == FFC_NS_CONVECTION ? C::N : 1];
-    if constexpr (FORM == FFC_NS_CONVECTION) {
-      const double* w = p.coeffs + e * C::N;
-#pragma unroll
-      for (int k = 0; k < C::N; ++k) wl[k] = __ldg(w + k);
-    }
-    geometry_tensor_f32<D, FORM, Q>(K, det, wl, p.mu, p.lambda, g32);
+    const double* w = FORM == FFC_NS_CONVECTION ? p.coeffs + e * C::N : nullptr;
+    geometry_tensor_f32<D, FORM, Q, false>(K, det, w, p.mu, p.lambda, g32);
   } else {
 #pragma unroll
     for (int a = 0; a < C::NA; ++a) g32[a] = 0.f;
