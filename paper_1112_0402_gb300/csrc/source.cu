@@ -49,8 +49,9 @@ struct SourceCfg {
   static constexpr size_t SMEM = size_t(TC) * NP * sizeof(T) + size_t(TC) * sizeof(T);
 };
 
+// four resident CTAs per SM for FP32 (64 registers), two for FP64
 template <int D, int Q, typename T, bool ASSEMBLE>
-__global__ void __launch_bounds__(256) source_kernel(SourceParams p) {
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) source_kernel(SourceParams p) {
   using C = SourceCfg<D, Q, T>;
   using V = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
   constexpr int N = C::N, NP = C::NP, TC = C::TC;
