@@ -471,23 +471,30 @@ def measure_detail(F, ctx, args, device, reps=5):
         torch.cuda.synchronize()
         rec["assemble_fp64_ms"] = a.elapsed_time(b) / reps
         if pr["q"] == 4:
-            # reference point: a plain atomic scatter of precomputed values into the same
-            # slots (torch index_add_), i.e. the insertion alone without any contraction
-            A = torch.empty((n_elem, n, n), dtype=torch.float64, device=device)
-            F.tabulate(pr["F"], ctx["cells"], ctx["verts"], out=A, precision="fp64")
-            idx = pr["slot"].reshape(-1).to(torch.int64)
-            flat = A.reshape(-1)
+            # the insertion alone (Algorithm 2's add of precomputed element tensors into the
+            # same slots, ffc_scatter_add, FP32 values and FP64 atomics as in the fused
+            # step), zeroing included as in the fused timing: the atomic ceiling of this
+            # slot pattern
+            A = torch.empty((n_elem, n, n), dtype=torch.float32, device=device)
+            F.tabulate(pr["F"], ctx["cells"], ctx["verts"], out=A, precision="fp32")
             pr["val"].zero_()
-            pr["val"].index_add_(0, idx, flat)
+            F.scatter_add(A, pr["slot"], pr["val"])
             torch.cuda.synchronize()
             a.record()
             for _ in range(3):
                 pr["val"].zero_()
-                pr["val"].index_add_(0, idx, flat)
+                F.scatter_add(A, pr["slot"], pr["val"])
             b.record()
             torch.cuda.synchronize()
-            rec["scatter_only_index_add_ms"] = a.elapsed_time(b) / 3
-            del A, idx, flat
+            rec["scatter_only_ms"] = a.elapsed_time(b) / 3
+            a.record()
+            for _ in range(3):
+                pr["val"].zero_()
+                F.assemble(pr["F"], ctx["cells"], ctx["verts"], pr["slot"], pr["val"], precision="fp32")
+            b.record()
+            torch.cuda.synchronize()
+            rec["assemble_fp32_with_zero_ms"] = a.elapsed_time(b) / 3
+            del A
             torch.cuda.empty_cache()
         out[key] = rec
     assert F.status_poll() == 0

@@ -145,6 +145,8 @@ void ffc_form_destroy(ffc_form* f);
  *   precision ffc_precision
  * n_elem == 0 launches nothing and returns FFC_OK. A vertex id outside
  * [0, n_vert) is replaced by 0 and sets FFC_FLAG_BOUNDS (never read out of range).
+ * Callers holding per-cell (gathered) vertex coordinates [n_elem][d+1][d] pass them as
+ * `vertices` with n_vert = n_elem*(d+1) and cells[e] = {(d+1)e, ..., (d+1)e+d}.
  */
 int ffc_tabulate(const ffc_form* f, int64_t n_elem, const int32_t* cells, const double* vertices,
                  int64_t n_vert, const double* coeffs, void* A_K, int precision, void* stream);
@@ -181,6 +183,22 @@ int ffc_csr_pattern(int64_t n_elem, int n_local, const int32_t* dofmap, int64_t 
 int ffc_assemble(const ffc_form* f, int64_t n_elem, const int32_t* cells, const double* vertices,
                  int64_t n_vert, const double* coeffs, const int32_t* slot, double* csr_val, int64_t nnz,
                  int precision, void* stream);
+
+/*
+ * ffc_scatter_add -- the insertion step of Algorithm 2 (Section 2.2) on its own: adds
+ * precomputed element tensors into the CSR values,
+ *   csr_val[slot[e][i]] += A_K[e][i]     for e < n_elem, i < n_entries (FP64 atomic adds).
+ *   A_K        device [n_elem][n_entries], double (precision FFC_FP64) or float
+ *              (FFC_FP32), e.g. from ffc_tabulate: n_entries = n*n, or n for a linear form
+ *   slot       device int32 [n_elem][n_entries] from ffc_csr_pattern (the dof map for a
+ *              linear form)
+ *   csr_val    device double [nnz], accumulated into
+ * ffc_assemble fuses this step into the contraction; this entry serves element tensors
+ * computed elsewhere. Slots outside [0, nnz) are skipped and set FFC_FLAG_BOUNDS; the
+ * order of the atomic adds is not deterministic.
+ */
+int ffc_scatter_add(int64_t n_elem, int n_entries, const void* A_K, int precision, const int32_t* slot,
+                    double* csr_val, int64_t nnz, void* stream);
 
 /*
  * ffc_tabulate_adjoint -- reverse mode of ffc_tabulate with respect to the vertex

@@ -172,6 +172,24 @@ def assemble(form: Form, cells, vertices, slot, csr_val, coeffs=None, precision=
     return csr_val
 
 
+def scatter_add(A_K, slot, csr_val, stream=None):
+    """The insertion step alone: csr_val[slot[e, ...]] += A_K[e, ...] (FP64 atomics).
+    A_K float64 or float32 [n_elem, ...]; slot int32 of the same shape."""
+    import torch
+
+    if A_K.dtype not in (torch.float64, torch.float32):
+        raise TypeError("A_K must be float64 or float32")
+    n_elem = A_K.shape[0]
+    n_entries = int(np.prod(A_K.shape[1:])) if A_K.dim() > 1 else 1
+    a = _dev_ptr(A_K, A_K.dtype, "A_K")
+    s = _dev_ptr(slot, torch.int32, "slot", tuple(A_K.shape))
+    val = _dev_ptr(csr_val, torch.float64, "csr_val")
+    p = FP64 if A_K.dtype == torch.float64 else FP32
+    _check(lib().ffc_scatter_add(n_elem, n_entries, a, p, s, val, csr_val.numel(), _stream(stream)),
+           "ffc_scatter_add")
+    return csr_val
+
+
 def tabulate_adjoint(form: Form, cells, vertices, dA_K, dvertices=None, stream=None):
     """dL/dvertices (accumulated into ``dvertices``) for the upstream gradient dA_K."""
     import torch

@@ -2,6 +2,7 @@
 // tensor, the library-owned status word, and dispatch to the kernels.
 #include <cuda_runtime.h>
 
+#include <climits>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -165,6 +166,29 @@ int ffc_assemble(const ffc_form* f, int64_t n_elem, const int32_t* cells, const 
   if (!st) { set_error("status word allocation failed"); return FFC_ECUDA; }
   LaunchArgs a{f, n_elem, cells, vertices, n_vert, coeffs, nullptr, slot, csr_val, nnz, t, st, stream};
   return dispatch(a, precision, true);
+}
+
+int ffc_scatter_add(int64_t n_elem, int n_entries, const void* A_K, int precision, const int32_t* slot,
+                    double* csr_val, int64_t nnz, void* stream) {
+  if (n_elem < 0 || n_entries <= 0 || (precision != FFC_FP64 && precision != FFC_FP32) || nnz < 0 ||
+      nnz > INT32_MAX) {
+    set_error("ffc_scatter_add: invalid argument");
+    return FFC_EINVAL;
+  }
+  if (n_elem == 0) return FFC_OK;
+  if (!A_K || !slot || !csr_val || nnz == 0) {
+    set_error("ffc_scatter_add: null pointer or empty CSR");
+    return FFC_EINVAL;
+  }
+  const size_t esize = precision == FFC_FP64 ? 8 : 4;
+  if ((reinterpret_cast<uintptr_t>(A_K) % esize) || (reinterpret_cast<uintptr_t>(slot) % 4) ||
+      (reinterpret_cast<uintptr_t>(csr_val) % 8)) {
+    set_error("ffc_scatter_add: misaligned pointer");
+    return FFC_EINVAL;
+  }
+  uint32_t* st = status_word();
+  if (!st) { set_error("status word allocation failed"); return FFC_ECUDA; }
+  return launch_scatter_add(A_K, precision, slot, csr_val, nnz, n_elem * (long long)n_entries, st, stream);
 }
 
 int ffc_tabulate_adjoint(const ffc_form* f, int64_t n_elem, const int32_t* cells, const double* vertices,

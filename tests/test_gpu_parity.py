@@ -194,6 +194,77 @@ def test_degeneracy_threshold_of_a_sliver(F, form):
         assert bool(F.status_poll() & F.FLAG_DEGENERATE) == flagged, eps
 
 
+@pytest.mark.parametrize("d,n,form,q,prec", [(3, 3, W.POISSON, 2, "fp64"), (3, 2, W.MASS, 4, "fp32"),
+                                               (2, 5, W.POISSON, 3, "fp64"), (3, 2, W.ELASTICITY, 2, "fp32"),
+                                               (3, 2, W.NS_CONVECTION, 2, "fp64")])
+def test_scatter_add_of_tabulated_tensors_equals_fused_assembly(F, d, n, form, q, prec):
+    """Algorithm 2's insertion on its own (tabulate, then scatter) gives the fused
+    assembly's matrix and the oracle's."""
+    import torch
+
+    p = _case(d, n, form, q)
+    row_ptr, col, slot = _pattern(F, p)
+    fm = F.Form(p.form, d, q)
+    cells, verts = _dev(p.mesh.cells, torch.int32), _dev(p.mesh.vertices, torch.float64)
+    coeffs = _dev(p.coeffs, torch.float64) if p.coeffs is not None else None
+    sl = _dev(slot, torch.int32)
+    fused = torch.zeros(col.size, dtype=torch.float64, device="cuda")
+    F.assemble(fm, cells, verts, sl, fused, coeffs=coeffs, precision=prec)
+    A = F.tabulate(fm, cells, verts, coeffs=coeffs, precision=prec)
+    split = torch.zeros_like(fused)
+    F.scatter_add(A, sl, split)
+    assert F.status_poll() == 0
+    scale = fused.abs().max().item()
+    assert (split - fused).abs().max().item() <= 1e-13 * scale
+    ref = OA.assemble_csr(_oracle(p), p.dofmap, p.n_dof)[2]
+    tol = FP64_TOL if prec == "fp64" else FP32_TOL
+    assert np.linalg.norm(split.cpu().numpy() - ref) <= tol * np.linalg.norm(ref)
+
+
+def test_scatter_add_edge_cases(F):
+    import torch
+
+    # ragged length (not a multiple of 4), an unaligned view, and an out-of-range slot
+    vals = torch.arange(1, 12, dtype=torch.float32, device="cuda").reshape(11, 1)
+    sl = torch.tensor([[0], [1], [2], [3], [4], [5], [6], [7], [8], [9], [2]], dtype=torch.int32, device="cuda")
+    out = torch.zeros(10, dtype=torch.float64, device="cuda")
+    F.scatter_add(vals, sl, out)
+    assert F.status_poll() == 0
+    want = np.arange(1, 11, dtype=float)
+    want[2] += 11
+    assert np.array_equal(out.cpu().numpy(), want)
+    out.zero_()
+    F.scatter_add(vals[1:], sl[1:], out)  # views that start 4 bytes past a 16-byte boundary
+    F.scatter_add(torch.ones((0, 3), dtype=torch.float64, device="cuda"),
+                  torch.zeros((0, 3), dtype=torch.int32, device="cuda"), out)
+    assert F.status_poll() == 0
+    want = np.zeros(10)
+    for v, k in zip(range(2, 12), [1, 2, 3, 4, 5, 6, 7, 8, 9, 2]):
+        want[k] += v
+    assert np.array_equal(out.cpu().numpy(), want)
+    bad = sl.clone()
+    bad[5, 0] = 10
+    out.zero_()
+    F.scatter_add(vals, bad, out)
+    assert F.status_poll() == F.FLAG_BOUNDS
+    assert out.sum().item() == pytest.approx(66.0 - 6.0)
+
+
+def test_gathered_vertices_through_iota_cells(F):
+    """Per-cell (gathered) vertex coordinates are accepted through cells[e] = (d+1)e + j:
+    the same element tensors as the indexed form."""
+    import torch
+
+    p = _case(3, 3, W.POISSON, 3)
+    fm = F.Form(W.POISSON, 3, 3)
+    gathered = M.gather_cell_vertices(p.mesh).reshape(-1, 3)
+    iota = np.arange(p.n_elem * 4, dtype=np.int32).reshape(p.n_elem, 4)
+    a = F.tabulate(fm, _dev(p.mesh.cells, torch.int32), _dev(p.mesh.vertices, torch.float64))
+    b = F.tabulate(fm, _dev(iota, torch.int32), _dev(gathered, torch.float64))
+    assert F.status_poll() == 0
+    assert torch.equal(a, b)
+
+
 def test_out_of_range_slot_is_skipped_and_flagged(F):
     import torch
 

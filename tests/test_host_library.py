@@ -207,3 +207,14 @@ def test_source_form_is_rank_one_with_the_mass_reference_tensor(d, q):
     assert F.Form(F.MASS, d, q).rank == 2
     with pytest.raises(F.FFCError):
         F.Form(5, d, q)
+
+
+def test_scatter_add_arguments_are_validated_on_the_host():
+    L = _lib()
+    # bad precision, empty entries, negative sizes, null pointers: rejected before any launch
+    assert L.ffc_scatter_add(10, 4, None, 2, None, None, 5, None) == -1
+    assert L.ffc_scatter_add(10, 0, None, 0, None, None, 5, None) == -1
+    assert L.ffc_scatter_add(-1, 4, None, 0, None, None, 5, None) == -1
+    assert L.ffc_scatter_add(10, 4, None, 0, None, None, 5, None) == -1
+    assert L.ffc_scatter_add(10, 4, None, 0, None, None, 2**31, None) == -1
+    assert L.ffc_scatter_add(0, 4, None, 0, None, None, 5, None) == 0  # nothing to do
