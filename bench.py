@@ -403,6 +403,7 @@ def main():
             "ms_per_step": elapsed / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32" if args.precision != "fp64" else "f64", "data": "synthetic",
             "nnz_per_s": world * total_nnz * args.steps / elapsed,
+            "insertions_per_s": world * n_elem * sum(p["n_local"] ** 2 for p in ctx["problems"]) * args.steps / elapsed,
             "config": {"workload": WORKLOAD, "cells": n_elem, "vertices": ctx["mesh"].n_vert,
                        "problems": [f"{FORM_NAME[p['form']]}_p{p['q']}" for p in ctx["problems"]],
                        "contraction": args.precision, "csr_accumulation": "f64", "nnz_total": total_nnz,
@@ -667,6 +668,7 @@ def run_other(args):
         byts = sum(pb.n_elem * (16 + 4 * pb.n_local) + pb.mesh.n_vert * 24 for pb in probs) + 16 * total_nnz
         out.update({"metric": "element tensors/s (batched: 32 meshes, elasticity vP1-vP3 + Poisson P2)",
                     "value": n_cells / t, "ms_per_step": t * 1e3, "dtype": "f32", "nnz_per_s": total_nnz / t,
+                    "insertions_per_s": sum(pb.n_elem * pb.n_local ** 2 for pb in probs) / t,
                     "config": {"workload": "batched", "meshes": len(probs), "cells": n_cells, "nnz": total_nnz,
                                "tile_cells_per_group": ke, "threads_per_block": b.threads_per_block,
                                "graph": True},
