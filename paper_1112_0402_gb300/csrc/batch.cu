@@ -10,8 +10,8 @@
 // shared CUDA-core tile body: FP64 geometry, FP32 contraction, FP64 atomic scatter
 // (elasticity through the block-structured contraction, the other forms densely).
 //
-// The tile variant (256 or 512 threads per block x 16, 32 or 64 cells per thread group
-// and tile) is chosen by timing all six on the caller's data (ffc_batch_tune). A run can be captured
+// The tile variant (256 or 416 threads per block x 16, 32, 64 or 128 cells per thread
+// group and tile) is chosen by timing all eight on the caller's data (ffc_batch_tune). A run can be captured
 // once into a CUDA graph (queue reset, optional CSR zeroing, kernel) and replayed.
 #include <cuda_runtime.h>
 
@@ -29,9 +29,10 @@ namespace ffc {
 namespace {
 
 // Tile variants the autotuner times: block size x cells per thread group and tile.
-constexpr int N_VARIANTS = 6;
-constexpr int VARIANT_BLOCK[N_VARIANTS] = {256, 256, 256, 512, 512, 512};
-constexpr int VARIANT_KE[N_VARIANTS] = {16, 32, 64, 16, 32, 64};
+constexpr int N_VARIANTS = 8;
+// 416 threads: 400 pairs of elasticity P3, 4 x 100 of elasticity P2 and Poisson P2
+constexpr int VARIANT_BLOCK[N_VARIANTS] = {256, 256, 256, 256, 416, 416, 416, 416};
+constexpr int VARIANT_KE[N_VARIANTS] = {16, 32, 64, 128, 16, 32, 64, 128};
 
 // Forms the batched kernel carries, by code.
 enum : int { CODE_ELAST_P1 = 0, CODE_ELAST_P2, CODE_ELAST_P3, CODE_POISSON_P1, CODE_POISSON_P2, CODE_MASS_P1,
@@ -77,7 +78,7 @@ __device__ __forceinline__ void run_tile(const SimtParams& p, long long tile, un
 }
 
 template <int BLK, int KE>
-__global__ void __launch_bounds__(BLK, BLK >= 512 ? 1 : 2)
+__global__ void __launch_bounds__(BLK, BLK > 256 ? 1 : 2)
     batch_assemble_kernel(const WorkItem* __restrict__ items, int n_items, long long total_tiles,
                           unsigned long long* queue) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -148,7 +149,9 @@ CodeInfo code_info_variant(int variant, int code) {
     case 2: return code_info<2>(code);
     case 3: return code_info<3>(code);
     case 4: return code_info<4>(code);
-    default: return code_info<5>(code);
+    case 5: return code_info<5>(code);
+    case 6: return code_info<6>(code);
+    default: return code_info<7>(code);
   }
 }
 
@@ -261,7 +264,9 @@ int enqueue(ffc_batch* b, int variant, cudaStream_t s) {
     case 2: return launch_variant<2>(b, s);
     case 3: return launch_variant<3>(b, s);
     case 4: return launch_variant<4>(b, s);
-    default: return launch_variant<5>(b, s);
+    case 5: return launch_variant<5>(b, s);
+    case 6: return launch_variant<6>(b, s);
+    default: return launch_variant<7>(b, s);
   }
 }
 

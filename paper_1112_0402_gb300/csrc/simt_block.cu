@@ -13,6 +13,13 @@ int run(const LaunchArgs& a) {
     if (C::SMEM > 48 * 1024 &&
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(C::SMEM)) != cudaSuccess)
       return FFC_ECUDA;
+    // elasticity: the whole unified L1 / shared array as shared memory, so the nine
+    // geometry blocks of several resident CTAs fit (measured faster; the convection
+    // kernel and the batched kernel, which lean on L1 for their streamed loads, keep the
+    // default split)
+    if (FORM == FFC_ELASTICITY &&
+        cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100) != cudaSuccess)
+      return FFC_ECUDA;
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);

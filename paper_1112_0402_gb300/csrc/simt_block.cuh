@@ -18,13 +18,17 @@
 // 27x (convection) and 9x (elasticity) fewer multiply-adds and a reference tensor small
 // enough for registers.
 //
-// Thread layout ("pair major"): a thread owns a pair (s1, s2) and keeps its reduced row
-// R[(s1,s2)] in registers; per cell it contracts that row with each of the cell's nb
-// geometry blocks (16-byte shared-memory loads, the same address across the warp) and
-// writes the d*d entries ((c1,s1),(c2,s2)) of the element tensor. Consecutive threads
-// hold consecutive s2, so each store instruction covers runs of n_s consecutive
-// entries. The convection form's one block goes to the d diagonal positions; the
-// structurally zero off-diagonal blocks are stored as 0 (tabulate) or skipped (assembly).
+// Thread layouts. Elasticity, "row slots": a slot is (s1, c2, s2), numbered with s2
+// fastest, then c2, then s1, so consecutive slots are consecutive entries of element
+// tensor row (c1, s1) for every c1; the slot keeps R[(s1,s2)] in registers and per cell
+// contracts it with the block (c1, c2) for each c1: a warp's store (or atomic) instruction
+// covers a contiguous run of one row (one CSR row in assembly). Convection, "pair major":
+// a slot is a pair (s1, s2); its one block is contracted once per cell and written to the
+// d diagonal positions, zeros elsewhere (tabulate) or nothing (assembly); row slots would
+// repeat that contraction d times. Earlier single layouts for both: "entry major" (each
+// thread an entry of the row-major element tensor; convection P2 1.57 ms) and pair major
+// for elasticity too (runs of n_s entries per store: elasticity P3 0.66 ms, batched 17.2
+// ms, against 0.56 and 15.1 ms with row slots).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -49,12 +53,15 @@ struct BlockCfg {
   static constexpr int NB = FORM == FFC_NS_CONVECTION ? 1 : D * D;
   static constexpr int VEC = 16 / int(sizeof(T));
   static constexpr int KRP = (KR + VEC - 1) / VEC * VEC;
-  static constexpr int NP2 = NS * NS;  // pairs (s1, s2)
-  // about 256 threads: whole groups of NP2 threads, rounded up to whole warps
-  static constexpr int NT0 = NP2 >= 256 ? NP2 : NP2 * (256 / NP2);
+  static constexpr bool DIAG = FORM == FFC_NS_CONVECTION;  // one block, on the diagonal
+  static constexpr int NP2 = NS * NS;                      // pairs (s1, s2): rows of R
+  static constexpr int NSL = DIAG ? NP2 : D * NS * NS;     // slots: pairs, or row slots (s1, c2, s2)
+  // about 256 threads: whole groups of NSL slots, or up to 512 threads with several
+  // slots each, rounded up to whole warps
+  static constexpr int NT0 = NSL >= 256 ? (NSL < 512 ? NSL : 512) : NSL * (256 / NSL);
   static constexpr int NT = BLOCK > 0 ? BLOCK : (NT0 + 31) / 32 * 32;
-  static constexpr int GRP = NT >= NP2 ? NT / NP2 : 1;  // thread groups; a tile's cells are dealt to them
-  static constexpr int PPT = (NP2 + NT - 1) / NT;       // pairs per thread
+  static constexpr int GRP = NT >= NSL ? NT / NSL : 1;  // thread groups; a tile's cells are dealt to them
+  static constexpr int PPT = (NSL + NT - 1) / NT;       // slots per thread
   static constexpr bool REG_R = PPT * KR * int(sizeof(T)) / 4 <= 64;
   static constexpr int E_DEF = (FORM == FFC_NS_CONVECTION && sizeof(T) == 8) ? 64 : 128;
   static constexpr int E = KE_T > 0 ? (KE_T * GRP < 128 ? KE_T * GRP : 128) : E_DEF;  // cells per tile
@@ -63,19 +70,29 @@ struct BlockCfg {
   static constexpr size_t R_BYTES = REG_R ? 0 : size_t(NP2) * KRP * sizeof(T);
   static constexpr size_t W_BYTES = size_t(E) * NCOEF * sizeof(double);
   static constexpr size_t SMEM = G_BYTES + R_BYTES + W_BYTES;
+  // register budget of the single-form FP32 kernel: about 16 resident warps per SM (one
+  // CTA of 512 threads with up to 128 registers, two of 257..511, three of up to 256);
+  // FP64 (bound by the FP64 pipe) keeps its reduced rows in registers without spills
+  static constexpr int MIN_BLOCKS = sizeof(T) == 8 ? 1 : (NT >= 512 ? 1 : (NT > 256 ? 2 : 3));
 };
 
 template <class C, typename T>
 struct BlockRows {
-  T rr[C::REG_R ? C::PPT : 1][C::REG_R ? C::KR : 1];  // reduced rows of the thread's pairs
+  T rr[C::REG_R ? C::PPT : 1][C::REG_R ? C::KR : 1];  // reduced rows of the thread's slots
 };
 
-// The thread's pairs: pair slot j holds pp = t mod NP2 (NT >= NP2, group t / NP2) or
-// pp = t + j*NT (NT < NP2, one group). -1: no pair.
+// The thread's slots: slot j is q = t mod NSL (NT >= NSL, group t / NSL) or q = t + j*NT
+// (NT < NSL, one group); -1: none. Slot q is (s1, c2, s2) with s2 fastest.
 template <class C>
-__device__ __forceinline__ int pair_of(int t, int j) {
-  if constexpr (C::NT >= C::NP2) return (j == 0 && t < C::GRP * C::NP2) ? t % C::NP2 : -1;
-  else return (t + j * C::NT < C::NP2) ? t + j * C::NT : -1;
+__device__ __forceinline__ int slot_of(int t, int j) {
+  if constexpr (C::NT >= C::NSL) return (j == 0 && t < C::GRP * C::NSL) ? t % C::NSL : -1;
+  else return (t + j * C::NT < C::NSL) ? t + j * C::NT : -1;
+}
+template <class C>
+__device__ __forceinline__ int pair_of_slot(int q) {  // the row (s1, s2) of R a slot uses
+  if constexpr (C::DIAG) return q;
+  const int s2 = q % C::NS, s1 = q / (C::NS * (C::N / C::NS));
+  return s1 * C::NS + s2;
 }
 
 // The reduced reference tensor rows (registers, or shared memory behind the geometry
@@ -87,9 +104,10 @@ __device__ __forceinline__ void block_rows_init(const void* r, BlockRows<C, T>& 
   if constexpr (C::REG_R) {
 #pragma unroll
     for (int j = 0; j < C::PPT; ++j) {
-      const int pp = pair_of<C>(t, j);
+      const int q = slot_of<C>(t, j);
+      const int pp = q >= 0 ? pair_of_slot<C>(q) : 0;
 #pragma unroll
-      for (int k = 0; k < C::KR; ++k) b.rr[j][k] = pp >= 0 ? Rg[size_t(pp) * C::KR + k] : T(0);
+      for (int k = 0; k < C::KR; ++k) b.rr[j][k] = q >= 0 ? Rg[size_t(pp) * C::KR + k] : T(0);
     }
   } else {
     T* Rs = reinterpret_cast<T*>(smem + C::G_BYTES);
@@ -182,84 +200,98 @@ __device__ __forceinline__ void block_tile(const SimtParams& p, long long tile, 
       for (int k = C::KR; k < C::KRP; ++k) g[b * C::KRP + k] = T(0);
   }
   __syncthreads();
-  // ---- contraction: pair slots x the group's cells x blocks
+  // ---- contraction: the thread's slots x the group's cells
   using V = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
-  const int grp = C::NT >= C::NP2 ? t / C::NP2 : 0;
+  constexpr bool DIAG = C::DIAG;
+  constexpr int NPOS = DIAG ? D * D : D;  // element-tensor entries a slot writes per cell
+  const int grp = C::NT >= C::NSL ? t / C::NSL : 0;
   const long long left = p.n_elem - e0;
   const int nc = int(left < C::E ? left : C::E);
+  // R[(s1,s2)] . block
+  auto contract = [&](const T* gblk, int j, const T* rrow) {
+    const V* gv = reinterpret_cast<const V*>(gblk);
+    T acc = T(0);
+#pragma unroll
+    for (int kv = 0; kv < C::KRP / C::VEC; ++kv) {
+      const V x = gv[kv];
+      T xs[C::VEC];
+      if constexpr (sizeof(T) == 4) {
+        xs[0] = x.x;
+        xs[1] = x.y;
+        xs[2] = x.z;
+        xs[3] = x.w;
+      } else {
+        xs[0] = x.x;
+        xs[1] = x.y;
+      }
+#pragma unroll
+      for (int m = 0; m < C::VEC; ++m) {
+        const int k = kv * C::VEC + m;
+        if (k < C::KR) {
+          if constexpr (C::REG_R) acc = fma(xs[m], br.rr[j][k < C::KR ? k : 0], acc);
+          else acc = fma(xs[m], rrow[k], acc);
+        }
+      }
+    }
+    return acc;
+  };
 #pragma unroll
   for (int j = 0; j < C::PPT; ++j) {
-    const int pp = pair_of<C>(t, j);
-    if (pp < 0) continue;
-    const int s1 = pp / C::NS, s2 = pp % C::NS;
-    const T* rrow = Rs + size_t(pp) * C::KRP;
-    // positions of the d*d entries ((c1,s1),(c2,s2)) in the cell's element tensor
-    int pos[D * D];
+    const int q = slot_of<C>(t, j);
+    if (q < 0) continue;
+    int s1, s2, c2 = 0;
+    if constexpr (DIAG) {
+      s1 = q / C::NS;
+      s2 = q % C::NS;
+    } else {
+      s2 = q % C::NS;
+      c2 = (q / C::NS) % D;
+      s1 = q / (C::NS * D);
+    }
+    const T* rrow = Rs + size_t(s1 * C::NS + s2) * C::KRP;
+    // positions of the slot's entries: all d*d blocks (c1, c2) of the pair (convection),
+    // or the d entries ((c1,s1),(c2,s2)) of the row slot (elasticity)
+    int pos[NPOS];
+    bool live_pos[NPOS];  // assembly: structural zeros add nothing
 #pragma unroll
-    for (int c1 = 0; c1 < D; ++c1)
-#pragma unroll
-      for (int c2 = 0; c2 < D; ++c2) pos[c1 * D + c2] = (c1 * C::NS + s1) * C::N + c2 * C::NS + s2;
-    constexpr bool DIAG = FORM == FFC_NS_CONVECTION;  // one block, on the diagonal
+    for (int m = 0; m < NPOS; ++m) {
+      const int c1 = DIAG ? m / D : m;
+      const int cc2 = DIAG ? m % D : c2;
+      pos[m] = (c1 * C::NS + s1) * C::N + cc2 * C::NS + s2;
+      live_pos[m] = !DIAG || c1 == cc2;
+    }
     // assembly: the slots of the next cell are loaded while this cell's atomics issue
-    int sl_next[ASSEMBLE ? D * D : 1];
+    int sl_next[ASSEMBLE ? NPOS : 1];
     if constexpr (ASSEMBLE) {
 #pragma unroll
-      for (int b = 0; b < D * D; ++b)
-        sl_next[b] = (grp < nc && (!DIAG || b % (D + 1) == 0)) ? __ldg(p.slot + (e0 + grp) * C::NN + pos[b]) : -1;
+      for (int m = 0; m < NPOS; ++m)
+        sl_next[m] = (grp < nc && live_pos[m]) ? __ldg(p.slot + (e0 + grp) * C::NN + pos[m]) : -1;
     }
 #pragma unroll 1
     for (int el = grp; el < nc; el += C::GRP) {
       const long long e = e0 + el;
-      int sl[ASSEMBLE ? D * D : 1];
+      int sl[ASSEMBLE ? NPOS : 1];
       if constexpr (ASSEMBLE) {
         const int en = el + C::GRP;
 #pragma unroll
-        for (int b = 0; b < D * D; ++b) {
-          sl[b] = sl_next[b];
-          sl_next[b] = (en < nc && (!DIAG || b % (D + 1) == 0)) ? __ldg(p.slot + (e0 + en) * C::NN + pos[b]) : -1;
+        for (int m = 0; m < NPOS; ++m) {
+          sl[m] = sl_next[m];
+          sl_next[m] = (en < nc && live_pos[m]) ? __ldg(p.slot + (e0 + en) * C::NN + pos[m]) : -1;
         }
       }
-      const V* gv = reinterpret_cast<const V*>(Gs + size_t(el) * C::NB * C::KRP);
-      T val[C::NB];
+      const T* gcell = Gs + size_t(el) * C::NB * C::KRP;
+      T vdiag = T(0);
+      if constexpr (DIAG) vdiag = contract(gcell, j, rrow);
 #pragma unroll
-      for (int b = 0; b < C::NB; ++b) {
-        T acc = T(0);
-#pragma unroll
-        for (int kv = 0; kv < C::KRP / C::VEC; ++kv) {
-          const V x = gv[b * (C::KRP / C::VEC) + kv];
-          T xs[C::VEC];
-          if constexpr (sizeof(T) == 4) {
-            xs[0] = x.x;
-            xs[1] = x.y;
-            xs[2] = x.z;
-            xs[3] = x.w;
-          } else {
-            xs[0] = x.x;
-            xs[1] = x.y;
-          }
-#pragma unroll
-          for (int q = 0; q < C::VEC; ++q) {
-            const int k = kv * C::VEC + q;
-            if (k < C::KR) {
-              if constexpr (C::REG_R) acc = fma(xs[q], br.rr[j][k < C::KR ? k : 0], acc);
-              else acc = fma(xs[q], rrow[k], acc);
-            }
-          }
-        }
-        val[b] = acc;
-      }
-#pragma unroll
-      for (int b = 0; b < D * D; ++b) {
-        const bool nonzero = !DIAG || b % (D + 1) == 0;
-        const T v = DIAG ? (nonzero ? val[0] : T(0)) : val[DIAG ? 0 : b];
+      for (int m = 0; m < NPOS; ++m) {
+        if (ASSEMBLE && !live_pos[m]) continue;
+        const T v = DIAG ? (live_pos[m] ? vdiag : T(0)) : contract(gcell + (m * D + c2) * C::KRP, j, rrow);
         if constexpr (ASSEMBLE) {
-          if (nonzero) {  // structural zeros add nothing
-            const int sv = sl[b];
-            if (sv >= 0 && sv < p.nnz) atomicAdd(p.csr_val + sv, double(v));
-            else atomicOr(p.status, FFC_FLAG_BOUNDS);
-          }
+          const int sv = sl[m];
+          if (sv >= 0 && sv < p.nnz) atomicAdd(p.csr_val + sv, double(v));
+          else atomicOr(p.status, FFC_FLAG_BOUNDS);
         } else {
-          __stcs(static_cast<T*>(p.out) + e * C::NN + pos[b], v);
+          __stcs(static_cast<T*>(p.out) + e * C::NN + pos[m], v);
         }
       }
     }
@@ -268,7 +300,8 @@ __device__ __forceinline__ void block_tile(const SimtParams& p, long long tile, 
 }
 
 template <int D, int FORM, int Q, typename T, bool ASSEMBLE>
-__global__ void __launch_bounds__(BlockCfg<D, FORM, Q, T>::NT) simt_block_kernel(SimtParams p) {
+__global__ void __launch_bounds__(BlockCfg<D, FORM, Q, T>::NT, BlockCfg<D, FORM, Q, T>::MIN_BLOCKS)
+    simt_block_kernel(SimtParams p) {
   using C = BlockCfg<D, FORM, Q, T>;
   extern __shared__ __align__(16) unsigned char smem[];
   BlockRows<C, T> rows;

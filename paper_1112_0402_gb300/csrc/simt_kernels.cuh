@@ -33,8 +33,14 @@ struct SimtCfg {
   static constexpr int VEC = 16 / int(sizeof(T));
   static constexpr int NAP = (NA + VEC - 1) / VEC * VEC;
   static constexpr int RMAX_THREADS = BLOCK > 0 ? BLOCK : 512;
-  static constexpr int R = (NN + RMAX_THREADS - 1) / RMAX_THREADS;
-  static constexpr int NTI = (NN + R - 1) / R;
+  // symmetric forms on the FP64 pipe contract only the entries i1 <= i2 (Section 3.5:
+  // a symmetric form needs fewer operations) and store each result at (i1, i2) and
+  // (i2, i1); the FP32 paths stay HBM-bound on stores and keep the full, coalesced layout
+  static constexpr bool SYMM =
+      BLOCK == 0 && sizeof(T) == 8 && (FORM == FFC_POISSON || FORM == FFC_ELASTICITY);
+  static constexpr int NE = SYMM ? N * (N + 1) / 2 : NN;  // entries contracted per cell
+  static constexpr int R = (NE + RMAX_THREADS - 1) / RMAX_THREADS;
+  static constexpr int NTI = (NE + R - 1) / R;
   static constexpr int EG = BLOCK > 0 ? BLOCK / NTI : (NTI >= 256 ? 1 : 256 / NTI);
   static constexpr int NT = BLOCK > 0 ? BLOCK : NTI * EG;
   // register-resident reference tensor rows; a shared block size (several forms in one
@@ -57,7 +63,7 @@ struct SimtParams {
   const double* vertices;
   long long n_vert;
   const double* coeffs;
-  const void* a0;       // REG_A0: [NN][NA]; otherwise [NA][NN]
+  const void* a0;       // REG_A0: [NN][NA]; otherwise [NA][NN] (rows by element-tensor position)
   void* out;            // A_K [n_elem][NN]
   const int32_t* slot;  // [n_elem][NN]
   double* csr_val;
@@ -72,6 +78,28 @@ __device__ __forceinline__ void put(OutT* p, OutT v) {
   __stcs(p, v);
 }
 
+// Element-tensor positions of contracted entry u: (u, u) for the full layout; for the
+// symmetric one, u numbers the entries i1 <= i2 row by row (row i1 starts at
+// i1*N - i1*(i1-1)/2) and the positions are i1*N + i2 and i2*N + i1.
+template <class C>
+__device__ __forceinline__ void entry_positions(int u, int& p1, int& p2) {
+  if constexpr (C::SYMM) {
+    constexpr int N = C::N;
+    auto start = [](int i) { return i * N - i * (i - 1) / 2; };
+    const float h = float(N) + 0.5f;
+    int i1 = int(h - sqrtf(h * h - 2.0f * float(u)));
+    i1 = i1 < 0 ? 0 : (i1 > N - 1 ? N - 1 : i1);
+    while (i1 > 0 && start(i1) > u) --i1;
+    while (i1 < N - 1 && start(i1 + 1) <= u) ++i1;
+    const int i2 = i1 + (u - start(i1));
+    p1 = i1 * N + i2;
+    p2 = i2 * N + i1;
+  } else {
+    p1 = u;
+    p2 = u;
+  }
+}
+
 // Loads the thread's rows of the reference tensor into registers (register path).
 template <class C, typename T>
 __device__ __forceinline__ void load_a0_rows(const void* a0, int t, T (&a0r)[C::REG_A0 ? C::R : 1][C::REG_A0 ? C::NA : 1]) {
@@ -80,9 +108,11 @@ __device__ __forceinline__ void load_a0_rows(const void* a0, int t, T (&a0r)[C::
     const T* A0 = static_cast<const T*>(a0);
 #pragma unroll
     for (int r = 0; r < C::R; ++r) {
-      const int i = ti + r * C::NTI;
+      const int u = ti + r * C::NTI;
+      int p1 = 0, p2 = 0;
+      if (u < C::NE) entry_positions<C>(u, p1, p2);
 #pragma unroll
-      for (int a = 0; a < C::NA; ++a) a0r[r][a] = (i < C::NN) ? A0[size_t(i) * C::NA + a] : T(0);
+      for (int a = 0; a < C::NA; ++a) a0r[r][a] = (u < C::NE) ? A0[size_t(p1) * C::NA + a] : T(0);
     }
   }
 }
@@ -140,14 +170,25 @@ __device__ __forceinline__ void simt_tile(const SimtParams& p, long long tile, u
     // ---- phase 2: contraction and epilogue (thread groups beyond EG idle)
     if (eg >= C::EG) {
     } else if constexpr (C::REG_A0) {
+      // element-tensor positions of the thread's entries (two for an off-diagonal entry
+      // of the symmetric layout)
+      int pos1[C::R], pos2[C::R];
+#pragma unroll
+      for (int r = 0; r < C::R; ++r) {
+        const int u = ti + r * C::NTI;
+        pos1[r] = pos2[r] = -1;
+        if (u < C::NE) entry_positions<C>(u, pos1[r], pos2[r]);
+      }
+      constexpr int NS_ = C::SYMM ? 2 : 1;  // slots per entry
       // assembly: the slots of the next cell are loaded while this cell's atomics issue
-      int slot_next[ASSEMBLE ? C::R : 1];
+      int slot_next[ASSEMBLE ? C::R : 1][NS_];
       if constexpr (ASSEMBLE) {
         const long long e = e0 + eg;
 #pragma unroll
         for (int r = 0; r < C::R; ++r) {
-          const int i = ti + r * C::NTI;
-          slot_next[r] = (e < p.n_elem && i < C::NN) ? __ldg(p.slot + e * C::NN + i) : -1;
+          const bool ok = e < p.n_elem && pos1[r] >= 0;
+          slot_next[r][0] = ok ? __ldg(p.slot + e * C::NN + pos1[r]) : -1;
+          if constexpr (C::SYMM) slot_next[r][1] = (ok && pos2[r] != pos1[r]) ? __ldg(p.slot + e * C::NN + pos2[r]) : -1;
         }
       }
 #pragma unroll 1
@@ -155,15 +196,19 @@ __device__ __forceinline__ void simt_tile(const SimtParams& p, long long tile, u
         const int el = eg + k * C::EG;
         const long long e = e0 + el;
         if (e >= p.n_elem) break;
-        int slot_cur[ASSEMBLE ? C::R : 1];
+        int slot_cur[ASSEMBLE ? C::R : 1][NS_];
         if constexpr (ASSEMBLE) {
           const long long en = e + C::EG;
           const bool more = (k + 1 < C::KE) && (en < p.n_elem);
 #pragma unroll
           for (int r = 0; r < C::R; ++r) {
-            const int i = ti + r * C::NTI;
-            slot_cur[r] = slot_next[r];
-            slot_next[r] = (more && i < C::NN) ? __ldg(p.slot + en * C::NN + i) : -1;
+            const bool ok = more && pos1[r] >= 0;
+            slot_cur[r][0] = slot_next[r][0];
+            slot_next[r][0] = ok ? __ldg(p.slot + en * C::NN + pos1[r]) : -1;
+            if constexpr (C::SYMM) {
+              slot_cur[r][1] = slot_next[r][1];
+              slot_next[r][1] = (ok && pos2[r] != pos1[r]) ? __ldg(p.slot + en * C::NN + pos2[r]) : -1;
+            }
           }
         }
         const T* g = Gs + el * C::NAP;
@@ -178,16 +223,18 @@ __device__ __forceinline__ void simt_tile(const SimtParams& p, long long tile, u
         }
 #pragma unroll
         for (int r = 0; r < C::R; ++r) {
-          const int i = ti + r * C::NTI;
-          if (i < C::NN) {
-            const long long o = e * C::NN + i;
-            if constexpr (ASSEMBLE) {
-              const int s = slot_cur[r];
+          if (pos1[r] < 0) continue;
+          if constexpr (ASSEMBLE) {
+#pragma unroll
+            for (int m = 0; m < NS_; ++m) {
+              if (m == 1 && pos2[r] == pos1[r]) continue;
+              const int s = slot_cur[r][m];
               if (s >= 0 && s < p.nnz) atomicAdd(p.csr_val + s, double(acc[r]));
               else atomicOr(p.status, FFC_FLAG_BOUNDS);
-            } else {
-              put(static_cast<OutT*>(p.out) + o, acc[r]);
             }
+          } else {
+            put(static_cast<OutT*>(p.out) + e * C::NN + pos1[r], acc[r]);
+            if (C::SYMM && pos2[r] != pos1[r]) put(static_cast<OutT*>(p.out) + e * C::NN + pos2[r], acc[r]);
           }
         }
       }
@@ -195,8 +242,10 @@ __device__ __forceinline__ void simt_tile(const SimtParams& p, long long tile, u
       const T* A0T = static_cast<const T*>(p.a0);
 #pragma unroll 1
       for (int r = 0; r < C::R; ++r) {
-        const int i = ti + r * C::NTI;
-        if (i >= C::NN) break;
+        const int u = ti + r * C::NTI;
+        if (u >= C::NE) break;
+        int p1, p2;
+        entry_positions<C>(u, p1, p2);
         T acc[C::KE];
 #pragma unroll
         for (int k = 0; k < C::KE; ++k) acc[k] = T(0);
@@ -206,7 +255,7 @@ __device__ __forceinline__ void simt_tile(const SimtParams& p, long long tile, u
         for (int a0 = 0; a0 < C::NAP; a0 += C::VEC) {
           T av[C::VEC];
 #pragma unroll
-          for (int j = 0; j < C::VEC; ++j) av[j] = (a0 + j < C::NA) ? __ldg(A0T + size_t(a0 + j) * C::NN + i) : T(0);
+          for (int j = 0; j < C::VEC; ++j) av[j] = (a0 + j < C::NA) ? __ldg(A0T + size_t(a0 + j) * C::NN + p1) : T(0);
 #pragma unroll
           for (int k = 0; k < C::KE; ++k) {
             const V gv = *reinterpret_cast<const V*>(Gs + (eg + k * C::EG) * C::NAP + a0);
@@ -225,13 +274,17 @@ __device__ __forceinline__ void simt_tile(const SimtParams& p, long long tile, u
         for (int k = 0; k < C::KE; ++k) {
           const long long e = e0 + eg + k * C::EG;
           if (e < p.n_elem) {
-            const long long o = e * C::NN + i;
-            if constexpr (ASSEMBLE) {
-              const int s = __ldg(p.slot + o);
-              if (s >= 0 && s < p.nnz) atomicAdd(p.csr_val + s, double(acc[k]));
-              else atomicOr(p.status, FFC_FLAG_BOUNDS);
-            } else {
-              put(static_cast<OutT*>(p.out) + o, acc[k]);
+#pragma unroll
+            for (int m = 0; m < (C::SYMM ? 2 : 1); ++m) {
+              if (m == 1 && p2 == p1) continue;
+              const long long o = e * C::NN + (m == 0 ? p1 : p2);
+              if constexpr (ASSEMBLE) {
+                const int s = __ldg(p.slot + o);
+                if (s >= 0 && s < p.nnz) atomicAdd(p.csr_val + s, double(acc[k]));
+                else atomicOr(p.status, FFC_FLAG_BOUNDS);
+              } else {
+                put(static_cast<OutT*>(p.out) + o, acc[k]);
+              }
             }
           }
         }
