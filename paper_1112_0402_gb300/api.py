@@ -138,6 +138,28 @@ def tabulate(form: Form, cells, vertices, coeffs=None, precision="fp64", out=Non
     return out
 
 
+def tabulate_static(form: Form, cells, vertices, coeffs=None, precision="fp64", out=None, stream=None):
+    """tabulate() through the allocation-free entry point (ffc_tabulate_static): the
+    reference tensor is staged in a fixed device array compiled into the library.
+    FP64 or FP32 only; synchronises ``stream`` and returns (A_K, device status bits)."""
+    import torch
+
+    p = _prec(precision)
+    n_elem = cells.shape[0]
+    shp = (n_elem,) + form.tensor_shape
+    dt = torch.float64 if p == FP64 else torch.float32
+    if out is None:
+        out = torch.empty(shp, dtype=dt, device=vertices.device)
+    c = _dev_ptr(cells, torch.int32, "cells", (n_elem, form.dim + 1))
+    v = _dev_ptr(vertices, torch.float64, "vertices")
+    w = _dev_ptr(coeffs, torch.float64, "coeffs", (n_elem, form.n_coeff)) if form.n_coeff else None
+    o = _dev_ptr(out, dt, "out", shp)
+    flags = ctypes.c_uint32()
+    _check(lib().ffc_tabulate_static(form.handle, n_elem, c, v, vertices.shape[0], w, o, p, _stream(stream),
+                                     ctypes.byref(flags)), "ffc_tabulate_static")
+    return out, flags.value
+
+
 def csr_pattern(dofmap: np.ndarray, n_dof: int, with_slots: bool = True):
     """Sorted-column CSR pattern (row_ptr int64, col int32) and slots int32 [n_elem, n, n]."""
     dm = np.ascontiguousarray(dofmap, dtype=np.int32)

@@ -68,3 +68,22 @@ def test_static_scratch_entry_point_matches_ffc_tabulate():
     rc, _ = _static_call(L, big, cells, verts, None, out, F.FP64)
     assert rc == -1
     assert np.isfinite(ref.cpu().numpy()).all()
+
+
+def test_static_entry_point_through_the_python_binding():
+    import torch
+
+    from paper_1112_0402_gb300 import build as B
+
+    B.build()
+    import paper_1112_0402_gb300 as F
+
+    m = M.unit_cube_tets(3, 0.15, seed=6)
+    form = F.Form(W.MASS, F.TETRAHEDRON, 2)
+    cells = torch.as_tensor(m.cells, device="cuda")
+    verts = torch.as_tensor(m.vertices, device="cuda")
+    ref = F.tabulate(form, cells, verts, precision="fp32")
+    for _ in range(2):  # two calls in a row reuse the fixed array
+        out, flags = F.tabulate_static(form, cells, verts, precision="fp32")
+        assert flags == 0
+        assert torch.equal(out, ref)
