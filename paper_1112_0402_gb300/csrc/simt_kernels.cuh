@@ -46,10 +46,10 @@ struct SimtCfg {
   // register-resident reference tensor rows; a shared block size (several forms in one
   // kernel) keeps it only for small |alpha| so the kernel's register count stays low
   static constexpr bool REG_A0 = (R * NA * int(sizeof(T)) / 4) <= (BLOCK > 0 ? 32 : 96);
-  // cells per thread group and tile (register path: 64; element tensors above 512
-  // entries, one thread group per CTA: 32, or 16 when the contraction is a single
-  // product, mass; measured on P4 tetrahedra)
-  static constexpr int KE_TARGET = KE_T > 0 ? KE_T : (REG_A0 ? (R > 1 ? (NA == 1 ? 16 : 32) : 64) : 16);
+  // cells per thread group and tile, measured on tetrahedra: register path 64 for mass,
+  // 128 for Poisson P1-P3 (its heavier geometry phase amortised over more stores);
+  // element tensors above 512 entries (one thread group per CTA) 32, or 16 for mass
+  static constexpr int KE_TARGET = KE_T > 0 ? KE_T : (REG_A0 ? (R > 1 ? (NA == 1 ? 16 : 32) : (NA > 1 ? 128 : 64)) : 16);
   static constexpr int KE = (KE_TARGET + EG - 1) / EG;
   static constexpr int E = EG * KE;
   static constexpr int NCOEF = (FORM == FFC_NS_CONVECTION) ? N : 0;
