@@ -361,21 +361,35 @@ def main():
         d_cells = torch.empty_like(ctx["cells"])
         d_verts = torch.empty_like(ctx["verts"])
 
+        # the read-back of problem k runs on its own stream while problem k+1 assembles;
+        # problem k's values are zeroed again only after its previous read-back finished
+        copy_stream = torch.cuda.Stream()
+        read_done = [None] * P
+
         def e2e_step():
+            cur = torch.cuda.current_stream()
             d_cells.copy_(h_cells, non_blocking=True)
             d_verts.copy_(h_verts, non_blocking=True)
-            for pr, ho in zip(ctx["problems"], h_out):
+            for k, (pr, ho) in enumerate(zip(ctx["problems"], h_out)):
+                if read_done[k] is not None:
+                    cur.wait_event(read_done[k])
                 pr["val"].zero_()
                 F.assemble(pr["F"], d_cells, d_verts, pr["slot"], pr["val"], precision=args.precision)
-                ho.copy_(pr["val"], non_blocking=True)
+                copy_stream.wait_stream(cur)
+                with torch.cuda.stream(copy_stream):
+                    ho.copy_(pr["val"], non_blocking=True)
+                    read_done[k] = torch.cuda.Event()
+                    read_done[k].record(copy_stream)
 
         for _ in range(max(1, args.warmup)):
             e2e_step()
+        torch.cuda.current_stream().wait_stream(copy_stream)
         barrier()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record()
         for _ in range(args.steps):
             e2e_step()
+        torch.cuda.current_stream().wait_stream(copy_stream)
         b.record()
         barrier()
         te = max_over_ranks(a.elapsed_time(b) / 1e3, world, device)
