@@ -40,6 +40,7 @@ extern "C" {
 
 typedef struct ffc_form ffc_form;   /* opaque; owns the reference tensor (host and device copies) */
 typedef struct ffc_batch ffc_batch; /* opaque; a heterogeneous work list for one persistent launch */
+typedef struct ffc_row_plan ffc_row_plan; /* opaque; row-owner view of a dof map (ffc_assemble_rows) */
 
 typedef enum {
   FFC_OK = 0,
@@ -247,6 +248,57 @@ int ffc_batch_run(ffc_batch* b, int use_graph, void* stream);
 int ffc_batch_info(const ffc_batch* b, int* n_items, long long* total_tiles, int* cells_per_tile_group,
                    int* threads_per_block);
 void ffc_batch_destroy(ffc_batch* b);
+
+/*
+ * Row-owner assembly: Algorithm 2 (Section 2.2) with its loops ordered by global row.
+ * Algorithm 2 adds the element tensor of each cell into the matrix; the entries of
+ * global row r therefore receive exactly the element-tensor rows A^K[i1][:] of the
+ * cells K with dofmap[K][i1] = r. ffc_assemble_rows lets one warp own each row: it
+ * computes those rows from a per-cell geometry tensor G_K (A^K = A0 : G_K, Section 3.2),
+ * sums them in shared memory and writes the finished row once. No global atomics, no
+ * zeroing: every CSR value is overwritten.
+ *
+ * The sums are exact: each contribution (FP32 or FP64, as the contraction produced it)
+ * is converted to 64-bit fixed point with a per-row unit u = 2^-62 * 2^eb, where 2^eb
+ * is at least twice a bound on the row's sum of |contributions|; integer sums do not
+ * depend on their order, and each result is rounded once to FP64 (nearest even). Per
+ * entry: |result - exact sum of the contributions| <= m * u + ulp(result) / 2 with m the
+ * entry's number of contributions. Results are bitwise reproducible.
+ *
+ * ffc_row_plan_create -- the row view of a dof map and its CSR pattern, built on the
+ * device once per (mesh, space):
+ *   dofmap   device int32 [n_elem][n_local], global ids in [0, n_dof)
+ *   row_ptr  device int64 [n_dof + 1], col device int32 [nnz]: the pattern of
+ *            ffc_csr_pattern (columns sorted within each row), copied to the device
+ * The plan stores, per row r, the (e, i1) pairs with dofmap[e][i1] = r in increasing
+ * e * n_local + i1 order, and for each pair the position of column dofmap[e][i2] inside
+ * row r (uint16). It owns n_elem * n_local * (n_local * 2 + 4) + n_dof * 12 bytes of
+ * device memory plus an [n_elem][8]-double geometry scratch; row_ptr is copied, so
+ * dofmap, row_ptr and col may be freed afterwards. The call synchronises `stream`.
+ * Errors: FFC_EBOUNDS for a dof id outside [0, n_dof) or a (row, col) pair of a cell
+ * missing from the pattern; FFC_EINVAL for a row longer than 65535 entries, a row_ptr
+ * that is not monotone within [0, nnz], or n_elem * n_local >= 2^31.
+ */
+int ffc_row_plan_create(int64_t n_elem, int n_local, const int32_t* dofmap, int64_t n_dof, const int64_t* row_ptr,
+                        const int32_t* col, int64_t nnz, void* stream, ffc_row_plan** out);
+/* Rows, stored entries, longest row and most cells sharing one dof. */
+int ffc_row_plan_info(const ffc_row_plan* p, int64_t* n_dof, int64_t* nnz, int* max_row, int* max_incidence);
+void ffc_row_plan_destroy(ffc_row_plan* p);
+
+/*
+ * ffc_assemble_rows -- the assembled matrix of a mass or Poisson form (any degree,
+ * triangles and tetrahedra) by row-owner assembly with `plan`:
+ *   csr_val[k] = sum of A^K[i1][i2] over the cells and local pairs that map to entry k,
+ * for every k < nnz (overwritten). cells / vertices / n_vert as for ffc_tabulate, for
+ * the cells the plan was built from. precision FFC_FP32: G_K and the contraction in
+ * FP32 exactly as ffc_assemble computes them (the same contributions), FFC_FP64: in FP64.
+ * Two launches on `stream`: the geometry tensors into the plan's scratch, then the rows.
+ * Calls that share a plan must be ordered on one stream (they share the scratch).
+ * A non-finite G_K (a degenerate cell, FFC_FLAG_DEGENERATE) makes its rows NaN.
+ * Other forms: FFC_EUNSUPPORTED. The plan's n_local must equal the form's.
+ */
+int ffc_assemble_rows(const ffc_form* f, const ffc_row_plan* plan, const int32_t* cells, const double* vertices,
+                      int64_t n_vert, double* csr_val, int precision, void* stream);
 
 /*
  * ffc_status_poll -- synchronise `stream`, return the device status bits

@@ -43,6 +43,12 @@ SIGNATURES = {
     "ffc_batch_info": (ctypes.c_int, [c_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_longlong),
                                       ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     "ffc_batch_destroy": (None, [c_vp]),
+    "ffc_row_plan_create": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int, c_vp, ctypes.c_int64, c_vp, c_vp,
+                                           ctypes.c_int64, c_vp, ctypes.POINTER(c_vp)]),
+    "ffc_row_plan_info": (ctypes.c_int, [c_vp, c_i64p, c_i64p, ctypes.POINTER(ctypes.c_int),
+                                         ctypes.POINTER(ctypes.c_int)]),
+    "ffc_row_plan_destroy": (None, [c_vp]),
+    "ffc_assemble_rows": (ctypes.c_int, [c_vp, c_vp, c_vp, c_vp, ctypes.c_int64, c_vp, ctypes.c_int, c_vp]),
     "ffc_status_poll": (ctypes.c_int, [c_vp, c_u32p]),
     "ffc_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "ffc_last_error": (ctypes.c_char_p, []),

@@ -5,6 +5,8 @@ library's CUDA kernels). PyTorch provides device memory and streams.
     A_K = tabulate(form, cells, vertices)                 # [n_elem, n, n] on the GPU
     row_ptr, col, slot = csr_pattern(dofmap, n_dof)       # host, setup
     assemble(form, cells, vertices, slot_dev, csr_val)    # csr_val[slot] += A^K
+    plan = RowPlan(dofmap_dev, n_dof, row_ptr_dev, col_dev)  # mass / Poisson, once per mesh
+    assemble_rows(form, plan, cells, vertices, csr_val)   # csr_val = A (row-owner, exact sums)
 
 A linear form (SOURCE, rank 1) has element vectors [n_elem, n]; its assembly adds
 them into a global vector, with the dof map in place of the slots:
@@ -191,6 +193,60 @@ def assemble(form: Form, cells, vertices, slot, csr_val, coeffs=None, precision=
     val = _dev_ptr(csr_val, torch.float64, "csr_val")
     _check(lib().ffc_assemble(form.handle, n_elem, c, v, vertices.shape[0], w, s, val, csr_val.numel(), p,
                               _stream(stream)), "ffc_assemble")
+    return csr_val
+
+
+class RowPlan:
+    """Row view of a dof map and its CSR pattern for :func:`assemble_rows`
+    (ffc_row_plan_create; built on the device, synchronises the stream).
+
+    dofmap int32 [n_elem, n_local], row_ptr int64 [n_dof + 1] and col int32 [nnz] are
+    CUDA tensors (the pattern of :func:`csr_pattern`); they may be freed afterwards."""
+
+    def __init__(self, dofmap, n_dof: int, row_ptr, col, stream=None):
+        import torch
+
+        n_elem, n_local = dofmap.shape
+        d = _dev_ptr(dofmap, torch.int32, "dofmap")
+        rp = _dev_ptr(row_ptr, torch.int64, "row_ptr", (n_dof + 1,))
+        c = _dev_ptr(col, torch.int32, "col")
+        h = ctypes.c_void_p()
+        _check(lib().ffc_row_plan_create(n_elem, n_local, d, n_dof, rp, c, col.numel(), _stream(stream),
+                                         ctypes.byref(h)), "ffc_row_plan_create")
+        self._h = h
+        self.n_local = n_local
+        nd, nnz, mr, mi = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int(), ctypes.c_int()
+        _check(lib().ffc_row_plan_info(h, ctypes.byref(nd), ctypes.byref(nnz), ctypes.byref(mr), ctypes.byref(mi)),
+               "ffc_row_plan_info")
+        self.n_dof, self.nnz, self.max_row, self.max_incidence = nd.value, nnz.value, mr.value, mi.value
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            lib().ffc_row_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def assemble_rows(form: Form, plan: RowPlan, cells, vertices, csr_val, precision="fp32", stream=None):
+    """csr_val = the assembled matrix of a mass or Poisson form (overwritten, no zeroing
+    needed), by row-owner assembly with exact fixed-point sums (ffc_assemble_rows)."""
+    import torch
+
+    p = _prec(precision)
+    c = _dev_ptr(cells, torch.int32, "cells", (cells.shape[0], form.dim + 1))
+    v = _dev_ptr(vertices, torch.float64, "vertices")
+    val = _dev_ptr(csr_val, torch.float64, "csr_val", (plan.nnz,))
+    _check(lib().ffc_assemble_rows(form.handle, plan.handle, c, v, vertices.shape[0], val, p, _stream(stream)),
+           "ffc_assemble_rows")
     return csr_val
 
 

@@ -218,3 +218,26 @@ def test_scatter_add_arguments_are_validated_on_the_host():
     assert L.ffc_scatter_add(10, 4, None, 0, None, None, 5, None) == -1
     assert L.ffc_scatter_add(10, 4, None, 0, None, None, 2**31, None) == -1
     assert L.ffc_scatter_add(0, 4, None, 0, None, None, 5, None) == 0  # nothing to do
+
+
+def test_row_plan_and_row_assembly_arguments_are_validated_on_the_host():
+    import ctypes
+
+    import paper_1112_0402_gb300 as F
+
+    L = _lib()
+    out = ctypes.c_void_p()
+    buf = np.zeros(64, dtype=np.int64)  # stands in for device pointers: never dereferenced
+    fake = ctypes.c_void_p(buf.ctypes.data)
+    assert L.ffc_row_plan_create(10, 4, None, 5, fake, fake, 8, None, ctypes.byref(out)) == -1  # no dofmap
+    assert L.ffc_row_plan_create(10, 4, fake, 5, None, fake, 8, None, ctypes.byref(out)) == -1  # no row_ptr
+    assert L.ffc_row_plan_create(10, 4, fake, 0, fake, fake, 8, None, ctypes.byref(out)) == -1  # no rows
+    assert L.ffc_row_plan_create(10, 0, fake, 5, fake, fake, 8, None, ctypes.byref(out)) == -1  # no local dofs
+    assert L.ffc_row_plan_create(10, 4, fake, 5, fake, fake, 8, None, None) == -1               # no output
+    assert L.ffc_row_plan_create(2**29, 4, fake, 5, fake, fake, 8, None, ctypes.byref(out)) == -1  # E*n >= 2^31
+    assert L.ffc_row_plan_info(None, None, None, None, None) == -1
+    L.ffc_row_plan_destroy(None)
+    f = F.Form(F.POISSON, F.TETRAHEDRON, 2)
+    assert L.ffc_assemble_rows(f.handle, None, fake, fake, 5, fake, 1, None) == -1  # no plan
+    assert L.ffc_assemble_rows(None, fake, fake, fake, 5, fake, 1, None) == -1      # no form
+    assert L.ffc_assemble_rows(f.handle, fake, fake, fake, 5, fake, 2, None) == -1  # tensor-core precision
