@@ -50,7 +50,8 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["tet_scalar", "ns_vp2", "batched", "adjoint", "source"], default="tet_scalar",
+    ap.add_argument("--workload", choices=["tet_scalar", "ns_vp2", "batched", "adjoint", "source", "rows"],
+                    default="tet_scalar",
                     help="tet_scalar is the headline; the others print their own line")
     ap.add_argument("--precision", default="fp32", help="contraction arithmetic of the headline step")
     ap.add_argument("--n", type=int, default=48, help="hexes per axis")
@@ -144,6 +145,8 @@ def build_workload(F, n, device):
         row_ptr, col, slot = F.csr_pattern(p.dofmap, p.n_dof)
         slot_d = torch.as_tensor(slot, device=device)
         del slot
+        if q >= 3:  # the row-owner assembly of the detail section needs the pattern
+            ctx.setdefault("patterns", {})[q] = (p.dofmap, p.n_dof, row_ptr, col)
         for form in FORMS:
             ctx["problems"].append({
                 "form": form, "q": q, "F": F.Form(form, F.TETRAHEDRON, q), "n_local": p.n_local,
@@ -430,7 +433,11 @@ def main():
                          "algorithmic_gb": alg_bytes_assemble(ctx, dpr) / 1e9,
                          "kernel": f"assemble {FORM_NAME[dpr['form']]} P{dpr['q']} ({args.precision})",
                          "launch_ms": per_launch[dom] * 1e3,
-                         "fp64_atomics_per_s": n_elem * dpr["n_local"] ** 2 / per_launch[dom]},
+                         "fp64_atomics_per_s": n_elem * dpr["n_local"] ** 2 / per_launch[dom],
+                         "fp64_atomic_ceiling_per_s": (detail or {}).get("fp64_atomic_ceiling_per_s"),
+                         "fp64_atomics_frac": (n_elem * dpr["n_local"] ** 2 / per_launch[dom] /
+                                               detail["fp64_atomic_ceiling_per_s"])
+                         if detail and detail.get("fp64_atomic_ceiling_per_s") else None},
             "per_launch_ms": {f"{FORM_NAME[p['form']]}_p{p['q']}": round(per_launch[k] * 1e3, 4)
                               for k, p in enumerate(ctx["problems"])},
             "clocks": clk, "gpu_launches": P * args.steps, "e2e": e2e, "cpu_baseline": cpu, "detail": detail,
@@ -511,7 +518,41 @@ def measure_detail(F, ctx, args, device, reps=5):
             rec["assemble_fp32_with_zero_ms"] = a.elapsed_time(b) / 3
             del A
             torch.cuda.empty_cache()
+            if pr["form"] == 1:
+                # the FP64 atomic ceiling of the GPU: ffc_scatter_add of as many FP32 values as
+                # the P4 matrix has entries, through the identity slot map (consecutive
+                # addresses, each entry once: no conflicts, fully coalesced)
+                ident = torch.arange(pr["nnz"], dtype=torch.int32, device=device)
+                ones = torch.ones(pr["nnz"], dtype=torch.float32, device=device)
+                F.scatter_add(ones, ident, pr["val"])
+                torch.cuda.synchronize()
+                a.record()
+                for _ in range(3):
+                    F.scatter_add(ones, ident, pr["val"])
+                b.record()
+                torch.cuda.synchronize()
+                out["fp64_atomic_ceiling_per_s"] = pr["nnz"] / (a.elapsed_time(b) / 3 / 1e3)
+                del ident, ones
+                torch.cuda.empty_cache()
         out[key] = rec
+    # row-owner assembly (ffc_assemble_rows: exact fixed-point sums, no atomics, no zeroing)
+    for q, (dofmap, n_dof, row_ptr, col) in sorted(ctx.get("patterns", {}).items()):
+        plan = F.RowPlan(torch.as_tensor(dofmap, device=device), n_dof, torch.as_tensor(row_ptr, device=device),
+                         torch.as_tensor(col, device=device))
+        for pr in ctx["problems"]:
+            if pr["q"] != q:
+                continue
+            F.assemble_rows(pr["F"], plan, ctx["cells"], ctx["verts"], pr["val"], precision=args.precision)
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            for _ in range(reps):
+                F.assemble_rows(pr["F"], plan, ctx["cells"], ctx["verts"], pr["val"], precision=args.precision)
+            b.record()
+            torch.cuda.synchronize()
+            out[f"{FORM_NAME[pr['form']]}_p{q}"]["assemble_rows_ms"] = a.elapsed_time(b) / reps
+        del plan
+        torch.cuda.empty_cache()
     assert F.status_poll() == 0
     return out
 
@@ -754,6 +795,76 @@ def run_other(args):
                     "clocks": clk, "gpu_launches": 2 * args.steps,
                     "cpu_baseline": {"value": rate, "unit": "elem/s", "cores": cores, "kind": "oracle",
                                      "sample": f"{S} cells"}, "detail": detail})
+    elif args.workload == "rows":
+        # the headline's eight problems by row-owner assembly (ffc_assemble_rows): exact
+        # fixed-point sums, every CSR value written once, no atomics and no zeroing
+        mesh = W.tet_scalar_mesh(args.n)
+        cells = torch.as_tensor(mesh.cells, device=device)
+        verts = torch.as_tensor(mesh.vertices, device=device)
+        probs = []
+        for q in DEGREES:
+            p = W.make_problem(mesh, W.POISSON, q)
+            row_ptr, col, _ = F.csr_pattern(p.dofmap, p.n_dof, with_slots=False)
+            plan = F.RowPlan(torch.as_tensor(p.dofmap, device=device), p.n_dof,
+                             torch.as_tensor(row_ptr, device=device), torch.as_tensor(col, device=device))
+            del col
+            for form in FORMS:
+                probs.append({"form": form, "q": q, "F": F.Form(form, F.TETRAHEDRON, q), "plan": plan,
+                              "n_local": p.n_local, "nnz": plan.nnz,
+                              "val": torch.empty(plan.nnz, dtype=torch.float64, device=device)})
+        P = len(probs)
+        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(P * args.steps)]
+
+        def rows_step(s=None):
+            for k, pr in enumerate(probs):
+                if s is not None:
+                    ev[s * P + k][0].record()
+                F.assemble_rows(pr["F"], pr["plan"], cells, verts, pr["val"], precision=args.precision)
+                if s is not None:
+                    ev[s * P + k][1].record()
+
+        for _ in range(args.warmup):
+            rows_step()
+        torch.cuda.synchronize()
+        clocks.start()
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record()
+        for s_ in range(args.steps):
+            rows_step(s_)
+        t1.record()
+        torch.cuda.synchronize()
+        clk = clocks.stop()
+        assert F.status_poll() == 0
+        t = t0.elapsed_time(t1) / 1e3 / args.steps
+        per = [sum(ev[s_ * P + k][0].elapsed_time(ev[s_ * P + k][1]) for s_ in range(args.steps)) / 1e3 / args.steps
+               for k in range(P)]
+        dom = int(np.argmax(per))
+        dpr = probs[dom]
+        # algorithmic bytes of one row-owner assembly: cells, vertices, the dof-map
+        # equivalent (4n per cell) and the CSR values written once
+        byts = mesh.n_elem * (16 + 4 * dpr["n_local"]) + mesh.n_vert * 24 + 8 * dpr["nnz"]
+        cpu = None
+        if not args.no_cpu_baseline:
+            pool, _ = oracle_pool()
+            S, t_cpu = cpu_oracle_step(args.n, REF_FRACTION, pool)
+            pool.close()
+            pool.join()
+            cpu = {"value": P * S / t_cpu, "unit": "elem/s", "cores": cores, "kind": "oracle",
+                   "sample": f"{S} cells of each of the 8 problems, element tensors and Algorithm 2, {t_cpu:.1f} s"}
+        out.update({"metric": "element tensors/s (row-owner assembly, exact sums, mass+Poisson P1..P4 on 48^3x6 tets)",
+                    "value": P * mesh.n_elem / t, "ms_per_step": t * 1e3, "dtype": "f32" if args.precision != "fp64"
+                    else "f64",
+                    "config": {"workload": f"tet_scalar_{args.n}_rows", "cells": mesh.n_elem,
+                               "problems": [f"{FORM_NAME[p_['form']]}_p{p_['q']}" for p_ in probs],
+                               "csr_accumulation": "exact (64-bit fixed point), rounded once to f64",
+                               "l2": "inputs larger than L2: ~8 GB of positions and CSR values per step"},
+                    "roofline": {"bound": "hbm", "achieved": byts / per[dom] / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                                 "frac": byts / per[dom] / 1e9 / hbm_peak, "traffic": None, "peak_kind": peak_kind,
+                                 "kernel": f"rows_assemble {FORM_NAME[dpr['form']]} P{dpr['q']}",
+                                 "launch_ms": per[dom] * 1e3},
+                    "per_launch_ms": {f"{FORM_NAME[p_['form']]}_p{p_['q']}": round(per[k] * 1e3, 4)
+                                      for k, p_ in enumerate(probs)},
+                    "clocks": clk, "gpu_launches": 2 * P * args.steps, "cpu_baseline": cpu})
     else:  # adjoint
         p, u, v = W.adjoint_p2(56 if args.n == 48 else args.n)
         m = p.mesh
