@@ -238,8 +238,9 @@ typedef struct {
 
 /* zero_csr != 0: every run first zeroes each item's csr_val (a fresh assembly). */
 int ffc_batch_create(const ffc_batch_item* items, int n_items, int zero_csr, ffc_batch** out);
-/* Times the eight tile variants (256 or 416 threads per block x 16, 32, 64 or 128 cells
- * per thread group and tile) on the caller's data, keeps the fastest and returns it
+/* Times the twelve tile variants (256 threads per block, or 416 with registers bounded for
+ * one or for two resident blocks; x 16, 32, 64 or 128 cells per thread group and tile) on
+ * the caller's data, keeps the fastest and returns it
  * (either output pointer may be NULL); leaves every csr_val zeroed. */
 int ffc_batch_tune(ffc_batch* b, void* stream, int* cells_per_tile_group, int* threads_per_block);
 /* One persistent launch (use_graph = 0), or the same work captured once into a CUDA

@@ -10,8 +10,9 @@
 // shared CUDA-core tile body: FP64 geometry, FP32 contraction, FP64 atomic scatter
 // (elasticity through the block-structured contraction, the other forms densely).
 //
-// The tile variant (256 or 416 threads per block x 16, 32, 64 or 128 cells per thread
-// group and tile) is chosen by timing all eight on the caller's data (ffc_batch_tune). A run can be captured
+// The tile variant (256 threads per block, or 416 with registers bounded for one or two
+// resident blocks; x 16, 32, 64 or 128 cells per thread group and tile) is chosen by
+// timing all twelve on the caller's data (ffc_batch_tune). A run can be captured
 // once into a CUDA graph (queue reset, optional CSR zeroing, kernel) and replayed.
 #include <cuda_runtime.h>
 
@@ -28,11 +29,14 @@
 namespace ffc {
 namespace {
 
-// Tile variants the autotuner times: block size x cells per thread group and tile.
-constexpr int N_VARIANTS = 8;
-// 416 threads: 400 pairs of elasticity P3, 4 x 100 of elasticity P2 and Poisson P2
-constexpr int VARIANT_BLOCK[N_VARIANTS] = {256, 256, 256, 256, 416, 416, 416, 416};
-constexpr int VARIANT_KE[N_VARIANTS] = {16, 32, 64, 128, 16, 32, 64, 128};
+// Tile variants the autotuner times: block size x cells per thread group and tile x
+// resident blocks per SM the registers are bounded for.
+constexpr int N_VARIANTS = 12;
+// 416 threads: 400 pairs of elasticity P3, 4 x 100 of elasticity P2 and Poisson P2;
+// 416 x 2 resident blocks caps the registers at 72 (a few spills, twice the warps)
+constexpr int VARIANT_BLOCK[N_VARIANTS] = {256, 256, 256, 256, 416, 416, 416, 416, 416, 416, 416, 416};
+constexpr int VARIANT_KE[N_VARIANTS] = {16, 32, 64, 128, 16, 32, 64, 128, 16, 32, 64, 128};
+constexpr int VARIANT_MINB[N_VARIANTS] = {2, 2, 2, 2, 1, 1, 1, 1, 2, 2, 2, 2};
 
 // Forms the batched kernel carries, by code.
 enum : int { CODE_ELAST_P1 = 0, CODE_ELAST_P2, CODE_ELAST_P3, CODE_POISSON_P1, CODE_POISSON_P2, CODE_MASS_P1,
@@ -77,8 +81,8 @@ __device__ __forceinline__ void run_tile(const SimtParams& p, long long tile, un
   }
 }
 
-template <int BLK, int KE>
-__global__ void __launch_bounds__(BLK, BLK > 256 ? 1 : 2)
+template <int BLK, int KE, int MINB>
+__global__ void __launch_bounds__(BLK, MINB)
     batch_assemble_kernel(const WorkItem* __restrict__ items, int n_items, long long total_tiles,
                           unsigned long long* queue) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -151,7 +155,11 @@ CodeInfo code_info_variant(int variant, int code) {
     case 4: return code_info<4>(code);
     case 5: return code_info<5>(code);
     case 6: return code_info<6>(code);
-    default: return code_info<7>(code);
+    case 7: return code_info<7>(code);
+    case 8: return code_info<8>(code);
+    case 9: return code_info<9>(code);
+    case 10: return code_info<10>(code);
+    default: return code_info<11>(code);
   }
 }
 
@@ -231,8 +239,8 @@ int build_table(ffc_batch* b, int variant) {
 
 template <int V>
 int launch_variant(ffc_batch* b, cudaStream_t s) {
-  constexpr int variant = V, BLK = VARIANT_BLOCK[V], KE = VARIANT_KE[V];
-  auto kern = batch_assemble_kernel<BLK, KE>;
+  constexpr int variant = V, BLK = VARIANT_BLOCK[V], KE = VARIANT_KE[V], MINB = VARIANT_MINB[V];
+  auto kern = batch_assemble_kernel<BLK, KE, MINB>;
   static bool attr = false;
   if (!attr) {
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024) != cudaSuccess)
@@ -266,7 +274,11 @@ int enqueue(ffc_batch* b, int variant, cudaStream_t s) {
     case 4: return launch_variant<4>(b, s);
     case 5: return launch_variant<5>(b, s);
     case 6: return launch_variant<6>(b, s);
-    default: return launch_variant<7>(b, s);
+    case 7: return launch_variant<7>(b, s);
+    case 8: return launch_variant<8>(b, s);
+    case 9: return launch_variant<9>(b, s);
+    case 10: return launch_variant<10>(b, s);
+    default: return launch_variant<11>(b, s);
   }
 }
 

@@ -58,7 +58,8 @@ struct BlockCfg {
   static constexpr int NSL = DIAG ? NP2 : D * NS * NS;     // slots: pairs, or row slots (s1, c2, s2)
   // about 256 threads: whole groups of NSL slots, or up to 512 threads with several
   // slots each, rounded up to whole warps
-  static constexpr int NT0 = NSL >= 256 ? (NSL < 512 ? NSL : 512) : NSL * (256 / NSL);
+  // (FP32 with 512 or more slots: 416 threads, two resident CTAs; see MIN_BLOCKS)
+  static constexpr int NT0 = NSL >= 256 ? (NSL < 512 ? NSL : (sizeof(T) == 4 ? 416 : 512)) : NSL * (256 / NSL);
   static constexpr int NT = BLOCK > 0 ? BLOCK : (NT0 + 31) / 32 * 32;
   static constexpr int GRP = NT >= NSL ? NT / NSL : 1;  // thread groups; a tile's cells are dealt to them
   static constexpr int PPT = (NSL + NT - 1) / NT;       // slots per thread
@@ -70,9 +71,9 @@ struct BlockCfg {
   static constexpr size_t R_BYTES = REG_R ? 0 : size_t(NP2) * KRP * sizeof(T);
   static constexpr size_t W_BYTES = size_t(E) * NCOEF * sizeof(double);
   static constexpr size_t SMEM = G_BYTES + R_BYTES + W_BYTES;
-  // register budget of the single-form FP32 kernel: about 16 resident warps per SM (one
-  // CTA of 512 threads with up to 128 registers, two of 257..511, three of up to 256);
-  // FP64 (bound by the FP64 pipe) keeps its reduced rows in registers without spills
+  // register budget of the single-form FP32 kernel: two resident CTAs of 257..511 threads
+  // (up to 78 registers), three of up to 256; FP64 (bound by the FP64 pipe) keeps its
+  // reduced rows in registers without spills
   static constexpr int MIN_BLOCKS = sizeof(T) == 8 ? 1 : (NT >= 512 ? 1 : (NT > 256 ? 2 : 3));
 };
 
