@@ -516,17 +516,27 @@ __global__ void __launch_bounds__(WS_THREADS, 1) tc_ws_kernel(TcParams p) {
             for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(rv[j]);
           }
           if (i < C::NN) {
+            const long long ec = e0 + c * 32;
+            if constexpr (!ASSEMBLE) {
+              // one base address per 32 cells; the cells' rows are constant offsets from it
+              float* dst = p.out + ec * C::NN + i;
+              if (ec + 32 <= p.n_elem) {
 #pragma unroll
-            for (int j = 0; j < 32; ++j) {
-              const long long e = e0 + c * 32 + j;
-              if (e < p.n_elem) {
-                const long long o = e * C::NN + i;
-                if constexpr (ASSEMBLE) {
+                for (int j = 0; j < 32; ++j) __stcs(dst + j * C::NN, v[j]);
+              } else {
+#pragma unroll
+                for (int j = 0; j < 32; ++j)
+                  if (ec + j < p.n_elem) __stcs(dst + j * C::NN, v[j]);
+              }
+            } else {
+#pragma unroll
+              for (int j = 0; j < 32; ++j) {
+                const long long e = ec + j;
+                if (e < p.n_elem) {
+                  const long long o = e * C::NN + i;
                   const int s = __ldg(p.slot + o);
                   if (s >= 0 && s < p.nnz) atomicAdd(p.csr_val + s, double(v[j]));
                   else atomicOr(p.status, FFC_FLAG_BOUNDS);
-                } else {
-                  __stcs(p.out + o, v[j]);
                 }
               }
             }
