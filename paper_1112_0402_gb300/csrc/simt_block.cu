@@ -7,11 +7,12 @@ namespace {
 template <int D, int FORM, int Q, typename T, bool ASSEMBLE>
 int run(const LaunchArgs& a) {
   using C = BlockCfg<D, FORM, Q, T>;
+  constexpr size_t SMEM = C::SMEM + BlockStaging<C, T, ASSEMBLE>::BYTES;
   auto kern = simt_block_kernel<D, FORM, Q, T, ASSEMBLE>;
   static int sms = 0, per_sm = 1;
   if (sms == 0) {
-    if (C::SMEM > 48 * 1024 &&
-        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(C::SMEM)) != cudaSuccess)
+    if (SMEM > 48 * 1024 &&
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(SMEM)) != cudaSuccess)
       return FFC_ECUDA;
     // elasticity: the whole unified L1 / shared array as shared memory, so the nine
     // geometry blocks of several resident CTAs fit (measured faster; the convection
@@ -23,7 +24,7 @@ int run(const LaunchArgs& a) {
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, C::NT, C::SMEM) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, C::NT, SMEM) != cudaSuccess)
       return FFC_ECUDA;
     if (per_sm < 1) per_sm = 1;
   }
@@ -44,7 +45,7 @@ int run(const LaunchArgs& a) {
   const long long n_tiles = (a.n_elem + C::E - 1) / C::E;
   long long grid = (long long)sms * per_sm;
   if (grid > n_tiles) grid = n_tiles;
-  kern<<<unsigned(grid), C::NT, C::SMEM, static_cast<cudaStream_t>(a.stream)>>>(p);
+  kern<<<unsigned(grid), C::NT, SMEM, static_cast<cudaStream_t>(a.stream)>>>(p);
   return cudaPeekAtLastError() == cudaSuccess ? FFC_OK : FFC_ECUDA;
 }
 

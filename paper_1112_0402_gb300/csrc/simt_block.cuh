@@ -82,6 +82,37 @@ struct BlockRows {
   T rr[C::REG_R ? C::PPT : 1][C::REG_R ? C::KR : 1];  // reduced rows of the thread's slots
 };
 
+// Tabulate of the single-form FP32 convection kernel: the element tensors of CELLS cells
+// at a time are put together in shared memory (the off-diagonal blocks, always zero, are
+// written there once), then one thread writes them to A_K with a TMA bulk copy, two
+// buffers deep, so A_K leaves the SM as whole contiguous lines (measured on 384,000 cells:
+// 0.362 ms with direct stores; 0.297 ms staged with 4-cell chunks and 128-cell tiles,
+// against 0.31-0.34 ms for 2-, 6- or 8-cell chunks or 64-cell tiles).
+template <class C, typename T, bool ASSEMBLE>
+struct BlockStaging {
+  static constexpr bool ON = !ASSEMBLE && C::DIAG && sizeof(T) == 4;
+  static constexpr int CELLS = 4;
+  static constexpr size_t BUF = size_t(CELLS) * C::NN * sizeof(T);  // a multiple of 16 bytes
+  static constexpr size_t BYTES = ON ? 2 * BUF : 0;
+};
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+// shared -> global bulk copy (addresses 16-byte aligned, size a multiple of 16)
+__device__ __forceinline__ void bulk_s2g(void* gdst, const void* ssrc, unsigned bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;\n" ::"l"(gdst), "r"(smem_u32(ssrc)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;\n" ::: "memory"); }
+template <int PENDING>
+__device__ __forceinline__ void bulk_wait_read() {
+  asm volatile("cp.async.bulk.wait_group.read %0;\n" ::"n"(PENDING) : "memory");
+}
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+
 // The thread's slots: slot j is q = t mod NSL (NT >= NSL, group t / NSL) or q = t + j*NT
 // (NT < NSL, one group); -1: none. Slot q is (s1, c2, s2) with s2 fastest.
 template <class C>
@@ -123,7 +154,7 @@ __device__ __forceinline__ void block_rows_init(const void* r, BlockRows<C, T>& 
 // contracts its pairs with every block of the group's cells. Contains block barriers.
 template <class C, int D, int FORM, int Q, typename T, bool ASSEMBLE>
 __device__ __forceinline__ void block_tile(const SimtParams& p, long long tile, unsigned char* smem,
-                                           const BlockRows<C, T>& br) {
+                                           const BlockRows<C, T>& br, int* staged_chunks = nullptr) {
   T* Gs = reinterpret_cast<T*>(smem);                                       // [E][NB][KRP]
   const T* Rs = reinterpret_cast<const T*>(smem + C::G_BYTES);              // [NP2][KRP]
   double* Ws = reinterpret_cast<double*>(smem + C::G_BYTES + C::R_BYTES);   // [E][NCOEF]
@@ -236,63 +267,96 @@ __device__ __forceinline__ void block_tile(const SimtParams& p, long long tile, 
     }
     return acc;
   };
+  using SG = BlockStaging<C, T, ASSEMBLE>;
+  if constexpr (SG::ON) {
+    // chunks of SG::CELLS cells; within a chunk the groups take cells grp, grp + GRP, ...
+    T* stage = reinterpret_cast<T*>(smem + C::SMEM);
+    for (int c0 = 0; c0 < nc; c0 += SG::CELLS) {
+      const int b = *staged_chunks & 1;
+      T* buf = stage + b * (SG::BUF / sizeof(T));
+      if (*staged_chunks >= 2 && t == 0) bulk_wait_read<1>();  // the copy that last read buf is done
+      __syncthreads();
+      const int ncc = nc - c0 < SG::CELLS ? nc - c0 : SG::CELLS;
 #pragma unroll
-  for (int j = 0; j < C::PPT; ++j) {
-    const int q = slot_of<C>(t, j);
-    if (q < 0) continue;
-    int s1, s2, c2 = 0;
-    if constexpr (DIAG) {
-      s1 = q / C::NS;
-      s2 = q % C::NS;
-    } else {
-      s2 = q % C::NS;
-      c2 = (q / C::NS) % D;
-      s1 = q / (C::NS * D);
-    }
-    const T* rrow = Rs + size_t(s1 * C::NS + s2) * C::KRP;
-    // positions of the slot's entries: all d*d blocks (c1, c2) of the pair (convection),
-    // or the d entries ((c1,s1),(c2,s2)) of the row slot (elasticity)
-    int pos[NPOS];
-    bool live_pos[NPOS];  // assembly: structural zeros add nothing
+      for (int j = 0; j < C::PPT; ++j) {
+        const int q = slot_of<C>(t, j);
+        if (q < 0) continue;
+        const int s1 = q / C::NS, s2 = q % C::NS;
+        const T* rrow = Rs + size_t(s1 * C::NS + s2) * C::KRP;
+        for (int el = c0 + grp; el < c0 + ncc; el += C::GRP) {
+          const T v = contract(Gs + size_t(el) * C::NB * C::KRP, j, rrow);
+          T* cb = buf + size_t(el - c0) * C::NN;
 #pragma unroll
-    for (int m = 0; m < NPOS; ++m) {
-      const int c1 = DIAG ? m / D : m;
-      const int cc2 = DIAG ? m % D : c2;
-      pos[m] = (c1 * C::NS + s1) * C::N + cc2 * C::NS + s2;
-      live_pos[m] = !DIAG || c1 == cc2;
-    }
-    // assembly: the slots of the next cell are loaded while this cell's atomics issue
-    int sl_next[ASSEMBLE ? NPOS : 1];
-    if constexpr (ASSEMBLE) {
-#pragma unroll
-      for (int m = 0; m < NPOS; ++m)
-        sl_next[m] = (grp < nc && live_pos[m]) ? __ldg(p.slot + (e0 + grp) * C::NN + pos[m]) : -1;
-    }
-#pragma unroll 1
-    for (int el = grp; el < nc; el += C::GRP) {
-      const long long e = e0 + el;
-      int sl[ASSEMBLE ? NPOS : 1];
-      if constexpr (ASSEMBLE) {
-        const int en = el + C::GRP;
-#pragma unroll
-        for (int m = 0; m < NPOS; ++m) {
-          sl[m] = sl_next[m];
-          sl_next[m] = (en < nc && live_pos[m]) ? __ldg(p.slot + (e0 + en) * C::NN + pos[m]) : -1;
+          for (int c = 0; c < D; ++c) cb[(c * C::NS + s1) * C::N + c * C::NS + s2] = v;
         }
       }
-      const T* gcell = Gs + size_t(el) * C::NB * C::KRP;
-      T vdiag = T(0);
-      if constexpr (DIAG) vdiag = contract(gcell, j, rrow);
+      fence_async_smem();
+      __syncthreads();
+      if (t == 0) {
+        bulk_s2g(static_cast<T*>(p.out) + (e0 + c0) * C::NN, buf, unsigned(ncc * C::NN * sizeof(T)));
+        bulk_commit();
+      }
+      ++*staged_chunks;
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < C::PPT; ++j) {
+      const int q = slot_of<C>(t, j);
+      if (q < 0) continue;
+      int s1, s2, c2 = 0;
+      if constexpr (DIAG) {
+        s1 = q / C::NS;
+        s2 = q % C::NS;
+      } else {
+        s2 = q % C::NS;
+        c2 = (q / C::NS) % D;
+        s1 = q / (C::NS * D);
+      }
+      const T* rrow = Rs + size_t(s1 * C::NS + s2) * C::KRP;
+      // positions of the slot's entries: all d*d blocks (c1, c2) of the pair (convection),
+      // or the d entries ((c1,s1),(c2,s2)) of the row slot (elasticity)
+      int pos[NPOS];
+      bool live_pos[NPOS];  // assembly: structural zeros add nothing
 #pragma unroll
       for (int m = 0; m < NPOS; ++m) {
-        if (ASSEMBLE && !live_pos[m]) continue;
-        const T v = DIAG ? (live_pos[m] ? vdiag : T(0)) : contract(gcell + (m * D + c2) * C::KRP, j, rrow);
+        const int c1 = DIAG ? m / D : m;
+        const int cc2 = DIAG ? m % D : c2;
+        pos[m] = (c1 * C::NS + s1) * C::N + cc2 * C::NS + s2;
+        live_pos[m] = !DIAG || c1 == cc2;
+      }
+      // assembly: the slots of the next cell are loaded while this cell's atomics issue
+      int sl_next[ASSEMBLE ? NPOS : 1];
+      if constexpr (ASSEMBLE) {
+#pragma unroll
+        for (int m = 0; m < NPOS; ++m)
+          sl_next[m] = (grp < nc && live_pos[m]) ? __ldg(p.slot + (e0 + grp) * C::NN + pos[m]) : -1;
+      }
+#pragma unroll 1
+      for (int el = grp; el < nc; el += C::GRP) {
+        const long long e = e0 + el;
+        int sl[ASSEMBLE ? NPOS : 1];
         if constexpr (ASSEMBLE) {
-          const int sv = sl[m];
-          if (sv >= 0 && sv < p.nnz) atomicAdd(p.csr_val + sv, double(v));
-          else atomicOr(p.status, FFC_FLAG_BOUNDS);
-        } else {
-          __stcs(static_cast<T*>(p.out) + e * C::NN + pos[m], v);
+          const int en = el + C::GRP;
+#pragma unroll
+          for (int m = 0; m < NPOS; ++m) {
+            sl[m] = sl_next[m];
+            sl_next[m] = (en < nc && live_pos[m]) ? __ldg(p.slot + (e0 + en) * C::NN + pos[m]) : -1;
+          }
+        }
+        const T* gcell = Gs + size_t(el) * C::NB * C::KRP;
+        T vdiag = T(0);
+        if constexpr (DIAG) vdiag = contract(gcell, j, rrow);
+#pragma unroll
+        for (int m = 0; m < NPOS; ++m) {
+          if (ASSEMBLE && !live_pos[m]) continue;
+          const T v = DIAG ? (live_pos[m] ? vdiag : T(0)) : contract(gcell + (m * D + c2) * C::KRP, j, rrow);
+          if constexpr (ASSEMBLE) {
+            const int sv = sl[m];
+            if (sv >= 0 && sv < p.nnz) atomicAdd(p.csr_val + sv, double(v));
+            else atomicOr(p.status, FFC_FLAG_BOUNDS);
+          } else {
+            __stcs(static_cast<T*>(p.out) + e * C::NN + pos[m], v);
+          }
         }
       }
     }
@@ -304,12 +368,21 @@ template <int D, int FORM, int Q, typename T, bool ASSEMBLE>
 __global__ void __launch_bounds__(BlockCfg<D, FORM, Q, T>::NT, BlockCfg<D, FORM, Q, T>::MIN_BLOCKS)
     simt_block_kernel(SimtParams p) {
   using C = BlockCfg<D, FORM, Q, T>;
+  using SG = BlockStaging<C, T, ASSEMBLE>;
   extern __shared__ __align__(16) unsigned char smem[];
   BlockRows<C, T> rows;
   block_rows_init<C, D, FORM, T>(p.a0, rows, smem);
+  if constexpr (SG::ON) {  // the zero blocks of both staging buffers, written once
+    T* stage = reinterpret_cast<T*>(smem + C::SMEM);
+    for (size_t k = threadIdx.x; k < SG::BYTES / sizeof(T); k += C::NT) stage[k] = T(0);
+  }
+  int staged_chunks = 0;
   const long long n_tiles = (p.n_elem + C::E - 1) / C::E;
   for (long long tile = blockIdx.x; tile < n_tiles; tile += gridDim.x)
-    block_tile<C, D, FORM, Q, T, ASSEMBLE>(p, tile, smem, rows);
+    block_tile<C, D, FORM, Q, T, ASSEMBLE>(p, tile, smem, rows, &staged_chunks);
+  if constexpr (SG::ON) {
+    if (threadIdx.x == 0) bulk_wait_all();  // shared memory stays valid until the copies are done
+  }
 }
 
 }  // namespace ffc
