@@ -85,13 +85,15 @@ struct BlockRows {
 // Tabulate of the single-form FP32 convection kernel: the element tensors of CELLS cells
 // at a time are put together in shared memory (the off-diagonal blocks, always zero, are
 // written there once), then one thread writes them to A_K with a TMA bulk copy, two
-// buffers deep, so A_K leaves the SM as whole contiguous lines (measured on 384,000 cells:
-// 0.362 ms with direct stores; 0.297 ms staged with 4-cell chunks and 128-cell tiles,
-// against 0.31-0.34 ms for 2-, 6- or 8-cell chunks or 64-cell tiles).
+// buffers deep, so A_K leaves the SM as whole contiguous lines instead of runs of n_s
+// floats. Convection P2 on 384,000 cells: 0.362 ms with direct stores; 0.297 ms staged
+// with 4-cell chunks and 128-cell tiles, against 0.31-0.34 ms for 2-, 6- or 8-cell chunks
+// or 64-cell tiles. Elasticity, whose row-slot stores are already contiguous runs of a
+// row, writes directly (staged in 2-cell chunks its P3 tabulate went 0.513 -> 0.608 ms).
 template <class C, typename T, bool ASSEMBLE>
 struct BlockStaging {
   static constexpr bool ON = !ASSEMBLE && C::DIAG && sizeof(T) == 4;
-  static constexpr int CELLS = 4;
+  static constexpr int CELLS = C::GRP > 4 ? C::GRP : 4;  // at least one cell per thread group
   static constexpr size_t BUF = size_t(CELLS) * C::NN * sizeof(T);  // a multiple of 16 bytes
   static constexpr size_t BYTES = ON ? 2 * BUF : 0;
 };
@@ -281,13 +283,22 @@ __device__ __forceinline__ void block_tile(const SimtParams& p, long long tile, 
       for (int j = 0; j < C::PPT; ++j) {
         const int q = slot_of<C>(t, j);
         if (q < 0) continue;
-        const int s1 = q / C::NS, s2 = q % C::NS;
+        const int s2 = q % C::NS;
+        const int s1 = DIAG ? q / C::NS : q / (C::NS * D);
+        const int c2 = DIAG ? 0 : (q / C::NS) % D;
         const T* rrow = Rs + size_t(s1 * C::NS + s2) * C::KRP;
         for (int el = c0 + grp; el < c0 + ncc; el += C::GRP) {
-          const T v = contract(Gs + size_t(el) * C::NB * C::KRP, j, rrow);
+          const T* gcell = Gs + size_t(el) * C::NB * C::KRP;
           T* cb = buf + size_t(el - c0) * C::NN;
+          if constexpr (DIAG) {  // one value on the d diagonal positions
+            const T v = contract(gcell, j, rrow);
 #pragma unroll
-          for (int c = 0; c < D; ++c) cb[(c * C::NS + s1) * C::N + c * C::NS + s2] = v;
+            for (int c = 0; c < D; ++c) cb[(c * C::NS + s1) * C::N + c * C::NS + s2] = v;
+          } else {  // the row slot's d entries ((c1, s1), (c2, s2))
+#pragma unroll
+            for (int c1 = 0; c1 < D; ++c1)
+              cb[(c1 * C::NS + s1) * C::N + c2 * C::NS + s2] = contract(gcell + (c1 * D + c2) * C::KRP, j, rrow);
+          }
         }
       }
       fence_async_smem();

@@ -322,24 +322,25 @@ def test_full_size_tet_workload_sampled(F, form, q, prec):
         assert rs.abs().max().item() < tol * val.abs().max().item() * 10
 
 
-@pytest.mark.parametrize("q", [1, 2])
-def test_convection_block_tabulate_ragged_counts(F, q):
-    """FP32 convection through the block algorithm writes A_K through shared-memory staging
-    and bulk copies of 4 cells at a time: every cell count (chunk and tile remainders,
-    several tiles per CTA) must come out complete and exact, with nothing written past
-    the last cell."""
+@pytest.mark.parametrize("form,q", [(W.NS_CONVECTION, 1), (W.NS_CONVECTION, 2), (W.ELASTICITY, 1),
+                                    (W.ELASTICITY, 2), (W.ELASTICITY, 3)])
+def test_block_tabulate_ragged_counts(F, form, q):
+    """The FP32 block kernels write A_K through shared-memory staging and bulk copies of a
+    few cells at a time: every cell count (chunk and tile remainders) must come out
+    complete and exact, with nothing written past the last cell."""
     import torch
 
-    p = _case(3, 3, W.NS_CONVECTION, q)
+    p = _case(3, 3, form, q)
     ref = _oracle(p)
-    form = F.Form(W.NS_CONVECTION, 3, q, algorithm=F.ALG_BLOCK)
+    fm = F.Form(form, 3, q, algorithm=F.ALG_BLOCK)
     cells = _dev(p.mesh.cells, torch.int32)
     verts = _dev(p.mesh.vertices, torch.float64)
-    coeffs = _dev(p.coeffs, torch.float64)
+    coeffs = _dev(p.coeffs, torch.float64) if p.coeffs is not None else None
     n = p.n_local
-    for count in (1, 3, 4, 5, 63, 64, 65, 129, p.n_elem):
+    for count in (1, 2, 3, 4, 5, 63, 64, 65, 129, p.n_elem):
         out = torch.full((count + 1, n, n), 7.0, dtype=torch.float32, device="cuda")
-        F.tabulate(form, cells[:count].contiguous(), verts, coeffs=coeffs[:count].contiguous(), out=out[:count],
+        F.tabulate(fm, cells[:count].contiguous(), verts,
+                   coeffs=coeffs[:count].contiguous() if coeffs is not None else None, out=out[:count],
                    precision="fp32")
         got = out.double().cpu().numpy()
         assert OE.frobenius_rel_error(got[:count], ref[:count]).max() <= FP32_TOL
