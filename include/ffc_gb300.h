@@ -331,6 +331,17 @@ int ffc_tabulate_static(const ffc_form* f, int64_t n_elem, const int32_t* cells,
                         int64_t n_vert, const double* coeffs, void* A_K, int precision, void* stream,
                         uint32_t* host_flags);
 
+/*
+ * ffc_diag_bounded_wait -- a check of the failure detection. Every device-side wait of the
+ * library (the mbarrier waits between the warp roles of the tensor-core kernels) is
+ * bounded: after its limit it gives up, sets FFC_FLAG_TIMEOUT and lets the kernel return,
+ * so a stalled partner never hangs the GPU. This launches one CTA that waits, with that
+ * same bounded wait and a limit of `polls` tries (at most 2^20), on an mbarrier that
+ * nothing arrives at. Afterwards ffc_status_poll reports FFC_FLAG_TIMEOUT and the device
+ * stays usable. FFC_EINVAL for polls > 2^20.
+ */
+int ffc_diag_bounded_wait(uint32_t polls, void* stream);
+
 /* Human-readable name of a status code (static string). */
 const char* ffc_status_string(int status);
 

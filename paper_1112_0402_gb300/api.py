@@ -285,6 +285,12 @@ def tabulate_adjoint(form: Form, cells, vertices, dA_K, dvertices=None, stream=N
     return dvertices
 
 
+def diag_bounded_wait(polls: int = 4096, stream=None) -> None:
+    """Launches the failure-detection probe (ffc_diag_bounded_wait): a bounded device
+    wait that nothing ends; status_poll() then reports FLAG_TIMEOUT."""
+    _check(lib().ffc_diag_bounded_wait(polls, _stream(stream)), "ffc_diag_bounded_wait")
+
+
 def status_poll(stream=None) -> int:
     flags = ctypes.c_uint32()
     _check(lib().ffc_status_poll(_stream(stream), ctypes.byref(flags)), "ffc_status_poll")

@@ -206,6 +206,16 @@ int ffc_tabulate_adjoint(const ffc_form* f, int64_t n_elem, const int32_t* cells
   return launch_adjoint(a, dA_K, dvertices);
 }
 
+int ffc_diag_bounded_wait(uint32_t polls, void* stream) {
+  if (polls > (1u << 20)) {
+    set_error("ffc_diag_bounded_wait: at most 2^20 polls");
+    return FFC_EINVAL;
+  }
+  uint32_t* st = status_word();
+  if (!st) { set_error("status word allocation failed"); return FFC_ECUDA; }
+  return launch_bounded_wait_probe(polls, st, stream);
+}
+
 int ffc_status_poll(void* stream, uint32_t* flags) {
   if (!flags) return FFC_EINVAL;
   uint32_t* st = status_word();

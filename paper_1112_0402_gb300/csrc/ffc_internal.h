@@ -99,6 +99,7 @@ int launch_simt_source(const LaunchArgs& a, int precision, bool assemble);
 int launch_tc(const LaunchArgs& a, int precision, bool assemble);
 int launch_simt_block(const LaunchArgs& a, int precision, bool assemble);
 int launch_adjoint(const LaunchArgs& a, const double* dA, double* dvert);
+int launch_bounded_wait_probe(uint32_t polls, unsigned* status, void* stream);
 int launch_scatter_add(const void* a, int precision, const int32_t* slot, double* csr_val, long long nnz,
                        long long total, unsigned* status, void* stream);
 

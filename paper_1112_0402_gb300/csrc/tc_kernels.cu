@@ -240,8 +240,9 @@ struct TcWsCfg {
 };
 
 // Bounded wait that also gives up when another role has aborted.
-__device__ __forceinline__ bool mbar_wait_or_abort(uint32_t bar, uint32_t phase, volatile int* abort_flag) {
-  for (uint32_t it = 0; it < WAIT_LIMIT; ++it) {
+__device__ __forceinline__ bool mbar_wait_or_abort(uint32_t bar, uint32_t phase, volatile int* abort_flag,
+                                                   uint32_t limit = WAIT_LIMIT) {
+  for (uint32_t it = 0; it < limit; ++it) {
     if (mbar_try_wait(bar, phase)) return true;
     if ((it & 1023u) == 1023u && *abort_flag) return false;
   }
@@ -741,6 +742,26 @@ int by_prec(const LaunchArgs& a, int precision, bool assemble) {
 }
 
 }  // namespace tc
+
+// Failure-detection probe: one CTA waits, with the pipeline's bounded wait and a limit of
+// `polls` tries, on an mbarrier that nothing arrives at; the wait gives up and the CTA sets
+// FFC_FLAG_TIMEOUT and returns, as a pipeline role does when its partner stops.
+__global__ void bounded_wait_probe_kernel(unsigned* status, uint32_t polls) {
+  __shared__ __align__(8) unsigned long long bar;
+  __shared__ int abort_flag;
+  if (threadIdx.x == 0) {
+    tc::mbar_init(tc::smem_u32(&bar), 1);
+    abort_flag = 0;
+  }
+  __syncthreads();
+  const bool ok = tc::mbar_wait_or_abort(tc::smem_u32(&bar), 0, &abort_flag, polls);
+  if (!ok && threadIdx.x == 0) atomicOr(status, FFC_FLAG_TIMEOUT);
+}
+
+int launch_bounded_wait_probe(uint32_t polls, unsigned* status, void* stream) {
+  bounded_wait_probe_kernel<<<1, 32, 0, static_cast<cudaStream_t>(stream)>>>(status, polls);
+  return cudaPeekAtLastError() == cudaSuccess ? FFC_OK : FFC_ECUDA;
+}
 
 int launch_tc(const LaunchArgs& a, int precision, bool assemble) {
   const ffc_form* f = a.f;

@@ -346,3 +346,20 @@ def test_block_tabulate_ragged_counts(F, form, q):
         assert OE.frobenius_rel_error(got[:count], ref[:count]).max() <= FP32_TOL
         assert np.all(got[count] == 7.0)  # the guard cell after the output is untouched
     assert F.status_poll() == 0
+
+
+def test_bounded_wait_gives_up_and_reports_timeout(F):
+    """Failure detection without a fault: a device wait that nothing ends (the probe's
+    mbarrier never completes) gives up after its limit, the status word reports
+    FLAG_TIMEOUT, and the context stays usable for the next launch."""
+    import torch
+
+    assert F.status_poll() == 0
+    for polls in (0, 1, 4096):
+        F.diag_bounded_wait(polls)
+        assert F.status_poll() & F.FLAG_TIMEOUT
+    p = _case(3, 2, W.POISSON, 2)
+    form = F.Form(W.POISSON, 3, 2)
+    A = F.tabulate(form, _dev(p.mesh.cells, torch.int32), _dev(p.mesh.vertices, torch.float64))
+    assert F.status_poll() == 0
+    assert OE.frobenius_rel_error(A.cpu().numpy(), _oracle(p)).max() <= FP64_TOL

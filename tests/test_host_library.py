@@ -241,3 +241,8 @@ def test_row_plan_and_row_assembly_arguments_are_validated_on_the_host():
     assert L.ffc_assemble_rows(f.handle, None, fake, fake, 5, fake, 1, None) == -1  # no plan
     assert L.ffc_assemble_rows(None, fake, fake, fake, 5, fake, 1, None) == -1      # no form
     assert L.ffc_assemble_rows(f.handle, fake, fake, fake, 5, fake, 2, None) == -1  # tensor-core precision
+
+
+def test_bounded_wait_probe_limit_is_validated_on_the_host():
+    L = _lib()
+    assert L.ffc_diag_bounded_wait(2**20 + 1, None) == -1
