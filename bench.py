@@ -7,8 +7,10 @@ forms with scalar Lagrange P1..P4 -- eight (form, degree) problems.
 
 One step = for each of the eight problems: zero the CSR values and run the fused
 assembly (geometry G_K -> contraction A0:G_K -> atomic scatter into CSR through the
-precomputed slots), i.e. Algorithm 2 with the tensor representation. The zeroing runs on
-a second stream ahead of the assemblies; the step's time covers both. The headline
+precomputed slots), i.e. Algorithm 2 with the tensor representation. The mass and
+Poisson matrices of one degree share their dof map and slots; through P3 they are
+assembled by one ffc_assemble_pair launch, at P4 by one launch each (--pair-degrees). The
+zeroing runs on a second stream ahead of the assemblies; the step's time covers both. The headline
 `value` is element tensors computed and inserted per second over the whole step
 (8 x 663,552 per step); `nnz_per_s` is the assembled CSR entries per second.
 
@@ -59,6 +61,9 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-detail", action="store_true")
+    ap.add_argument("--pair-degrees", default="1,2,3",
+                    help="degrees whose mass and Poisson matrices share one ffc_assemble_pair launch "
+                         "(others: one launch per matrix); empty for none")
     return ap.parse_args()
 
 
@@ -155,9 +160,30 @@ def build_workload(F, n, device):
     return ctx
 
 
+def launch_list(ctx, pair_degrees):
+    """The step's launches: (label, problem indices). For a degree in `pair_degrees` the
+    mass and Poisson problems (same dof map, same slots) share one ffc_assemble_pair launch.
+    Measured: pairs are faster through P3; at P4 the two 4.3 GB matrices' atomics compete
+    for L2 and two launches are a little faster (7.09 vs 7.17 ms)."""
+    probs = ctx["problems"]
+    out = []
+    k = 0
+    while k < len(probs):
+        a = probs[k]
+        if a["q"] in pair_degrees and k + 1 < len(probs):
+            b = probs[k + 1]
+            assert b["q"] == a["q"] and (a["form"], b["form"]) == (0, 1)
+            out.append((f"mass+poisson_p{a['q']}", [k, k + 1]))
+            k += 2
+        else:
+            out.append((f"{FORM_NAME[a['form']]}_p{a['q']}", [k]))
+            k += 1
+    return out
+
+
 def assemble_step(F, ctx, precision, events=None):
     """Zero every CSR matrix and assemble it. The zeroing (bandwidth bound) runs on a side
-    stream, ahead of the assemblies (atomic-throughput bound) that wait for their matrix."""
+    stream, ahead of the assemblies (atomic-throughput bound) that wait for their matrices."""
     import torch
 
     main = torch.cuda.current_stream()
@@ -170,21 +196,31 @@ def assemble_step(F, ctx, precision, events=None):
             ev = torch.cuda.Event()
             ev.record(side)
             zeroed.append(ev)
-    for k, pr in enumerate(ctx["problems"]):
-        main.wait_event(zeroed[k])
+    for j, (_, ks) in enumerate(ctx["launches"]):
+        for k in ks:
+            main.wait_event(zeroed[k])
         if events is not None:
-            events[k][0].record(main)
-        F.assemble(pr["F"], ctx["cells"], ctx["verts"], pr["slot"], pr["val"], precision=precision)
+            events[j][0].record(main)
+        launch_assembly(F, ctx, ks, ctx["cells"], ctx["verts"], precision)
         if events is not None:
-            events[k][1].record(main)
+            events[j][1].record(main)
     main.wait_stream(side)
 
 
-def alg_bytes_assemble(ctx, pr):
-    """Algorithmic bytes of one fused assembly: cells + vertices + dofmap + CSR values
-    read and written once (slot map not counted)."""
+def launch_assembly(F, ctx, ks, cells, verts, precision):
+    prs = [ctx["problems"][k] for k in ks]
+    if len(prs) == 2:
+        F.assemble_pair(prs[0]["F"], prs[1]["F"], cells, verts, prs[0]["slot"], prs[0]["val"], prs[1]["val"],
+                        precision=precision)
+    else:
+        F.assemble(prs[0]["F"], cells, verts, prs[0]["slot"], prs[0]["val"], precision=precision)
+
+
+def alg_bytes_assemble(ctx, prs):
+    """Algorithmic bytes of one fused assembly launch: cells + vertices + dofmap once, and
+    the CSR values of each of its matrices read and written once (slot map not counted)."""
     m = ctx["mesh"]
-    return m.n_elem * 16 + m.n_vert * 24 + m.n_elem * 4 * pr["n_local"] + 16 * pr["nnz"]
+    return m.n_elem * 16 + m.n_vert * 24 + m.n_elem * 4 * prs[0]["n_local"] + sum(16 * pr["nnz"] for pr in prs)
 
 
 def alg_bytes_tabulate(ctx, n_local, out_bytes):
@@ -197,7 +233,7 @@ def alg_bytes_tabulate(ctx, n_local, out_bytes):
 # count (x8; slots, CSR values and cells all grow with it). Only valid for the FP32 SIMT
 # assembly kernels as captured; other kernels report null.
 FP64_NOMINAL_TFLOPS = 1.25  # GB300 FP64 (CUDA cores), nominal
-CAPTURED_TRAFFIC_GB = {("mass", 4, "fp32"): 1.467 * 8, ("poisson", 4, "fp32"): 1.524 * 8}
+CAPTURED_TRAFFIC_GB = {("mass_p4", "fp32"): 1.467 * 8, ("poisson_p4", "fp32"): 1.524 * 8}
 
 
 def measured_peaks():
@@ -313,7 +349,9 @@ def main():
     import paper_1112_0402_gb300 as F
 
     ctx = build_workload(F, args.n, device)
+    ctx["launches"] = launch_list(ctx, {int(q) for q in args.pair_degrees.split(",") if q.strip()})
     P = len(ctx["problems"])
+    NL = len(ctx["launches"])
     n_elem = ctx["mesh"].n_elem
     total_nnz = sum(pr["nnz"] for pr in ctx["problems"])
 
@@ -325,7 +363,7 @@ def main():
     for _ in range(args.warmup):
         assemble_step(F, ctx, args.precision)
     assert F.status_poll() == 0
-    events = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(P * args.steps)]
+    events = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(NL * args.steps)]
     bus = None
     try:
         bus = torch.cuda.get_device_properties(device).pci_bus_id  # noqa
@@ -337,22 +375,25 @@ def main():
     start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     start.record()
     for s in range(args.steps):
-        assemble_step(F, ctx, args.precision, events[s * P:(s + 1) * P])
+        assemble_step(F, ctx, args.precision, events[s * NL:(s + 1) * NL])
     stop.record()
     barrier()
     clk = clocks.stop()
     elapsed = max_over_ranks(start.elapsed_time(stop) / 1e3, world, device)
     assert F.status_poll() == 0
-    per_launch = np.zeros(P)
+    per_launch = np.zeros(NL)
     for s in range(args.steps):
-        for k in range(P):
-            ev = events[s * P + k]
+        for k in range(NL):
+            ev = events[s * NL + k]
             per_launch[k] += ev[0].elapsed_time(ev[1]) / 1e3
     per_launch /= args.steps
     dom = int(np.argmax(per_launch))
-    dpr = ctx["problems"][dom]
+    dlabel, dks = ctx["launches"][dom]
+    dprs = [ctx["problems"][k] for k in dks]
+    dpr = dprs[0]
     hbm_peak, peak_kind = measured_peaks()
-    achieved = alg_bytes_assemble(ctx, dpr) / per_launch[dom] / 1e9
+    achieved = alg_bytes_assemble(ctx, dprs) / per_launch[dom] / 1e9
+    dat = n_elem * sum(pr["n_local"] ** 2 for pr in dprs) / per_launch[dom]  # FP64 atomics per second
     value = world * P * n_elem / elapsed * args.steps
 
     # ---- end to end through the C ABI: pinned host inputs in, CSR values out
@@ -373,16 +414,18 @@ def main():
             cur = torch.cuda.current_stream()
             d_cells.copy_(h_cells, non_blocking=True)
             d_verts.copy_(h_verts, non_blocking=True)
-            for k, (pr, ho) in enumerate(zip(ctx["problems"], h_out)):
-                if read_done[k] is not None:
-                    cur.wait_event(read_done[k])
-                pr["val"].zero_()
-                F.assemble(pr["F"], d_cells, d_verts, pr["slot"], pr["val"], precision=args.precision)
+            for _, ks in ctx["launches"]:
+                for k in ks:
+                    if read_done[k] is not None:
+                        cur.wait_event(read_done[k])
+                    ctx["problems"][k]["val"].zero_()
+                launch_assembly(F, ctx, ks, d_cells, d_verts, args.precision)
                 copy_stream.wait_stream(cur)
                 with torch.cuda.stream(copy_stream):
-                    ho.copy_(pr["val"], non_blocking=True)
-                    read_done[k] = torch.cuda.Event()
-                    read_done[k].record(copy_stream)
+                    for k in ks:
+                        h_out[k].copy_(ctx["problems"][k]["val"], non_blocking=True)
+                        read_done[k] = torch.cuda.Event()
+                        read_done[k].record(copy_stream)
 
         for _ in range(max(1, args.warmup)):
             e2e_step()
@@ -428,19 +471,17 @@ def main():
                        "parallelism": f"replicas x{world}"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                          "frac": achieved / hbm_peak, "peak_kind": peak_kind,
-                         "traffic": CAPTURED_TRAFFIC_GB.get((FORM_NAME[dpr["form"]], dpr["q"], args.precision)),
+                         "traffic": CAPTURED_TRAFFIC_GB.get((dlabel, args.precision)),
                          "traffic_unit": "GB per launch (ncu, scaled from 82,944 cells)",
-                         "algorithmic_gb": alg_bytes_assemble(ctx, dpr) / 1e9,
-                         "kernel": f"assemble {FORM_NAME[dpr['form']]} P{dpr['q']} ({args.precision})",
+                         "algorithmic_gb": alg_bytes_assemble(ctx, dprs) / 1e9,
+                         "kernel": f"assemble {dlabel} ({args.precision})",
                          "launch_ms": per_launch[dom] * 1e3,
-                         "fp64_atomics_per_s": n_elem * dpr["n_local"] ** 2 / per_launch[dom],
+                         "fp64_atomics_per_s": dat,
                          "fp64_atomic_ceiling_per_s": (detail or {}).get("fp64_atomic_ceiling_per_s"),
-                         "fp64_atomics_frac": (n_elem * dpr["n_local"] ** 2 / per_launch[dom] /
-                                               detail["fp64_atomic_ceiling_per_s"])
+                         "fp64_atomics_frac": dat / detail["fp64_atomic_ceiling_per_s"]
                          if detail and detail.get("fp64_atomic_ceiling_per_s") else None},
-            "per_launch_ms": {f"{FORM_NAME[p['form']]}_p{p['q']}": round(per_launch[k] * 1e3, 4)
-                              for k, p in enumerate(ctx["problems"])},
-            "clocks": clk, "gpu_launches": P * args.steps, "e2e": e2e, "cpu_baseline": cpu, "detail": detail,
+            "per_launch_ms": {lab: round(per_launch[k] * 1e3, 4) for k, (lab, _) in enumerate(ctx["launches"])},
+            "clocks": clk, "gpu_launches": NL * args.steps, "e2e": e2e, "cpu_baseline": cpu, "detail": detail,
         }
         print(json.dumps(line), flush=True)
     if world > 1:

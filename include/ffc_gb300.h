@@ -186,6 +186,22 @@ int ffc_assemble(const ffc_form* f, int64_t n_elem, const int32_t* cells, const 
                  int precision, void* stream);
 
 /*
+ * ffc_assemble_pair -- ffc_assemble for two bilinear forms on the same space (same cell,
+ * degree and dof map, hence the same CSR pattern and slots), e.g. the mass and stiffness
+ * matrices of a time step or an eigenproblem:
+ *   csr_val_a[slot[e][i1][i2]] += A_a^K[i1][i2],  csr_val_b[slot[e][i1][i2]] += A_b^K[i1][i2]
+ * The pair (mass, Poisson), in either order, with FFC_FP32 runs as one launch: the cell's
+ * geometry is computed once and each slot is loaded once for both matrices; each matrix
+ * receives the contributions ffc_assemble computes for it. Any other pair of forms without
+ * coefficients runs as two ffc_assemble calls. csr_val_a and csr_val_b are distinct
+ * device double [nnz] arrays, accumulated into. FFC_EINVAL for forms on different
+ * spaces or one array passed twice; FFC_EUNSUPPORTED for forms with coefficients.
+ */
+int ffc_assemble_pair(const ffc_form* fa, const ffc_form* fb, int64_t n_elem, const int32_t* cells,
+                      const double* vertices, int64_t n_vert, const int32_t* slot, double* csr_val_a,
+                      double* csr_val_b, int64_t nnz, int precision, void* stream);
+
+/*
  * ffc_scatter_add -- the insertion step of Algorithm 2 (Section 2.2) on its own: adds
  * precomputed element tensors into the CSR values,
  *   csr_val[slot[e][i]] += A_K[e][i]     for e < n_elem, i < n_entries (FP64 atomic adds).

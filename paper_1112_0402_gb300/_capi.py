@@ -32,6 +32,8 @@ SIGNATURES = {
                                        ctypes.c_int64, c_vp]),
     "ffc_assemble": (ctypes.c_int, [c_vp, ctypes.c_int64, c_vp, c_vp, ctypes.c_int64, c_vp, c_vp, c_vp,
                                     ctypes.c_int64, ctypes.c_int, c_vp]),
+    "ffc_assemble_pair": (ctypes.c_int, [c_vp, c_vp, ctypes.c_int64, c_vp, c_vp, ctypes.c_int64, c_vp, c_vp, c_vp,
+                                         ctypes.c_int64, ctypes.c_int, c_vp]),
     "ffc_scatter_add": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int, c_vp, ctypes.c_int, c_vp, c_vp, ctypes.c_int64,
                                        c_vp]),
     "ffc_tabulate_adjoint": (ctypes.c_int, [c_vp, ctypes.c_int64, c_vp, c_vp, ctypes.c_int64, c_vp, c_vp, c_vp]),

@@ -250,6 +250,25 @@ def assemble_rows(form: Form, plan: RowPlan, cells, vertices, csr_val, precision
     return csr_val
 
 
+def assemble_pair(form_a: Form, form_b: Form, cells, vertices, slot, csr_val_a, csr_val_b, precision="fp32",
+                  stream=None):
+    """Two forms on one space into two matrices sharing the pattern (ffc_assemble_pair):
+    csr_val_a[slot] += A_a^K, csr_val_b[slot] += A_b^K. The (mass, Poisson) pair in FP32 is
+    one launch (geometry and slot loads shared)."""
+    import torch
+
+    p = _prec(precision)
+    n_elem = cells.shape[0]
+    c = _dev_ptr(cells, torch.int32, "cells", (n_elem, form_a.dim + 1))
+    v = _dev_ptr(vertices, torch.float64, "vertices")
+    s = _dev_ptr(slot, torch.int32, "slot", (n_elem,) + form_a.tensor_shape)
+    va = _dev_ptr(csr_val_a, torch.float64, "csr_val_a")
+    vb = _dev_ptr(csr_val_b, torch.float64, "csr_val_b", tuple(csr_val_a.shape))
+    _check(lib().ffc_assemble_pair(form_a.handle, form_b.handle, n_elem, c, v, vertices.shape[0], s, va, vb,
+                                   csr_val_a.numel(), p, _stream(stream)), "ffc_assemble_pair")
+    return csr_val_a, csr_val_b
+
+
 def scatter_add(A_K, slot, csr_val, stream=None):
     """The insertion step alone: csr_val[slot[e, ...]] += A_K[e, ...] (FP64 atomics).
     A_K float64 or float32 [n_elem, ...]; slot int32 of the same shape."""

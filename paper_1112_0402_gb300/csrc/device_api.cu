@@ -168,6 +168,45 @@ int ffc_assemble(const ffc_form* f, int64_t n_elem, const int32_t* cells, const 
   return dispatch(a, precision, true);
 }
 
+int ffc_assemble_pair(const ffc_form* fa, const ffc_form* fb, int64_t n_elem, const int32_t* cells,
+                      const double* vertices, int64_t n_vert, const int32_t* slot, double* csr_val_a,
+                      double* csr_val_b, int64_t nnz, int precision, void* stream) {
+  if (!fa || !fb || fa->rank != 2 || fb->rank != 2 || fa->d != fb->d || fa->q != fb->q || fa->n != fb->n ||
+      csr_val_a == csr_val_b) {
+    set_error("ffc_assemble_pair: two bilinear forms on one space, two distinct matrices");
+    return FFC_EINVAL;
+  }
+  if (fa->ncoeff > 0 || fb->ncoeff > 0) {
+    set_error("ffc_assemble_pair: forms with coefficients are assembled with ffc_assemble");
+    return FFC_EUNSUPPORTED;
+  }
+  int rc = common_checks(fa, n_elem, cells, vertices, n_vert, nullptr, precision);
+  if (rc != FFC_OK) { set_error("ffc_assemble_pair: invalid argument"); return rc; }
+  if (n_elem == 0) return FFC_OK;
+  if (!slot || !csr_val_a || !csr_val_b || nnz <= 0 || nnz > INT32_MAX) {
+    set_error("ffc_assemble_pair: slot/csr");
+    return FFC_EINVAL;
+  }
+  const bool mp = fa->kind == FFC_MASS && fb->kind == FFC_POISSON;
+  const bool pm = fa->kind == FFC_POISSON && fb->kind == FFC_MASS;
+  if ((mp || pm) && precision == FFC_FP32) {
+    DeviceTensors *ta = nullptr, *tb = nullptr;
+    if ((rc = ensure_device_tensors(const_cast<ffc_form*>(fa), &ta)) != FFC_OK ||
+        (rc = ensure_device_tensors(const_cast<ffc_form*>(fb), &tb)) != FFC_OK)
+      return rc;
+    uint32_t* st = status_word();
+    if (!st) { set_error("status word allocation failed"); return FFC_ECUDA; }
+    LaunchArgs a{fa, n_elem, cells, vertices, n_vert, nullptr, nullptr, slot, nullptr, nnz, ta, st, stream};
+    rc = mp ? launch_simt_pair(a, ta, tb, csr_val_a, csr_val_b) : launch_simt_pair(a, tb, ta, csr_val_b, csr_val_a);
+    if (rc == FFC_ECUDA) set_error(std::string("kernel launch: ") + cudaGetErrorString(cudaGetLastError()));
+    return rc;
+  }
+  // any other pair: the two assemblies one after the other
+  if ((rc = ffc_assemble(fa, n_elem, cells, vertices, n_vert, nullptr, slot, csr_val_a, nnz, precision, stream)))
+    return rc;
+  return ffc_assemble(fb, n_elem, cells, vertices, n_vert, nullptr, slot, csr_val_b, nnz, precision, stream);
+}
+
 int ffc_scatter_add(int64_t n_elem, int n_entries, const void* A_K, int precision, const int32_t* slot,
                     double* csr_val, int64_t nnz, void* stream) {
   if (n_elem < 0 || n_entries <= 0 || (precision != FFC_FP64 && precision != FFC_FP32) || nnz < 0 ||

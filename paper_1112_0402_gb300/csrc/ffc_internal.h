@@ -100,6 +100,9 @@ int launch_tc(const LaunchArgs& a, int precision, bool assemble);
 int launch_simt_block(const LaunchArgs& a, int precision, bool assemble);
 int launch_adjoint(const LaunchArgs& a, const double* dA, double* dvert);
 int launch_bounded_wait_probe(uint32_t polls, unsigned* status, void* stream);
+// the mass + Poisson pair in one launch (FP32 contraction); a.f is either form of the pair
+int launch_simt_pair(const LaunchArgs& a, const DeviceTensors* t_mass, const DeviceTensors* t_poisson,
+                     double* val_mass, double* val_poisson);
 int launch_scatter_add(const void* a, int precision, const int32_t* slot, double* csr_val, long long nnz,
                        long long total, unsigned* status, void* stream);
 

@@ -24,7 +24,14 @@ constexpr int nalpha(int form, int d, int q) {
 // Column layout of the CUDA-core kernels' reference tensor: the Poisson G_K is
 // symmetric, so it is kept once per pair a1 <= a2 (Section 3.5: symmetry means fewer
 // operations), d(d+1)/2 columns: diagonal pairs first, then (0,1) [, (0,2), (1,2)].
-constexpr int nalpha_k(int form, int d, int q) { return form == FFC_POISSON ? d * (d + 1) / 2 : nalpha(form, d, q); }
+// Internal form code of the fused mass + Poisson pair (one launch, two matrices): its
+// kernel columns are the mass column followed by the d(d+1)/2 symmetric Poisson columns.
+constexpr int FFC_PAIR_MASS_POISSON = 100;
+constexpr int nalpha_k(int form, int d, int q) {
+  return form == FFC_POISSON ? d * (d + 1) / 2
+       : form == FFC_PAIR_MASS_POISSON ? 1 + d * (d + 1) / 2
+       : nalpha(form, d, q);
+}
 template <int D>
 __host__ __device__ constexpr int sym_pair_index(int a, int b) {
   return a == b ? a : (D == 2 ? 2 : (a == 0 ? (b == 1 ? 3 : 4) : 5));

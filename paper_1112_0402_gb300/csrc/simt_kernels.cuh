@@ -30,6 +30,7 @@ struct SimtCfg {
   static constexpr int N = nlocal(FORM, D, Q);
   static constexpr int NN = N * N;
   static constexpr int NA = nalpha_k(FORM, D, Q);
+  static constexpr bool PAIR = FORM == FFC_PAIR_MASS_POISSON;  // two outputs per entry
   static constexpr int VEC = 16 / int(sizeof(T));
   static constexpr int NAP = (NA + VEC - 1) / VEC * VEC;
   static constexpr int RMAX_THREADS = BLOCK > 0 ? BLOCK : 512;
@@ -64,6 +65,8 @@ struct SimtParams {
   long long n_vert;
   const double* coeffs;
   const void* a0;       // REG_A0: [NN][NA]; otherwise [NA][NN] (rows by element-tensor position)
+  const void* a0b;      // mass + Poisson pair: the Poisson rows [NN][NA - 1] (a0: the mass rows [NN][1])
+  double* csr_val2;     // mass + Poisson pair: the Poisson matrix (csr_val: the mass matrix)
   void* out;            // A_K [n_elem][NN]
   const int32_t* slot;  // [n_elem][NN]
   double* csr_val;
@@ -100,19 +103,28 @@ __device__ __forceinline__ void entry_positions(int u, int& p1, int& p2) {
   }
 }
 
-// Loads the thread's rows of the reference tensor into registers (register path).
+// Loads the thread's rows of the reference tensor into registers (register path). The
+// mass + Poisson pair takes column 0 from the mass rows `a0` and the rest from the
+// Poisson rows `a0b`.
 template <class C, typename T>
-__device__ __forceinline__ void load_a0_rows(const void* a0, int t, T (&a0r)[C::REG_A0 ? C::R : 1][C::REG_A0 ? C::NA : 1]) {
+__device__ __forceinline__ void load_a0_rows(const void* a0, int t, T (&a0r)[C::REG_A0 ? C::R : 1][C::REG_A0 ? C::NA : 1],
+                                             const void* a0b = nullptr) {
   if constexpr (C::REG_A0) {
     const int ti = t % C::NTI;
     const T* A0 = static_cast<const T*>(a0);
+    const T* A0b = static_cast<const T*>(a0b);
 #pragma unroll
     for (int r = 0; r < C::R; ++r) {
       const int u = ti + r * C::NTI;
       int p1 = 0, p2 = 0;
       if (u < C::NE) entry_positions<C>(u, p1, p2);
 #pragma unroll
-      for (int a = 0; a < C::NA; ++a) a0r[r][a] = (u < C::NE) ? A0[size_t(p1) * C::NA + a] : T(0);
+      for (int a = 0; a < C::NA; ++a) {
+        if constexpr (C::PAIR)
+          a0r[r][a] = (u < C::NE) ? (a == 0 ? A0[p1] : A0b[size_t(p1) * (C::NA - 1) + a - 1]) : T(0);
+        else
+          a0r[r][a] = (u < C::NE) ? A0[size_t(p1) * C::NA + a] : T(0);
+      }
     }
   }
 }
@@ -142,7 +154,13 @@ __device__ __forceinline__ void simt_tile(const SimtParams& p, long long tile, u
       T* g = Gs + el * C::NAP;
       if (e < p.n_elem) {
         bool degenerate, bad_index;
-        if constexpr (sizeof(T) == 4 && FORM != FFC_MASS) {
+        if constexpr (C::PAIR) {
+          // mass G = |det J| (the value the mass kernel takes), then the Poisson G_K
+          float K[D][D], det;
+          cell_geometry_f32<D>(p.cells, p.vertices, p.n_vert, e, K, det, degenerate, bad_index);
+          g[0] = det;
+          geometry_tensor_f32<D, FFC_POISSON, Q, true>(K, det, nullptr, 0.0, 0.0, g + 1);
+        } else if constexpr (sizeof(T) == 4 && FORM != FFC_MASS) {
           // FP32 contraction: FP64 J, adj(J), det J; K and G_K in FP32
           float K[D][D], det;
           cell_geometry_f32<D>(p.cells, p.vertices, p.n_vert, e, K, det, degenerate, bad_index);
@@ -212,14 +230,28 @@ __device__ __forceinline__ void simt_tile(const SimtParams& p, long long tile, u
           }
         }
         const T* g = Gs + el * C::NAP;
-        T acc[C::R];
+        T acc[C::R], acc2[C::PAIR ? C::R : 1];
 #pragma unroll
         for (int r = 0; r < C::R; ++r) acc[r] = T(0);
+        if constexpr (C::PAIR) {  // mass: column 0; Poisson: columns 1.., in the Poisson kernel's order
 #pragma unroll
-        for (int a = 0; a < C::NA; ++a) {
-          const T gv = g[a];
+          for (int r = 0; r < C::R; ++r) {
+            acc[r] = fma(g[0], a0r[r][0], T(0));
+            acc2[r] = T(0);
+          }
 #pragma unroll
-          for (int r = 0; r < C::R; ++r) acc[r] = fma(gv, a0r[r][a], acc[r]);
+          for (int a = 1; a < C::NA; ++a) {
+            const T gv = g[a];
+#pragma unroll
+            for (int r = 0; r < C::R; ++r) acc2[r] = fma(gv, a0r[r][a], acc2[r]);
+          }
+        } else {
+#pragma unroll
+          for (int a = 0; a < C::NA; ++a) {
+            const T gv = g[a];
+#pragma unroll
+            for (int r = 0; r < C::R; ++r) acc[r] = fma(gv, a0r[r][a], acc[r]);
+          }
         }
 #pragma unroll
         for (int r = 0; r < C::R; ++r) {
@@ -229,8 +261,12 @@ __device__ __forceinline__ void simt_tile(const SimtParams& p, long long tile, u
             for (int m = 0; m < NS_; ++m) {
               if (m == 1 && pos2[r] == pos1[r]) continue;
               const int s = slot_cur[r][m];
-              if (s >= 0 && s < p.nnz) atomicAdd(p.csr_val + s, double(acc[r]));
-              else atomicOr(p.status, FFC_FLAG_BOUNDS);
+              if (s >= 0 && s < p.nnz) {
+                atomicAdd(p.csr_val + s, double(acc[r]));
+                if constexpr (C::PAIR) atomicAdd(p.csr_val2 + s, double(acc2[r]));
+              } else {
+                atomicOr(p.status, FFC_FLAG_BOUNDS);
+              }
             }
           } else {
             put(static_cast<OutT*>(p.out) + e * C::NN + pos1[r], acc[r]);
@@ -239,6 +275,7 @@ __device__ __forceinline__ void simt_tile(const SimtParams& p, long long tile, u
         }
       }
     } else {
+      static_assert(!C::PAIR, "the mass + Poisson pair keeps its reference tensor rows in registers");
       const T* A0T = static_cast<const T*>(p.a0);
 #pragma unroll 1
       for (int r = 0; r < C::R; ++r) {
@@ -300,7 +337,7 @@ __global__ void __launch_bounds__(SimtCfg<D, FORM, Q, T>::NT, SimtCfg<D, FORM, Q
   using C = SimtCfg<D, FORM, Q, T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T a0r[C::REG_A0 ? C::R : 1][C::REG_A0 ? C::NA : 1];
-  load_a0_rows<C, T>(p.a0, threadIdx.x, a0r);
+  load_a0_rows<C, T>(p.a0, threadIdx.x, a0r, p.a0b);
   const long long n_tiles = (p.n_elem + C::E - 1) / C::E;
   for (long long tile = blockIdx.x; tile < n_tiles; tile += gridDim.x)
     simt_tile<C, D, FORM, Q, T, ASSEMBLE>(p, tile, smem_raw, a0r);

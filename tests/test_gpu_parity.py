@@ -363,3 +363,59 @@ def test_bounded_wait_gives_up_and_reports_timeout(F):
     A = F.tabulate(form, _dev(p.mesh.cells, torch.int32), _dev(p.mesh.vertices, torch.float64))
     assert F.status_poll() == 0
     assert OE.frobenius_rel_error(A.cpu().numpy(), _oracle(p)).max() <= FP64_TOL
+
+
+@pytest.mark.parametrize("d,n,q", [(3, 3, 1), (3, 3, 2), (3, 3, 3), (3, 2, 4), (2, 6, 1), (2, 4, 4)])
+def test_assemble_pair_matches_the_single_assemblies(F, d, n, q):
+    """ffc_assemble_pair(mass, Poisson) in FP32 is one launch; each matrix must equal its own
+    ffc_assemble (same contributions: FP64 rounding apart) and the oracle's Algorithm 2.
+    The reversed order and FP64 (two launches) give the same matrices."""
+    import torch
+
+    p = _case(d, n, W.POISSON, q)
+    row_ptr, col, slot_h = F.csr_pattern(p.dofmap, p.n_dof)
+    slot = _dev(slot_h, torch.int32)
+    cells, verts = _dev(p.mesh.cells, torch.int32), _dev(p.mesh.vertices, torch.float64)
+    fm, fp = F.Form(W.MASS, d, q), F.Form(W.POISSON, d, q)
+    gv = M.gather_cell_vertices(p.mesh)
+    for prec, tol in (("fp32", FP32_TOL), ("fp64", FP64_TOL)):
+        single = []
+        for f in (fm, fp):
+            v = torch.zeros(col.size, dtype=torch.float64, device="cuda")
+            F.assemble(f, cells, verts, slot, v, precision=prec)
+            single.append(v)
+        vm = torch.zeros(col.size, dtype=torch.float64, device="cuda")
+        vp = torch.zeros_like(vm)
+        F.assemble_pair(fm, fp, cells, verts, slot, vm, vp, precision=prec)
+        wp = torch.zeros_like(vm)
+        wm = torch.zeros_like(vm)
+        F.assemble_pair(fp, fm, cells, verts, slot, wp, wm, precision=prec)
+        assert F.status_poll() == 0
+        for got, alt, ref, form in ((vm, wm, single[0], W.MASS), (vp, wp, single[1], W.POISSON)):
+            scale = ref.abs().max().item()
+            assert (got - ref).abs().max().item() <= 1e-12 * scale
+            assert (alt - ref).abs().max().item() <= 1e-12 * scale
+            _, _, oracle_val = OA.assemble_csr(OE.element_tensors(form, gv, q), p.dofmap, p.n_dof)
+            g = got.cpu().numpy()
+            assert np.linalg.norm(g - oracle_val) <= tol * np.linalg.norm(oracle_val)
+
+
+def test_assemble_pair_arguments(F):
+    import torch
+
+    p = _case(3, 2, W.POISSON, 2)
+    _, col, slot_h = F.csr_pattern(p.dofmap, p.n_dof)
+    slot = _dev(slot_h, torch.int32)
+    cells, verts = _dev(p.mesh.cells, torch.int32), _dev(p.mesh.vertices, torch.float64)
+    a = torch.zeros(col.size, dtype=torch.float64, device="cuda")
+    b = torch.zeros_like(a)
+    with pytest.raises(F.FFCError) as e:  # one matrix passed twice
+        F.assemble_pair(F.Form(W.MASS, 3, 2), F.Form(W.POISSON, 3, 2), cells, verts, slot, a, a)
+    assert e.value.code == -1
+    with pytest.raises(F.FFCError) as e:  # forms on different spaces
+        F.assemble_pair(F.Form(W.MASS, 3, 2), F.Form(W.POISSON, 3, 1), cells, verts, slot, a, b)
+    assert e.value.code == -1
+    # another pair without coefficients: two assemblies
+    F.assemble_pair(F.Form(W.POISSON, 3, 2), F.Form(W.POISSON, 3, 2), cells, verts, slot, a, b, precision="fp32")
+    assert torch.equal(a, b)
+    assert F.status_poll() == 0

@@ -246,3 +246,17 @@ def test_row_plan_and_row_assembly_arguments_are_validated_on_the_host():
 def test_bounded_wait_probe_limit_is_validated_on_the_host():
     L = _lib()
     assert L.ffc_diag_bounded_wait(2**20 + 1, None) == -1
+
+
+def test_assemble_pair_arguments_are_validated_on_the_host():
+    import paper_1112_0402_gb300 as F
+
+    L = _lib()
+    m2, p1 = F.Form(F.MASS, F.TETRAHEDRON, 2), F.Form(F.POISSON, F.TETRAHEDRON, 1)
+    ns = F.Form(F.NS_CONVECTION, F.TETRAHEDRON, 2)
+    buf = np.zeros(4)
+    x, y = buf[:2].ctypes.data, buf[2:].ctypes.data
+    assert L.ffc_assemble_pair(None, m2.handle, 0, None, None, 0, None, x, y, 0, 1, None) == -1
+    assert L.ffc_assemble_pair(m2.handle, p1.handle, 0, None, None, 0, None, x, y, 0, 1, None) == -1  # spaces
+    assert L.ffc_assemble_pair(m2.handle, m2.handle, 0, None, None, 0, None, x, x, 0, 1, None) == -1  # one array
+    assert L.ffc_assemble_pair(ns.handle, ns.handle, 0, None, None, 0, None, x, y, 0, 1, None) == -5  # coefficients
