@@ -282,10 +282,11 @@ def cpu_oracle_step(n, frac, pool):
     return S, dt
 
 
-def oracle_pool():
+def oracle_pool(cores=None):
     import multiprocessing as mp
 
-    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    if cores is None:
+        cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
     pool = mp.get_context("spawn").Pool(cores)
     warm = (0, 1, np.zeros((1, 4, 3)) + np.eye(4, 3)[None], np.zeros((1, 4), np.int32), 1)
     pool.map(_oracle_chunk, [warm] * cores)
@@ -339,9 +340,10 @@ def main():
 
     # the CPU oracle pool starts before the first GPU call
     cpu = None
-    pool = None
+    pool = pool1 = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         pool, cores = oracle_pool()
+        pool1, _ = oracle_pool(1)  # the same oracle on one host thread
 
     from paper_1112_0402_gb300 import build as B
 
@@ -452,9 +454,14 @@ def main():
         S, t_cpu = cpu_oracle_step(args.n, 2 * REF_FRACTION, pool)
         pool.close()
         pool.join()
+        S1, t1 = cpu_oracle_step(args.n, REF_FRACTION / 8, pool1)
+        pool1.close()
+        pool1.join()
         cpu = {"value": P * S / t_cpu, "unit": "elem/s", "cores": cores, "kind": "oracle",
                "sample": f"{S} cells (1/8) of each of the 8 problems, spread evenly over the mesh, "
-                         f"{t_cpu:.1f} s; same problem mix as the GPU step"}
+                         f"{t_cpu:.1f} s; same problem mix as the GPU step",
+               "single_thread": {"value": P * S1 / t1, "unit": "elem/s", "cores": 1,
+                                 "sample": f"{S1} cells (1/128) of each of the 8 problems, {t1:.1f} s"}}
 
     if rank == 0:
         line = {
