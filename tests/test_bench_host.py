@@ -1,0 +1,50 @@
+"""Host logic of bench.py that needs no GPU: the launch list of the headline step (which
+problems share an ffc_assemble_pair launch) and the algorithmic byte count of a launch."""
+import os
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+
+
+def _ctx():
+    probs = [{"form": f, "q": q, "n_local": (q + 1) * (q + 2) * (q + 3) // 6, "nnz": 1000 * q}
+             for q in (1, 2, 3, 4) for f in (0, 1)]
+
+    class Mesh:
+        n_elem, n_vert = 10, 7
+
+    return {"problems": probs, "mesh": Mesh()}
+
+
+def test_launch_list_pairs_the_requested_degrees():
+    ctx = _ctx()
+    ll = bench.launch_list(ctx, {1, 2, 3})
+    assert [lab for lab, _ in ll] == ["mass+poisson_p1", "mass+poisson_p2", "mass+poisson_p3", "mass_p4",
+                                      "poisson_p4"]
+    assert [ks for _, ks in ll] == [[0, 1], [2, 3], [4, 5], [6], [7]]
+    # every problem exactly once, in order
+    assert sum((ks for _, ks in ll), []) == list(range(8))
+    assert [ks for _, ks in bench.launch_list(ctx, set())] == [[k] for k in range(8)]
+    assert len(bench.launch_list(ctx, {1, 2, 3, 4})) == 4
+
+
+def test_launch_list_rejects_a_problem_order_it_cannot_pair():
+    ctx = _ctx()
+    ctx["problems"][0], ctx["problems"][1] = ctx["problems"][1], ctx["problems"][0]
+    with pytest.raises(AssertionError):
+        bench.launch_list(ctx, {1})
+
+
+def test_algorithmic_bytes_count_the_shared_inputs_once():
+    ctx = _ctx()
+    one = bench.alg_bytes_assemble(ctx, [ctx["problems"][6]])
+    two = bench.alg_bytes_assemble(ctx, ctx["problems"][6:8])
+    # cells, vertices and the dof map once, CSR values read and written once per matrix
+    assert one == 10 * 16 + 7 * 24 + 10 * 4 * 35 + 16 * 4000
+    assert two - one == 16 * 4000
