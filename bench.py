@@ -162,9 +162,12 @@ def build_workload(F, n, device):
 
 def launch_list(ctx, pair_degrees):
     """The step's launches: (label, problem indices). For a degree in `pair_degrees` the
-    mass and Poisson problems (same dof map, same slots) share one ffc_assemble_pair launch.
-    Measured: pairs are faster through P3; at P4 the two 4.3 GB matrices' atomics compete
-    for L2 and two launches are a little faster (7.09 vs 7.17 ms)."""
+    mass and Poisson problems (same dof map, same slots) share one ffc_assemble_pair
+    launch. Measured: pairs are faster through P3; at P4 the two 4.3 GB matrices' atomics
+    compete for L2 and two launches are a little faster (7.09 vs 7.17 ms). The launches
+    alternate between the smallest and the largest remaining, so the zeroing that runs on
+    the side stream (in launch order) overlaps long assemblies: 10.91-11.09 ms per step on
+    two boxes, against 11.15-11.31 ms in increasing and 10.93-11.24 ms in decreasing order."""
     probs = ctx["problems"]
     out = []
     k = 0
@@ -178,7 +181,13 @@ def launch_list(ctx, pair_degrees):
         else:
             out.append((f"{FORM_NAME[a['form']]}_p{a['q']}", [k]))
             k += 1
-    return out
+    rest = sorted(out, key=lambda lk: sum(probs[k]["nnz"] for k in lk[1]))
+    order = []
+    while rest:
+        order.append(rest.pop(0))
+        if rest:
+            order.append(rest.pop())
+    return order
 
 
 def assemble_step(F, ctx, precision, events=None):
@@ -189,13 +198,14 @@ def assemble_step(F, ctx, precision, events=None):
     main = torch.cuda.current_stream()
     side = ctx.setdefault("side_stream", torch.cuda.Stream())
     side.wait_stream(main)  # the previous step's assemblies are done with these values
-    zeroed = []
-    with torch.cuda.stream(side):
-        for pr in ctx["problems"]:
-            pr["val"].zero_()
-            ev = torch.cuda.Event()
-            ev.record(side)
-            zeroed.append(ev)
+    zeroed = {}
+    with torch.cuda.stream(side):  # in launch order, so the first launch waits for its own matrices only
+        for _, ks in ctx["launches"]:
+            for k in ks:
+                ctx["problems"][k]["val"].zero_()
+                ev = torch.cuda.Event()
+                ev.record(side)
+                zeroed[k] = ev
     for j, (_, ks) in enumerate(ctx["launches"]):
         for k in ks:
             main.wait_event(zeroed[k])
@@ -463,6 +473,7 @@ def main():
                "single_thread": {"value": P * S1 / t1, "unit": "elem/s", "cores": 1,
                                  "sample": f"{S1} cells (1/128) of each of the 8 problems, {t1:.1f} s"}}
 
+    iso_ms = (detail or {}).get(dlabel, {}).get("assemble_fp32_ms") if args.precision == "fp32" else None
     if rank == 0:
         line = {
             "metric": METRIC,
@@ -486,7 +497,12 @@ def main():
                          "fp64_atomics_per_s": dat,
                          "fp64_atomic_ceiling_per_s": (detail or {}).get("fp64_atomic_ceiling_per_s"),
                          "fp64_atomics_frac": dat / detail["fp64_atomic_ceiling_per_s"]
-                         if detail and detail.get("fp64_atomic_ceiling_per_s") else None},
+                         if detail and detail.get("fp64_atomic_ceiling_per_s") else None,
+                         # in the step the launch overlaps the side-stream zeroing of other
+                         # matrices; the same launch timed alone (detail section):
+                         "isolated_launch_ms": iso_ms,
+                         "isolated_frac": alg_bytes_assemble(ctx, dprs) / (iso_ms / 1e3) / 1e9 / hbm_peak
+                         if iso_ms else None},
             "per_launch_ms": {lab: round(per_launch[k] * 1e3, 4) for k, (lab, _) in enumerate(ctx["launches"])},
             "clocks": clk, "gpu_launches": NL * args.steps, "e2e": e2e, "cpu_baseline": cpu, "detail": detail,
         }
@@ -564,6 +580,13 @@ def measure_detail(F, ctx, args, device, reps=5):
             b.record()
             torch.cuda.synchronize()
             rec["assemble_fp32_with_zero_ms"] = a.elapsed_time(b) / 3
+            # the launch alone: no zeroing, nothing else running (the values accumulate)
+            a.record()
+            for _ in range(3):
+                F.assemble(pr["F"], ctx["cells"], ctx["verts"], pr["slot"], pr["val"], precision="fp32")
+            b.record()
+            torch.cuda.synchronize()
+            rec["assemble_fp32_ms"] = a.elapsed_time(b) / 3
             del A
             torch.cuda.empty_cache()
             if pr["form"] == 1:
