@@ -502,7 +502,10 @@ def main():
                          # matrices; the same launch timed alone (detail section):
                          "isolated_launch_ms": iso_ms,
                          "isolated_frac": alg_bytes_assemble(ctx, dprs) / (iso_ms / 1e3) / 1e9 / hbm_peak
-                         if iso_ms else None},
+                         if iso_ms else None,
+                         "isolated_fp64_atomics_frac": dat * per_launch[dom] / (iso_ms / 1e3) /
+                         detail["fp64_atomic_ceiling_per_s"]
+                         if iso_ms and detail.get("fp64_atomic_ceiling_per_s") else None},
             "per_launch_ms": {lab: round(per_launch[k] * 1e3, 4) for k, (lab, _) in enumerate(ctx["launches"])},
             "clocks": clk, "gpu_launches": NL * args.steps, "e2e": e2e, "cpu_baseline": cpu, "detail": detail,
         }
