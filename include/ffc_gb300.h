@@ -192,7 +192,8 @@ int ffc_assemble(const ffc_form* f, int64_t n_elem, const int32_t* cells, const 
  *   csr_val_a[slot[e][i1][i2]] += A_a^K[i1][i2],  csr_val_b[slot[e][i1][i2]] += A_b^K[i1][i2]
  * The pair (mass, Poisson), in either order, with FFC_FP32 runs as one launch: the cell's
  * geometry is computed once and each slot is loaded once for both matrices; each matrix
- * receives the contributions ffc_assemble computes for it. Any other pair of forms without
+ * receives the contributions ffc_assemble computes for it (the same arithmetic; the sums
+ * agree to rounding, the atomic order being free). Any other pair of forms without
  * coefficients runs as two ffc_assemble calls. csr_val_a and csr_val_b are distinct
  * device double [nnz] arrays, accumulated into. FFC_EINVAL for forms on different
  * spaces or one array passed twice; FFC_EUNSUPPORTED for forms with coefficients.
