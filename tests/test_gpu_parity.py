@@ -419,3 +419,32 @@ def test_assemble_pair_arguments(F):
     F.assemble_pair(F.Form(W.POISSON, 3, 2), F.Form(W.POISSON, 3, 2), cells, verts, slot, a, b, precision="fp32")
     assert torch.equal(a, b)
     assert F.status_poll() == 0
+
+
+@pytest.mark.parametrize("q", [2, 3])
+def test_full_size_pair_assembly(F, q):
+    """48^3 x 6 = 663,552 tets, P2 / P3, as the benchmark assembles them: the pair launch's
+    mass and Poisson matrices equal the single-form assemblies to FP64 rounding, the mass
+    matrix sums to |Omega| = 1 and the Poisson rows sum to zero."""
+    import torch
+
+    mesh = W.tet_scalar_mesh(48)
+    p = W.make_problem(mesh, W.POISSON, q)
+    row_ptr, col, slot_h = _pattern(F, p)
+    slot = _dev(slot_h, torch.int32)
+    cells, verts = _dev(mesh.cells, torch.int32), _dev(mesh.vertices, torch.float64)
+    fm, fp = F.Form(W.MASS, 3, q), F.Form(W.POISSON, 3, q)
+    vm = torch.zeros(col.size, dtype=torch.float64, device="cuda")
+    vp = torch.zeros_like(vm)
+    F.assemble_pair(fm, fp, cells, verts, slot, vm, vp, precision="fp32")
+    for f, got in ((fm, vm), (fp, vp)):
+        ref = torch.zeros_like(vm)
+        F.assemble(f, cells, verts, slot, ref, precision="fp32")
+        assert (got - ref).abs().max().item() <= 1e-13 * ref.abs().max().item()
+        del ref
+    assert F.status_poll() == 0
+    assert abs(vm.sum().item() - 1.0) < 1e-6
+    rows = torch.repeat_interleave(torch.arange(p.n_dof, device="cuda"),
+                                   torch.as_tensor(np.diff(row_ptr), device="cuda"))
+    rs = torch.zeros(p.n_dof, dtype=torch.float64, device="cuda").index_add_(0, rows, vp)
+    assert rs.abs().max().item() < 1e-5 * vp.abs().max().item()
