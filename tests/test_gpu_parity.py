@@ -448,3 +448,25 @@ def test_full_size_pair_assembly(F, q):
                                    torch.as_tensor(np.diff(row_ptr), device="cuda"))
     rs = torch.zeros(p.n_dof, dtype=torch.float64, device="cuda").index_add_(0, rows, vp)
     assert rs.abs().max().item() < 1e-5 * vp.abs().max().item()
+
+
+@pytest.mark.parametrize("prec,alg", [("fp32", "block"), ("fp64", "block"), ("bf16x3", "dense")])
+def test_full_size_convection_sampled(F, prec, alg):
+    """The vector-P2 convection workload at full size (40^3 x 6 = 384,000 tets), as the
+    benchmark tabulates it: several tiles per CTA, so the FP32 block kernel's staging
+    buffers rotate across tiles. 500 seeded cells and the last one against the oracle."""
+    import torch
+
+    p = W.ns_vp2(40)
+    m = p.mesh
+    fm = F.Form(W.NS_CONVECTION, 3, 2, algorithm=F.ALG_BLOCK if alg == "block" else F.ALG_DENSE)
+    A = F.tabulate(fm, _dev(m.cells, torch.int32), _dev(m.vertices, torch.float64),
+                   coeffs=_dev(p.coeffs, torch.float64), precision=prec)
+    assert F.status_poll() == 0
+    rng = np.random.default_rng(11)
+    idx = np.sort(rng.choice(m.n_elem, 500, replace=False))
+    idx[-1] = m.n_elem - 1
+    ref = OE.element_tensors(W.NS_CONVECTION, m.vertices[m.cells[idx]], 2, coeffs=p.coeffs[idx])
+    got = A[torch.as_tensor(idx, device="cuda")].double().cpu().numpy()
+    err = OE.frobenius_rel_error(got, ref)
+    assert err.max() <= (FP64_TOL if prec == "fp64" else FP32_TOL), err.max()
