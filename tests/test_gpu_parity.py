@@ -470,3 +470,22 @@ def test_full_size_convection_sampled(F, prec, alg):
     got = A[torch.as_tensor(idx, device="cuda")].double().cpu().numpy()
     err = OE.frobenius_rel_error(got, ref)
     assert err.max() <= (FP64_TOL if prec == "fp64" else FP32_TOL), err.max()
+
+
+@pytest.mark.parametrize("prec,alg", [("fp32", "block"), ("tf32x3", "dense")])
+def test_full_size_elasticity_p3_sampled(F, prec, alg):
+    """Elasticity vector P3 on the batched workload's largest mesh size (31^3 x 6 = 178,746
+    tets), tabulated as the benchmark times it (FP32 block kernel: 416 threads, two CTAs
+    per SM; 3xTF32 tensor cores): 300 seeded cells and the last one against the oracle."""
+    import torch
+
+    m = M.unit_cube_tets(31, 0.15, seed=4031)
+    fm = F.Form(W.ELASTICITY, 3, 3, algorithm=F.ALG_BLOCK if alg == "block" else F.ALG_DENSE)
+    A = F.tabulate(fm, _dev(m.cells, torch.int32), _dev(m.vertices, torch.float64), precision=prec)
+    assert F.status_poll() == 0
+    rng = np.random.default_rng(12)
+    idx = np.sort(rng.choice(m.n_elem, 300, replace=False))
+    idx[-1] = m.n_elem - 1
+    ref = OE.element_tensors(W.ELASTICITY, m.vertices[m.cells[idx]], 3)
+    got = A[torch.as_tensor(idx, device="cuda")].double().cpu().numpy()
+    assert OE.frobenius_rel_error(got, ref).max() <= FP32_TOL
