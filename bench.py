@@ -243,7 +243,7 @@ def alg_bytes_tabulate(ctx, n_local, out_bytes):
 # count (x8; slots, CSR values and cells all grow with it). Only valid for the FP32 SIMT
 # assembly kernels as captured; other kernels report null.
 FP64_NOMINAL_TFLOPS = 1.25  # GB300 FP64 (CUDA cores), nominal
-CAPTURED_TRAFFIC_GB = {("mass_p4", "fp32"): 1.467 * 8, ("poisson_p4", "fp32"): 1.524 * 8}
+CAPTURED_TRAFFIC_GB = {("mass_p4", "fp32"): 1.490 * 8, ("poisson_p4", "fp32"): 1.554 * 8}
 
 
 def measured_peaks():
