@@ -319,8 +319,10 @@ int ffc_assemble_rows(const ffc_form* f, const ffc_row_plan* plan, const int32_t
                       int64_t n_vert, double* csr_val, int precision, void* stream);
 
 /*
- * ffc_status_poll -- synchronise `stream`, return the device status bits
- * (FFC_FLAG_*) accumulated by earlier launches on the current device, and clear them.
+ * ffc_status_poll -- return the device status bits (FFC_FLAG_*) accumulated by earlier
+ * launches on the current device, and clear them. The read and the clear are ordered on
+ * `stream`, and the call then waits for `stream` only: launches on other streams keep
+ * running, and bits they set after the read are reported by a later poll.
  */
 int ffc_status_poll(void* stream, uint32_t* flags);
 
@@ -337,12 +339,16 @@ int ffc_status_poll(void* stream, uint32_t* flags);
  *   precision   FFC_FP64 or FFC_FP32 only
  *   host_flags  NULL, or receives the FFC_FLAG_* bits of this call; when non-NULL
  *               the call synchronises `stream` before returning
- * Forms whose reference tensor does not fit (4 copies of n*n*|alpha| values, e.g.
- * elasticity P3) are rejected with FFC_EINVAL before any device work.
+ * Forms whose reference tensor does not fit (4 copies of n*n*|alpha| values plus the
+ * reduced tensor of the block algorithm, e.g. elasticity P3) are rejected with FFC_EINVAL
+ * before any device work. The kernels are those ffc_tabulate chooses (the vector forms
+ * follow ffc_form_set_algorithm), so the results equal ffc_tabulate's bit for bit.
  * The first call on a device looks up the array's device address (with that device
- * current); make it before any stream capture. All calls share the array and leave
- * their contents in it: each call clears the status word and rewrites the reference
- * tensor, so calls that overlap on the GPU race and must be serialised by the caller.
+ * current). The reference tensor is uploaded from the form's host copy on every call,
+ * so the call returns FFC_EINVAL while `stream` is being captured into a graph. All
+ * calls share the array and leave their contents in it: each call clears the status
+ * word and rewrites the reference tensor, so calls that overlap on the GPU race and must
+ * be serialised by the caller.
  */
 int ffc_tabulate_static(const ffc_form* f, int64_t n_elem, const int32_t* cells, const double* vertices,
                         int64_t n_vert, const double* coeffs, void* A_K, int precision, void* stream,

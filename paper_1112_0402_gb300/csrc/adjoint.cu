@@ -126,18 +126,9 @@ int run(const LaunchArgs& a, const double* dA, double* dvert) {
   constexpr int N = nscalar(D, Q);
   constexpr size_t SMEM = size_t(D * (D + 1) / 2) * N * N * sizeof(double);
   auto kern = poisson_adjoint_kernel<D, Q>;
-  static int sms = 0, per_sm = 1;
-  if (sms == 0) {
-    if (SMEM > 48 * 1024 &&
-        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(SMEM)) != cudaSuccess)
-      return FFC_ECUDA;
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, THREADS, SMEM) != cudaSuccess)
-      return FFC_ECUDA;
-    if (per_sm < 1) per_sm = 1;
-  }
+  int sms = 0, per_sm = 1;
+  if (launch_config(reinterpret_cast<const void*>(kern), THREADS, SMEM, -1, &sms, &per_sm) != FFC_OK)
+    return FFC_ECUDA;
   long long grid = (long long)sms * per_sm;
   const long long need = (a.n_elem + THREADS - 1) / THREADS;
   if (grid > need) grid = need;

@@ -241,19 +241,11 @@ template <int V>
 int launch_variant(ffc_batch* b, cudaStream_t s) {
   constexpr int variant = V, BLK = VARIANT_BLOCK[V], KE = VARIANT_KE[V], MINB = VARIANT_MINB[V];
   auto kern = batch_assemble_kernel<BLK, KE, MINB>;
-  static bool attr = false;
-  if (!attr) {
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024) != cudaSuccess)
-      return FFC_ECUDA;
-    attr = true;
-  }
   if (b->smem[variant] > 96 * 1024) return FFC_EUNSUPPORTED;
-  if (b->grid[variant] == 0) {
-    int per_sm = 1;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, BLK, b->smem[variant]) != cudaSuccess)
-      return FFC_ECUDA;
-    b->grid[variant] = b->sms * std::max(1, per_sm);
-  }
+  int sms = 0, per_sm = 1;
+  if (launch_config(reinterpret_cast<const void*>(kern), BLK, b->smem[variant], -1, &sms, &per_sm) != FFC_OK)
+    return FFC_ECUDA;
+  b->grid[variant] = sms * std::max(1, per_sm);
   kern<<<b->grid[variant], BLK, b->smem[variant], s>>>(b->d_items[variant], int(b->items.size()),
                                                                   b->total_tiles[variant], b->d_queue);
   const cudaError_t e = cudaPeekAtLastError();

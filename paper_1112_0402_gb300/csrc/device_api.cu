@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <climits>
+#include <map>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -41,6 +42,46 @@ uint32_t* status_word() {
     g_status[dev] = p;
   }
   return g_status[dev];
+}
+
+int launch_config(const void* kernel, int threads, size_t dyn_smem, int carveout, int* sms, int* blocks_per_sm) {
+  struct Key {
+    const void* k;
+    int dev, threads, carveout;
+    size_t smem;
+    bool operator<(const Key& o) const {
+      if (k != o.k) return k < o.k;
+      if (dev != o.dev) return dev < o.dev;
+      if (threads != o.threads) return threads < o.threads;
+      if (carveout != o.carveout) return carveout < o.carveout;
+      return smem < o.smem;
+    }
+  };
+  static std::mutex lock;
+  static std::map<Key, std::pair<int, int>> cache;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  const Key key{kernel, dev, threads, carveout, dyn_smem};
+  std::lock_guard<std::mutex> g(lock);
+  auto it = cache.find(key);
+  if (it == cache.end()) {
+    int n_sm = 0, per_sm = 0;
+    if ((e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+      return cuda_fail(e, "cudaDeviceGetAttribute");
+    if (dyn_smem > 48 * 1024 &&
+        (e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(dyn_smem))) != cudaSuccess)
+      return cuda_fail(e, "cudaFuncSetAttribute");
+    if (carveout >= 0 &&
+        (e = cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, carveout)) != cudaSuccess)
+      return cuda_fail(e, "cudaFuncSetAttribute");
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, dyn_smem)) != cudaSuccess)
+      return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+    it = cache.emplace(key, std::make_pair(n_sm, per_sm > 0 ? per_sm : 1)).first;
+  }
+  if (sms) *sms = it->second.first;
+  if (blocks_per_sm) *blocks_per_sm = it->second.second;
+  return FFC_OK;
 }
 
 int ensure_device_tensors(ffc_form* f, DeviceTensors** out) {
@@ -259,14 +300,18 @@ int ffc_status_poll(void* stream, uint32_t* flags) {
   if (!flags) return FFC_EINVAL;
   uint32_t* st = status_word();
   if (!st) return FFC_ECUDA;
-  cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+  // read and clear in the order of `stream`, then wait for that stream only: work queued
+  // on other streams keeps running (bits it sets later appear at the next poll)
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  uint32_t v = 0;
+  cudaError_t e = cudaMemcpyAsync(&v, st, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync status");
+  e = cudaMemsetAsync(st, 0, sizeof(uint32_t), s);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync status");
+  e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
-  e = cudaMemcpy(flags, st, sizeof(uint32_t), cudaMemcpyDeviceToHost);
-  if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy status");
-  e = cudaMemset(st, 0, sizeof(uint32_t));
-  if (e != cudaSuccess) return cuda_fail(e, "cudaMemset status");
-  e = cudaDeviceSynchronize();
-  return e == cudaSuccess ? FFC_OK : cuda_fail(e, "cudaDeviceSynchronize");
+  *flags = v;
+  return FFC_OK;
 }
 
 }  // extern "C"

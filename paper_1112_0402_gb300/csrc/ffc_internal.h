@@ -74,6 +74,15 @@ int ensure_device_tensors(ffc_form* f, DeviceTensors** out);
 void release_device_tensors(ffc_form* f);
 uint32_t* status_word();  // library-owned device status word of the current device
 
+// Launch shape of one kernel on the current device: the device's SM count and how many
+// CTAs of `threads` threads with `dyn_smem` bytes of dynamic shared memory are resident
+// per SM. The first call for a (kernel, device, threads, dyn_smem) tuple raises the
+// kernel's dynamic shared-memory limit on that device when dyn_smem exceeds 48 KiB (and
+// sets its shared-memory carveout when carveout >= 0); the answers are cached per device
+// under a lock, so several host threads and several devices are served correctly.
+// Returns FFC_OK or FFC_ECUDA (message via ffc_last_error).
+int launch_config(const void* kernel, int threads, size_t dyn_smem, int carveout, int* sms, int* blocks_per_sm);
+
 struct LaunchArgs {
   const ffc_form* f;
   int64_t n_elem;

@@ -46,12 +46,9 @@ __global__ void __launch_bounds__(256) scatter_add_kernel(const T* __restrict__ 
 template <typename T>
 int run(const void* a, const int32_t* slot, double* csr_val, long long nnz, long long total, unsigned* status,
         cudaStream_t s) {
-  static int sms = 0;
-  if (sms == 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  }
+  int sms = 0;
+  if (launch_config(reinterpret_cast<const void*>(scatter_add_kernel<T>), 256, 0, -1, &sms, nullptr) != FFC_OK)
+    return FFC_ECUDA;
   long long grid = (total + 4 * 256 - 1) / (4 * 256);
   const long long cap = (long long)sms * 8;  // 8 CTAs of 256 threads per SM, grid-stride beyond
   if (grid > cap) grid = cap;

@@ -9,25 +9,14 @@ int run(const LaunchArgs& a) {
   using C = BlockCfg<D, FORM, Q, T>;
   constexpr size_t SMEM = C::SMEM + BlockStaging<C, T, ASSEMBLE>::BYTES;
   auto kern = simt_block_kernel<D, FORM, Q, T, ASSEMBLE>;
-  static int sms = 0, per_sm = 1;
-  if (sms == 0) {
-    if (SMEM > 48 * 1024 &&
-        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(SMEM)) != cudaSuccess)
-      return FFC_ECUDA;
-    // elasticity: the whole unified L1 / shared array as shared memory, so the nine
-    // geometry blocks of several resident CTAs fit (measured faster; the convection
-    // kernel and the batched kernel, which lean on L1 for their streamed loads, keep the
-    // default split)
-    if (FORM == FFC_ELASTICITY &&
-        cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100) != cudaSuccess)
-      return FFC_ECUDA;
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, C::NT, SMEM) != cudaSuccess)
-      return FFC_ECUDA;
-    if (per_sm < 1) per_sm = 1;
-  }
+  // elasticity: the whole unified L1 / shared array as shared memory, so the nine
+  // geometry blocks of several resident CTAs fit (measured faster; the convection
+  // kernel and the batched kernel, which lean on L1 for their streamed loads, keep the
+  // default split)
+  int sms = 0, per_sm = 1;
+  if (launch_config(reinterpret_cast<const void*>(kern), C::NT, SMEM, FORM == FFC_ELASTICITY ? 100 : -1, &sms,
+                    &per_sm) != FFC_OK)
+    return FFC_ECUDA;
   SimtParams p{};
   p.cells = a.cells;
   p.vertices = a.vertices;

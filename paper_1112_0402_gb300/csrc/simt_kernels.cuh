@@ -375,19 +375,9 @@ template <int D, int FORM, int Q, typename T, bool ASSEMBLE>
 int launch_simt_one(const SimtParams& prm, const void* a0_rows, const void* a0_cols, cudaStream_t stream) {
   using C = SimtCfg<D, FORM, Q, T, 0, 0, ASSEMBLE>;
   auto kern = simt_tabulate_kernel<D, FORM, Q, T, ASSEMBLE>;
-  static int blocks_per_sm = -1;
-  static int sms = 0;
-  if (blocks_per_sm < 0) {
-    if (C::SMEM > 48 * 1024)
-      if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(C::SMEM)) != cudaSuccess)
-        return FFC_ECUDA;
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    int b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, C::NT, C::SMEM) != cudaSuccess) return FFC_ECUDA;
-    blocks_per_sm = b > 0 ? b : 1;
-  }
+  int sms = 0, blocks_per_sm = 1;
+  if (launch_config(reinterpret_cast<const void*>(kern), C::NT, C::SMEM, -1, &sms, &blocks_per_sm) != FFC_OK)
+    return FFC_ECUDA;
   SimtParams p = prm;
   p.a0 = C::REG_A0 ? a0_rows : a0_cols;
   const long long n_tiles = (p.n_elem + C::E - 1) / C::E;

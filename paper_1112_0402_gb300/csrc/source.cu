@@ -133,16 +133,9 @@ template <int D, int Q, typename T, bool ASSEMBLE>
 int launch_source_one(const SourceParams& p, cudaStream_t stream) {
   using C = SourceCfg<D, Q, T>;
   auto kern = source_kernel<D, Q, T, ASSEMBLE>;
-  static int blocks_per_sm = -1;
-  static int sms = 0;
-  if (blocks_per_sm < 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    int b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, C::NT, C::SMEM) != cudaSuccess) return FFC_ECUDA;
-    blocks_per_sm = b > 0 ? b : 1;
-  }
+  int sms = 0, blocks_per_sm = 1;
+  if (launch_config(reinterpret_cast<const void*>(kern), C::NT, C::SMEM, -1, &sms, &blocks_per_sm) != FFC_OK)
+    return FFC_ECUDA;
   const long long n_tiles = (p.n_elem + C::TC - 1) / C::TC;
   long long grid = (long long)sms * blocks_per_sm;
   if (grid > n_tiles) grid = n_tiles;

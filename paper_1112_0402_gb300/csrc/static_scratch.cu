@@ -11,8 +11,8 @@
 //
 // The array lives in every GPU that loads the library until the process exits.
 // Its device address is looked up once per device (cudaGetSymbolAddress, with that
-// device current) on the first call there; make that first call before any stream
-// capture. Every call shares the array and leaves its contents behind: the status
+// device current) on the first call there. The call refuses to run while its stream is
+// being captured into a graph. Every call shares the array and leaves its contents behind: the status
 // word is cleared at the start of each call and the reference tensor is rewritten,
 // so calls that overlap on the GPU (different streams, different host threads)
 // race with each other and must be serialised by the caller.
@@ -49,6 +49,11 @@ __global__ void expand_reference_tensor(double* rows64, double* cols64, float* r
   }
 }
 
+__global__ void narrow_to_f32(const double* src, float* dst, long long n) {
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x)
+    dst[k] = float(src[k]);
+}
+
 int scratch_address(unsigned char** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -82,8 +87,10 @@ extern "C" int ffc_tabulate_static(const ffc_form* f, int64_t n_elem, const int3
     set_error("ffc_tabulate_static: invalid argument (precision must be FFC_FP64 or FFC_FP32)");
     return FFC_EINVAL;
   }
-  const size_t nn = f->n_entries(), na = size_t(f->kernel_na());
-  const size_t need = nn * na * (2 * sizeof(double) + 2 * sizeof(float)) + 4 * 256;
+  auto align = [](size_t x) { return (x + 255) / 256 * 256; };
+  const size_t nn = f->n_entries(), na = size_t(f->kernel_na()), nr = f->R.size();
+  const size_t need = 2 * align(nn * na * sizeof(double)) + 2 * align(nn * na * sizeof(float)) +
+                      align(nr * sizeof(double)) + align(nr * sizeof(float));
   if (need > kStaticA0Bytes) {
     set_error("ffc_tabulate_static: the reference tensor needs " + std::to_string(need) +
               " bytes, more than the fixed 2 MiB scratch");
@@ -92,15 +99,23 @@ extern "C" int ffc_tabulate_static(const ffc_form* f, int64_t n_elem, const int3
   if (host_flags) *host_flags = 0;
   if (n_elem == 0) return FFC_OK;
   if (!cells || !vertices || n_vert == 0 || !A_K || (f->ncoeff > 0 && !coeffs) ||
-      (reinterpret_cast<uintptr_t>(cells) & 15) || (reinterpret_cast<uintptr_t>(A_K) & 15)) {
-    set_error("ffc_tabulate_static: invalid pointer");
+      (reinterpret_cast<uintptr_t>(cells) & 15) || (reinterpret_cast<uintptr_t>(vertices) & 7) ||
+      (reinterpret_cast<uintptr_t>(A_K) & 15)) {
+    set_error("ffc_tabulate_static: null or misaligned pointer");
+    return FFC_EINVAL;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // the reference tensor is uploaded from the form's host copy on every call: a captured
+  // copy would keep that host pointer, so capture is refused rather than recorded
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  cudaError_t e = cudaStreamIsCapturing(s, &cap);
+  if (e != cudaSuccess || cap != cudaStreamCaptureStatusNone) {
+    set_error("ffc_tabulate_static: not callable while the stream is being captured");
     return FFC_EINVAL;
   }
   unsigned char* base = nullptr;
   int rc = scratch_address(&base);
   if (rc != FFC_OK) return rc;
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  auto align = [](size_t x) { return (x + 255) / 256 * 256; };
   uint32_t* status = reinterpret_cast<uint32_t*>(base);
   unsigned char* p = base + kStatusSlot;
   DeviceTensors t;
@@ -111,21 +126,45 @@ extern "C" int ffc_tabulate_static(const ffc_form* f, int64_t n_elem, const int3
   t.a0_f32 = reinterpret_cast<float*>(p);
   p += align(nn * na * sizeof(float));
   t.a0t_f32 = reinterpret_cast<float*>(p);
-  cudaError_t e = cudaMemsetAsync(status, 0, sizeof(uint32_t), s);
+  p += align(nn * na * sizeof(float));
+  if (nr > 0) {  // reduced reference tensor of the block algorithm (vector forms)
+    t.r_f64 = reinterpret_cast<double*>(p);
+    p += align(nr * sizeof(double));
+    t.r_f32 = reinterpret_cast<float*>(p);
+  }
+  e = cudaMemsetAsync(status, 0, sizeof(uint32_t), s);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(t.a0_f64, f->kernel_a0().data(), nn * na * sizeof(double), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && nr > 0)
+    e = cudaMemcpyAsync(t.r_f64, f->R.data(), nr * sizeof(double), cudaMemcpyHostToDevice, s);
   if (e != cudaSuccess) {
     set_error(std::string("ffc_tabulate_static: ") + cudaGetErrorString(e));
     return FFC_ECUDA;
   }
   expand_reference_tensor<<<64, 256, 0, s>>>(t.a0_f64, t.a0t_f64, t.a0_f32, t.a0t_f32, int(nn), int(na));
-  if (cudaPeekAtLastError() != cudaSuccess) return FFC_ECUDA;
+  if ((e = cudaPeekAtLastError()) != cudaSuccess) {
+    set_error(std::string("ffc_tabulate_static: ") + cudaGetErrorString(e));
+    return FFC_ECUDA;
+  }
+  if (nr > 0) {  // FP32 copy of R (a host conversion would need a staging buffer)
+    narrow_to_f32<<<8, 256, 0, s>>>(t.r_f64, t.r_f32, (long long)nr);
+    if ((e = cudaPeekAtLastError()) != cudaSuccess) {
+      set_error(std::string("ffc_tabulate_static: ") + cudaGetErrorString(e));
+      return FFC_ECUDA;
+    }
+  }
   LaunchArgs a{f, n_elem, cells, vertices, n_vert, coeffs, A_K, nullptr, nullptr, 0, &t, status, stream};
-  rc = launch_simt_tri(a, precision, false);
+  // the same kernel choice as ffc_tabulate for the CUDA-core precisions
+  rc = FFC_EUNSUPPORTED;
+  if (f->kr > 0 && f->algorithm != FFC_ALG_DENSE) rc = launch_simt_block(a, precision, false);
+  if (rc == FFC_EUNSUPPORTED) rc = launch_simt_tri(a, precision, false);
   if (rc == FFC_EUNSUPPORTED) rc = launch_simt_tet_mass(a, precision, false);
   if (rc == FFC_EUNSUPPORTED) rc = launch_simt_tet_poisson(a, precision, false);
   if (rc == FFC_EUNSUPPORTED) rc = launch_simt_vector(a, precision, false);
   if (rc == FFC_EUNSUPPORTED) rc = launch_simt_source(a, precision, false);
+  if (rc == FFC_EUNSUPPORTED) set_error("ffc_tabulate_static: no kernel built for this form/precision");
+  if (rc == FFC_ECUDA) set_error(std::string("ffc_tabulate_static: kernel launch: ") +
+                                 cudaGetErrorString(cudaGetLastError()));
   if (rc != FFC_OK) return rc;
   if (host_flags) {
     e = cudaMemcpyAsync(host_flags, status, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);

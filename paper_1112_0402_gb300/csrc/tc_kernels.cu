@@ -710,14 +710,9 @@ int launch_one(const LaunchArgs& a) {
   p.status = a.status;
   using W = TcWsCfg<D, FORM, Q, MODE>;
   auto kern = tc_ws_kernel<D, FORM, Q, MODE, ASSEMBLE>;
-  static int sms = 0;
-  if (sms == 0) {
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(W::SMEM)) != cudaSuccess)
-      return FFC_ECUDA;
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  }
+  int sms = 0;
+  if (launch_config(reinterpret_cast<const void*>(kern), WS_THREADS, W::SMEM, -1, &sms, nullptr) != FFC_OK)
+    return FFC_ECUDA;
   const long long n_tiles = (a.n_elem + N_CELLS - 1) / N_CELLS;
   long long grid = sms;
   if (grid > n_tiles) grid = n_tiles;
