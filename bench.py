@@ -150,8 +150,8 @@ def build_workload(F, n, device):
         row_ptr, col, slot = F.csr_pattern(p.dofmap, p.n_dof)
         slot_d = torch.as_tensor(slot, device=device)
         del slot
-        if q >= 3:  # the row-owner assembly of the detail section needs the pattern
-            ctx.setdefault("patterns", {})[q] = (p.dofmap, p.n_dof, row_ptr, col)
+        # host copy of the pattern: the row-owner assembly and the full-size tests use it
+        ctx.setdefault("patterns", {})[q] = {"dofmap": p.dofmap, "n_dof": p.n_dof, "row_ptr": row_ptr, "col": col}
         for form in FORMS:
             ctx["problems"].append({
                 "form": form, "q": q, "F": F.Form(form, F.TETRAHEDRON, q), "n_local": p.n_local,
@@ -215,6 +215,13 @@ def assemble_step(F, ctx, precision, events=None):
         if events is not None:
             events[j][1].record(main)
     main.wait_stream(side)
+
+
+def run_headline_step(F, ctx, precision, pair_degrees=(1, 2, 3)):
+    """One headline step (every matrix zeroed and assembled) on the current stream."""
+    if "launches" not in ctx:
+        ctx["launches"] = launch_list(ctx, set(pair_degrees))
+    assemble_step(F, ctx, precision)
 
 
 def launch_assembly(F, ctx, ks, cells, verts, precision):
@@ -610,7 +617,10 @@ def measure_detail(F, ctx, args, device, reps=5):
                 torch.cuda.empty_cache()
         out[key] = rec
     # row-owner assembly (ffc_assemble_rows: exact fixed-point sums, no atomics, no zeroing)
-    for q, (dofmap, n_dof, row_ptr, col) in sorted(ctx.get("patterns", {}).items()):
+    for q, pat in sorted(ctx.get("patterns", {}).items()):
+        if q < 3:
+            continue
+        dofmap, n_dof, row_ptr, col = pat["dofmap"], pat["n_dof"], pat["row_ptr"], pat["col"]
         plan = F.RowPlan(torch.as_tensor(dofmap, device=device), n_dof, torch.as_tensor(row_ptr, device=device),
                          torch.as_tensor(col, device=device))
         for pr in ctx["problems"]:

@@ -271,36 +271,46 @@ void ffc_batch_destroy(ffc_batch* b);
  * Row-owner assembly: Algorithm 2 (Section 2.2) with its loops ordered by global row.
  * Algorithm 2 adds the element tensor of each cell into the matrix; the entries of
  * global row r therefore receive exactly the element-tensor rows A^K[i1][:] of the
- * cells K with dofmap[K][i1] = r. ffc_assemble_rows lets one warp own each row: it
- * computes those rows from a per-cell geometry tensor G_K (A^K = A0 : G_K, Section 3.2),
- * sums them in shared memory and writes the finished row once. No global atomics, no
- * zeroing: every CSR value is overwritten.
+ * cells K with dofmap[K][i1] = r (the "pairs" (K, i1) of row r). The rows are cut into
+ * chunks of consecutive rows (at most 4096 stored entries each); one CTA sums a chunk in
+ * shared memory, computing the entries from a per-cell geometry tensor G_K
+ * (A^K = A0 : G_K, Section 3.2), and writes the chunk's CSR values once, in order. No
+ * global atomics, no zeroing: every CSR value is overwritten.
  *
  * The sums are exact: each contribution (FP32 or FP64, as the contraction produced it)
- * is converted to 64-bit fixed point with a per-row unit u = 2^-62 * 2^eb, where 2^eb
- * is at least twice a bound on the row's sum of |contributions|; integer sums do not
+ * is converted to fixed point with one unit per chunk, u = 2^(eb-62), where 2^(eb-1)
+ * bounds every partial sum of the chunk's entries (the largest per-pair bound
+ * max|A0[i1][.][.]| * sum|G_K| times the most pairs of one row); integer sums do not
  * depend on their order, and each result is rounded once to FP64 (nearest even). Per
  * entry: |result - exact sum of the contributions| <= m * u + ulp(result) / 2 with m the
  * entry's number of contributions. Results are bitwise reproducible.
  *
  * ffc_row_plan_create -- the row view of a dof map and its CSR pattern, built on the
  * device once per (mesh, space):
- *   dofmap   device int32 [n_elem][n_local], global ids in [0, n_dof)
+ *   dofmap   device int32 [n_elem][n_local], global ids in [0, n_dof), n_local <= 64
  *   row_ptr  device int64 [n_dof + 1], col device int32 [nnz]: the pattern of
  *            ffc_csr_pattern (columns sorted within each row), copied to the device
- * The plan stores, per row r, the (e, i1) pairs with dofmap[e][i1] = r in increasing
- * e * n_local + i1 order, and for each pair the position of column dofmap[e][i2] inside
- * row r (uint16). It owns n_elem * n_local * (n_local * 2 + 4) + n_dof * 12 bytes of
- * device memory plus an [n_elem][8]-double geometry scratch; row_ptr is copied, so
- * dofmap, row_ptr and col may be freed afterwards. The call synchronises `stream`.
+ * The plan stores, per chunk, the chunk's pairs grouped by local index i1 as
+ * e * n_local + i1, and for every pair and local column i2 the position of column
+ * dofmap[e][i2] inside the chunk (uint16). It owns
+ * about n_elem * n_local * (2 * n_local + 4) + n_dof * 8 bytes of device memory plus an
+ * [n_elem][12]-double geometry scratch (ffc_row_plan_layout reports the exact figure);
+ * row_ptr is copied, so dofmap, row_ptr and col may be freed afterwards. The call
+ * synchronises `stream`.
  * Errors: FFC_EBOUNDS for a dof id outside [0, n_dof) or a (row, col) pair of a cell
- * missing from the pattern; FFC_EINVAL for a row longer than 65535 entries, a row_ptr
- * that is not monotone within [0, nnz], or n_elem * n_local >= 2^31.
+ * missing from the pattern; FFC_EINVAL for n_local outside [2, 64], a row with more than
+ * 4096 entries or more than 512 pairs, a row_ptr that is not monotone within [0, nnz], or
+ * n_elem * n_local >= 2^31.
  */
 int ffc_row_plan_create(int64_t n_elem, int n_local, const int32_t* dofmap, int64_t n_dof, const int64_t* row_ptr,
                         const int32_t* col, int64_t nnz, void* stream, ffc_row_plan** out);
 /* Rows, stored entries, longest row and most cells sharing one dof. */
 int ffc_row_plan_info(const ffc_row_plan* p, int64_t* n_dof, int64_t* nnz, int* max_row, int* max_incidence);
+/* Chunks, entries and pairs of the largest chunk, bytes of the largest chunk's plan data
+ * (class offsets, pairs and positions) and the plan's device memory in bytes. Any output
+ * pointer may be NULL. */
+int ffc_row_plan_layout(const ffc_row_plan* p, int64_t* n_chunks, int* max_chunk_values, int* max_chunk_pairs,
+                        int* max_region_bytes, int64_t* device_bytes);
 void ffc_row_plan_destroy(ffc_row_plan* p);
 
 /*
@@ -312,11 +322,24 @@ void ffc_row_plan_destroy(ffc_row_plan* p);
  * FP32 exactly as ffc_assemble computes them (the same contributions), FFC_FP64: in FP64.
  * Two launches on `stream`: the geometry tensors into the plan's scratch, then the rows.
  * Calls that share a plan must be ordered on one stream (they share the scratch).
- * A non-finite G_K (a degenerate cell, FFC_FLAG_DEGENERATE) makes its rows NaN.
- * Other forms: FFC_EUNSUPPORTED. The plan's n_local must equal the form's.
+ * A non-finite G_K (a degenerate cell, FFC_FLAG_DEGENERATE) makes the values of the
+ * chunk that holds its rows NaN. Other forms: FFC_EUNSUPPORTED. The plan's n_local must
+ * equal the form's.
  */
 int ffc_assemble_rows(const ffc_form* f, const ffc_row_plan* plan, const int32_t* cells, const double* vertices,
                       int64_t n_vert, double* csr_val, int precision, void* stream);
+
+/*
+ * ffc_assemble_rows_pair -- ffc_assemble_rows for two forms on the plan's space into two
+ * matrices with the plan's pattern. The pair (mass, Poisson), in either order, is one
+ * pass: each cell's geometry is computed once, each position is read once and feeds both
+ * matrices; every value equals the one ffc_assemble_rows writes for that form, bit for
+ * bit. Two forms of one kind run as two ffc_assemble_rows calls. csr_val_a and csr_val_b
+ * are distinct device double [nnz] arrays, overwritten.
+ */
+int ffc_assemble_rows_pair(const ffc_form* fa, const ffc_form* fb, const ffc_row_plan* plan, const int32_t* cells,
+                           const double* vertices, int64_t n_vert, double* csr_val_a, double* csr_val_b,
+                           int precision, void* stream);
 
 /*
  * ffc_status_poll -- return the device status bits (FFC_FLAG_*) accumulated by earlier
@@ -364,6 +387,29 @@ int ffc_tabulate_static(const ffc_form* f, int64_t n_elem, const int32_t* cells,
  * stays usable. FFC_EINVAL for polls > 2^20.
  */
 int ffc_diag_bounded_wait(uint32_t polls, void* stream);
+
+/*
+ * ffc_diag_peak -- measures one compute ceiling of the current device (the denominators
+ * of the roofline fractions of ALU-, tensor- and shared-atomic-bound kernels):
+ *   FFC_PEAK_FP64_FMA, FFC_PEAK_FP32_FMA   fused multiply-add rate of the CUDA cores
+ *                                          (flop/s, an FMA counts 2): eight independent
+ *                                          chains per thread, 1024 threads per SM;
+ *   FFC_PEAK_TF32_MMA, FFC_PEAK_BF16_MMA   dense tcgen05.mma rate (flop/s): one CTA per SM
+ *                                          issuing M=128, N=256 MMAs (K = 8 tf32 / 16 bf16)
+ *                                          on shared-memory operands, FP32 accumulation;
+ *   FFC_PEAK_SMEM_ATOMIC_U32               32-bit shared-memory atomic adds per second,
+ *                                          conflict-free addresses.
+ * The probe is launched once to warm up and once timed with CUDA events on `stream`;
+ * the call synchronises `stream`. rate receives the operations per second, seconds (may
+ * be NULL) the timed launch's duration. FFC_ETIMEOUT if the tensor-core probe's bounded
+ * wait gave up. There is no INT8 probe: sm_103a has no tcgen05 kind::i8.
+ */
+#define FFC_PEAK_FP64_FMA 0
+#define FFC_PEAK_FP32_FMA 1
+#define FFC_PEAK_TF32_MMA 2
+#define FFC_PEAK_BF16_MMA 3
+#define FFC_PEAK_SMEM_ATOMIC_U32 4
+int ffc_diag_peak(int kind, double* rate, double* seconds, void* stream);
 
 /* Human-readable name of a status code (static string). */
 const char* ffc_status_string(int status);

@@ -7,5 +7,5 @@ this package only marshals arguments to it.
 """
 from .api import (ALG_AUTO, ALG_BLOCK, ALG_DENSE, BF16X3, ELASTICITY, FLAG_BOUNDS, FLAG_DEGENERATE, FLAG_TIMEOUT, FP32, FP64, MASS, NS_CONVECTION,  # noqa
                   POISSON, SOURCE, TETRAHEDRON, TF32, TF32X3, TRIANGLE, Batch, FFCError, Form, RowPlan, assemble,
-                  assemble_pair, assemble_rows, csr_pattern, diag_bounded_wait,
+                  assemble_pair, assemble_rows, assemble_rows_pair, csr_pattern, diag_bounded_wait, diag_peak,
                   scatter_add, status_poll, tabulate, tabulate_adjoint, tabulate_static)

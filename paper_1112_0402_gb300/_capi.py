@@ -49,9 +49,14 @@ SIGNATURES = {
                                            ctypes.c_int64, c_vp, ctypes.POINTER(c_vp)]),
     "ffc_row_plan_info": (ctypes.c_int, [c_vp, c_i64p, c_i64p, ctypes.POINTER(ctypes.c_int),
                                          ctypes.POINTER(ctypes.c_int)]),
+    "ffc_row_plan_layout": (ctypes.c_int, [c_vp, c_i64p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                           ctypes.POINTER(ctypes.c_int), c_i64p]),
     "ffc_row_plan_destroy": (None, [c_vp]),
+    "ffc_assemble_rows_pair": (ctypes.c_int, [c_vp, c_vp, c_vp, c_vp, c_vp, ctypes.c_int64, c_vp, c_vp, ctypes.c_int,
+                                              c_vp]),
     "ffc_assemble_rows": (ctypes.c_int, [c_vp, c_vp, c_vp, c_vp, ctypes.c_int64, c_vp, ctypes.c_int, c_vp]),
     "ffc_diag_bounded_wait": (ctypes.c_int, [ctypes.c_uint32, c_vp]),
+    "ffc_diag_peak": (ctypes.c_int, [ctypes.c_int, c_dblp, c_dblp, c_vp]),
     "ffc_status_poll": (ctypes.c_int, [c_vp, c_u32p]),
     "ffc_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "ffc_last_error": (ctypes.c_char_p, []),

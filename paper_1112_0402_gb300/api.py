@@ -219,6 +219,11 @@ class RowPlan:
         _check(lib().ffc_row_plan_info(h, ctypes.byref(nd), ctypes.byref(nnz), ctypes.byref(mr), ctypes.byref(mi)),
                "ffc_row_plan_info")
         self.n_dof, self.nnz, self.max_row, self.max_incidence = nd.value, nnz.value, mr.value, mi.value
+        nc, vm, pm, gr, nb = ctypes.c_int64(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int64()
+        _check(lib().ffc_row_plan_layout(h, ctypes.byref(nc), ctypes.byref(vm), ctypes.byref(pm), ctypes.byref(gr),
+                                         ctypes.byref(nb)), "ffc_row_plan_layout")
+        self.n_chunks, self.max_chunk_values, self.max_chunk_pairs = nc.value, vm.value, pm.value
+        self.max_region_bytes, self.device_bytes = gr.value, nb.value
 
     @property
     def handle(self):
@@ -248,6 +253,22 @@ def assemble_rows(form: Form, plan: RowPlan, cells, vertices, csr_val, precision
     _check(lib().ffc_assemble_rows(form.handle, plan.handle, c, v, vertices.shape[0], val, p, _stream(stream)),
            "ffc_assemble_rows")
     return csr_val
+
+
+def assemble_rows_pair(form_a: Form, form_b: Form, plan: RowPlan, cells, vertices, csr_val_a, csr_val_b,
+                       precision="fp32", stream=None):
+    """Two forms on the plan's space into two matrices (overwritten) by row-owner assembly
+    (ffc_assemble_rows_pair); the (mass, Poisson) pair is one pass."""
+    import torch
+
+    p = _prec(precision)
+    c = _dev_ptr(cells, torch.int32, "cells", (cells.shape[0], form_a.dim + 1))
+    v = _dev_ptr(vertices, torch.float64, "vertices")
+    va = _dev_ptr(csr_val_a, torch.float64, "csr_val_a", (plan.nnz,))
+    vb = _dev_ptr(csr_val_b, torch.float64, "csr_val_b", (plan.nnz,))
+    _check(lib().ffc_assemble_rows_pair(form_a.handle, form_b.handle, plan.handle, c, v, vertices.shape[0], va, vb, p,
+                                        _stream(stream)), "ffc_assemble_rows_pair")
+    return csr_val_a, csr_val_b
 
 
 def assemble_pair(form_a: Form, form_b: Form, cells, vertices, slot, csr_val_a, csr_val_b, precision="fp32",
@@ -308,6 +329,18 @@ def diag_bounded_wait(polls: int = 4096, stream=None) -> None:
     """Launches the failure-detection probe (ffc_diag_bounded_wait): a bounded device
     wait that nothing ends; status_poll() then reports FLAG_TIMEOUT."""
     _check(lib().ffc_diag_bounded_wait(polls, _stream(stream)), "ffc_diag_bounded_wait")
+
+
+PEAKS = {"fp64_fma": 0, "fp32_fma": 1, "tf32_mma": 2, "bf16_mma": 3, "smem_atomic_u32": 4}
+
+
+def diag_peak(kind: str, stream=None) -> tuple[float, float]:
+    """Measured compute ceiling of the current device (ffc_diag_peak): (operations per
+    second, seconds of the timed launch). kind is one of PEAKS."""
+    rate, sec = ctypes.c_double(), ctypes.c_double()
+    _check(lib().ffc_diag_peak(PEAKS[kind], ctypes.byref(rate), ctypes.byref(sec), _stream(stream)),
+           "ffc_diag_peak")
+    return rate.value, sec.value
 
 
 def status_poll(stream=None) -> int:

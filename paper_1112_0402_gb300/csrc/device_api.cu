@@ -59,6 +59,9 @@ int launch_config(const void* kernel, int threads, size_t dyn_smem, int carveout
   };
   static std::mutex lock;
   static std::map<Key, std::pair<int, int>> cache;
+  // the dynamic shared-memory limit is a property of the kernel on a device: only raised,
+  // never lowered, so every launch shape cached before stays valid
+  static std::map<std::pair<const void*, int>, size_t> smem_limit;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
@@ -69,9 +72,12 @@ int launch_config(const void* kernel, int threads, size_t dyn_smem, int carveout
     int n_sm = 0, per_sm = 0;
     if ((e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
       return cuda_fail(e, "cudaDeviceGetAttribute");
-    if (dyn_smem > 48 * 1024 &&
-        (e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(dyn_smem))) != cudaSuccess)
-      return cuda_fail(e, "cudaFuncSetAttribute");
+    size_t& limit = smem_limit[std::make_pair(kernel, dev)];
+    if (dyn_smem > 48 * 1024 && dyn_smem > limit) {
+      if ((e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(dyn_smem))) != cudaSuccess)
+        return cuda_fail(e, "cudaFuncSetAttribute");
+      limit = dyn_smem;
+    }
     if (carveout >= 0 &&
         (e = cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, carveout)) != cudaSuccess)
       return cuda_fail(e, "cudaFuncSetAttribute");
@@ -121,6 +127,25 @@ int ensure_device_tensors(ffc_form* f, DeviceTensors** out) {
       return rc;
     }
   }
+  if (f->rank == 2) {
+    const size_t n = size_t(f->n);
+    std::vector<double> soa(nn * na);
+    for (size_t i1 = 0; i1 < n; ++i1)
+      for (size_t a = 0; a < na; ++a)
+        for (size_t i2 = 0; i2 < n; ++i2) soa[(i1 * na + a) * n + i2] = rows[(i1 * n + i2) * na + a];
+    std::vector<float> soa32(soa.begin(), soa.end());
+    if ((rc = upload(&t.a0s_f64, soa)) || (rc = upload(&t.a0s_f32, soa32))) {
+      cudaFree(t.a0_f64);
+      cudaFree(t.a0t_f64);
+      cudaFree(t.a0_f32);
+      cudaFree(t.a0t_f32);
+      cudaFree(t.r_f64);
+      cudaFree(t.r_f32);
+      cudaFree(t.a0s_f64);
+      cudaFree(t.a0s_f32);
+      return rc;
+    }
+  }
   auto res = f->dev.emplace(dev, t);
   *out = &res.first->second;
   return FFC_OK;
@@ -141,6 +166,8 @@ void release_device_tensors(ffc_form* f) {
       for (void* q : fam) cudaFree(q);
     cudaFree(t.r_f64);
     cudaFree(t.r_f32);
+    cudaFree(t.a0s_f64);
+    cudaFree(t.a0s_f32);
   }
   f->dev.clear();
   cudaSetDevice(cur);

@@ -18,6 +18,10 @@ struct DeviceTensors {
   double* a0t_f64 = nullptr;  // [na][nn]  transposed (coalesced over i)
   float* a0_f32 = nullptr;    // [nn][na]
   float* a0t_f32 = nullptr;   // [na][nn]
+  // bilinear forms: rows of A0 by i1, then alpha, then i2 ([n][na][n]; the row-owner kernels,
+  // whose lanes take consecutive columns i2 of one row i1)
+  double* a0s_f64 = nullptr;
+  float* a0s_f32 = nullptr;
   // tcgen05 operands: A0 split into TF32 (family 0: 2 parts) or BF16 (family 1: 3 parts),
   // each part laid out per 128-entry M-tile in the core-matrix layout
   void* tc_part[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};

@@ -4,38 +4,72 @@
 // A^K[i1][i2]; done cell by cell on a GPU, every addition is a global FP64 atomic and the
 // matrix must be zeroed first. Here the same sums are taken row by row instead: the
 // entries of global row r receive exactly the rows A^K[i1][:] of the cells K that hold r
-// as local dof i1. A warp owns a row, computes those element-tensor rows on the fly from
-// a per-cell geometry tensor G_K (A^K[i1][i2] = sum_alpha A0[i1][i2][alpha] G_K[alpha],
-// Section 3.2) and sums them in shared memory, then writes the finished row once: no
-// global atomics, no zeroing pass, every CSR value written exactly once.
+// as local dof i1 (the "pairs" (K, i1) of row r). The rows are cut into chunks of
+// consecutive rows (at most 4096 values and 512 pairs each); a CTA sums one chunk at a
+// time in shared memory, computing every element-tensor entry on the fly from a per-cell
+// geometry tensor G_K (A^K[i1][i2] = sum_alpha A0[i1][i2][alpha] G_K[alpha], Section
+// 3.2), and then writes the chunk's CSR values once, in order: no global atomics, no
+// zeroing pass, every value written exactly once.
 //
-// Exact accumulation. The sums are kept in 64-bit two's-complement fixed point with a
-// per-row unit u = 2^(eb - 64), where 2^eb is at least four times a bound on the sum of
-// the magnitudes of every contribution to the row (|A^K[i1][i2]| <= max|A0[i1][.][.]| *
-// sum|G_K|), so every partial sum stays below 2^62 units. An FP32 contribution is split
-// into three signed 21-bit digits on the grids 2^(eb-22), 2^(eb-43), 2^(eb-64) by adding
-// and subtracting the constants 1.5 * 2^(grid + 23) (each add rounds to the grid, each
-// subtraction is exact, and the digit is the difference of the float bit patterns): seven
-// FP32 additions and three integer subtractions, error <= u / 2. Rows whose bound lies
-// outside the range where those constants are normal floats, and FP64 contributions, take
-// an integer conversion (truncation, error < u). Integer addition is exact and
-// associative, so the result does not depend on the order of the additions; the final
-// value is rounded once to FP64 (round to nearest even). Absolute error per entry <=
-// (contributions) * u + half an ulp of the result: far below the rounding of the
-// contributions themselves.
+// Work layout inside a chunk. The plan stores each chunk's pairs grouped by local index
+// i1 (a "class"; within a class the pairs of different rows alternate) and, per pair,
+// the chunk-relative positions of its columns i2 = 0..n-1. A warp takes a unit of up to
+// a few dozen pairs of one class: the reference-tensor entries A0[i1][i2][.] its lanes
+// need stay in registers for the whole unit, each pair's G_K is a shared-memory
+// broadcast, and one warp instruction adds the contributions of one element-tensor row
+// (or of a few rows of different global rows), whose positions are distinct: the
+// shared-memory atomics meet no same-address conflicts and few bank conflicts. For n
+// >= 32 lane l takes column l of every pair (and the columns beyond 32 are spread over the
+// lanes); for n < 32 the unit's (pair, column) items are spread over the lanes in order.
+// The next chunk's plan data and geometry tensors are copied into a second shared-memory
+// buffer with cp.async while the current chunk is summed.
 //
-// The row plan (built once per dof map on the device) stores, for every row, the
-// (cell, local index) pairs that hold it and, for each such pair, the position of every
-// column dofmap[e][i2] inside the row (uint16, relative to the row start).
+// Exact accumulation. The sums are kept in fixed point with one unit per chunk:
+// u = 2^(eb - 62), where 2^(eb-1) bounds every partial sum of every entry of the chunk
+// (the largest |contribution| bound of a pair, a0max[i1] * sum|G_K|, times the largest
+// number of pairs of one row). A contribution x is split into three signed digits on the
+// grids 2^(eb-20), 2^(eb-41), 2^(eb-62), each found by adding and subtracting the FP32
+// constant 1.5 * 2^(grid + 23) (the addition rounds to the grid; the subtraction is
+// exact), and each digit is added with a 32-bit shared-memory atomic into its own array:
+// 32-bit shared atomics run about seven times faster than 64-bit ones on this GPU, and a
+// digit sum of up to 1023 contributions cannot overflow 32 bits. Chunks whose bound lies
+// outside the range of those FP32 constants, and FP64 contributions, take an integer
+// conversion instead (truncation, error < u). The value of an entry is
+// (S1 2^42 + S2 2^21 + S3) u, rounded once to FP64 (nearest even) in integer arithmetic.
+// Integer addition is exact and associative, so the result does not depend on the order
+// of the additions: per entry |result - exact sum of the contributions| <= m u + half an
+// ulp of the result (m contributions), and the matrix is reproducible bit for bit.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cfloat>
 #include <climits>
 #include <cstring>
 #include <string>
+#include <vector>
 
 #include "ffc_internal.h"
 #include "geometry.cuh"
+
+namespace ffc {
+namespace {
+
+constexpr int ROWS_VMAX = 4096;           // values of one chunk (shared-memory accumulators)
+constexpr int ROWS_PMAX = 320;            // pairs of one chunk
+constexpr int ROWS_MAX_INCIDENCE = 1023;  // digit sums of 21-bit digits stay within 32 bits
+constexpr int ROWS_MAX_LOCAL = 64;        // local dofs per cell the plan carries
+
+// A chunk's region of plan data (16-byte aligned, a multiple of 16 bytes):
+//   uint16 cls[n + 1]  first pair of each class i1 (chunk-relative), padded to 4 bytes
+//   int32  pr[P]       the pairs e * n + i1, grouped by class
+//   uint16 pos[P][n]   chunk-relative value index of column i2 of each pair
+__host__ __device__ constexpr int region_cls_bytes(int n) { return ((n + 1) * 2 + 3) / 4 * 4; }
+__host__ __device__ constexpr long long region_bytes(int n, long long P) {
+  return (region_cls_bytes(n) + 4 * P + 2 * P * n + 15) / 16 * 16;
+}
+
+}  // namespace
+}  // namespace ffc
 
 struct ffc_row_plan {
   int device = 0;
@@ -45,17 +79,25 @@ struct ffc_row_plan {
   int64_t nnz = 0;
   int max_row = 0;
   int max_incidence = 0;
-  int64_t* row_ptr = nullptr;  // [n_dof + 1] copy of the pattern's row offsets
-  int32_t* inc_ptr = nullptr;  // [n_dof + 1]
-  int32_t* inc = nullptr;      // [n_elem * n_local] (+16 bytes), entries e * n_local + i1
-  uint16_t* pos = nullptr;     // [n_elem * n_local * n_local] (+16 bytes)
-  void* geom = nullptr;        // per-cell geometry scratch, [n_elem][8] doubles
+  int vmax = 0;                     // values of the largest chunk
+  int max_pairs = 0;                // pairs of the largest chunk
+  int max_region = 0;               // bytes of the largest chunk region
+  int64_t n_chunks = 0;
+  int64_t region_total = 0;         // bytes of all regions
+  int64_t* row_ptr = nullptr;       // [n_dof + 1] copy of the pattern's row offsets
+  int32_t* chunk_row = nullptr;     // [n_chunks + 1] first row of each chunk
+  int32_t* chunk_pair = nullptr;    // [n_chunks + 1] first pair of each chunk (row order)
+  int64_t* chunk_off = nullptr;     // [n_chunks + 1] byte offset of each chunk's region
+  int64_t* chunk_val = nullptr;     // [n_chunks + 1] first CSR value of each chunk
+  int32_t* chunk_inc = nullptr;     // [n_chunks] most pairs of one row in the chunk
+  unsigned char* region = nullptr;  // [region_total] chunk regions (see region_bytes)
+  void* geom = nullptr;             // per-cell geometry scratch, [n_elem][12] doubles
 };
 
 namespace ffc {
 namespace {
 
-constexpr unsigned PLAN_BAD_DOF = 1u, PLAN_MISSING = 2u, PLAN_LONG_ROW = 4u, PLAN_BAD_ROW_PTR = 8u;
+constexpr unsigned PLAN_BAD_DOF = 1u, PLAN_MISSING = 2u, PLAN_BAD_ROW_PTR = 8u;
 
 int cuda_fail(cudaError_t e, const char* what) {
   set_error(std::string(what) + ": " + cudaGetErrorString(e));
@@ -150,6 +192,7 @@ __global__ void __launch_bounds__(SCAN_T) scan_add(int32_t* __restrict__ a, long
     if (base + j < n) a[base + j] += off;
 }
 
+// the pairs (e, i1) of each row, grouped by row (order within a row: arbitrary)
 __global__ void plan_fill(const int32_t* __restrict__ dofmap, long long total, long long n_dof,
                           const int32_t* __restrict__ inc_ptr, int32_t* __restrict__ fill,
                           int32_t* __restrict__ inc_tmp) {
@@ -162,97 +205,111 @@ __global__ void plan_fill(const int32_t* __restrict__ dofmap, long long total, l
   }
 }
 
-// A warp per row: orders the row's (cell, i1) pairs by e * n + i1 (they are distinct, so
-// each one's rank is the count of smaller ones), then finds the position of every
-// column dofmap[e][i2] in the row's sorted columns by binary search.
-__global__ void plan_rows(const int32_t* __restrict__ dofmap, int n, long long n_dof,
-                          const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col, long long nnz,
-                          const int32_t* __restrict__ inc_ptr, const int32_t* __restrict__ inc_tmp,
-                          int32_t* __restrict__ inc, uint16_t* __restrict__ pos, int* max_row, int* max_inc,
-                          unsigned* err) {
-  const int lane = threadIdx.x & 31;
-  const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
-  for (long long r = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; r < n_dof; r += warps) {
-    const int k0 = inc_ptr[r], c = inc_ptr[r + 1] - k0;
-    const long long rp0 = row_ptr[r], rp1 = row_ptr[r + 1];
-    if (rp0 < 0 || rp1 < rp0 || rp1 > nnz) {
-      if (lane == 0) atomicOr(err, PLAN_BAD_ROW_PTR);
-      continue;
-    }
-    const long long L = rp1 - rp0;
-    if (L > 65535) {
-      if (lane == 0) atomicOr(err, PLAN_LONG_ROW);
-      continue;
-    }
-    if (lane == 0) {
-      atomicMax(max_row, int(L));
-      atomicMax(max_inc, c);
-    }
-    for (int j = lane; j < c; j += 32) {
-      const int x = inc_tmp[k0 + j];
-      int rank = 0;
-      for (int m = 0; m < c; ++m) rank += inc_tmp[k0 + m] < x;
-      inc[k0 + rank] = x;
-    }
-    __syncwarp();
-    const long long items = (long long)c * n;
-    for (long long it = lane; it < items; it += 32) {
-      const int k = int(it / n), i2 = int(it - (long long)k * n);
-      const int e = inc[k0 + k] / n;
-      const int cj = dofmap[(long long)e * n + i2];
-      long long lo = rp0, hi = rp1;
-      while (lo < hi) {
-        const long long mid = (lo + hi) >> 1;
-        if (col[mid] < cj) lo = mid + 1;
-        else hi = mid;
+// One thread per chunk: the chunk's pairs grouped by class i1; within a class ordered by
+// (rank of the pair among the class's pairs of its row, row, cell), so consecutive pairs
+// of a class belong to different rows where the class has several. Writes the class
+// offsets and the ordered pairs into the chunk's region. `key` is scratch [total].
+__global__ void plan_sort(const int32_t* __restrict__ dofmap, const int32_t* __restrict__ chunk_row,
+                          const int32_t* __restrict__ chunk_pair, const int64_t* __restrict__ chunk_off,
+                          long long n_chunks, int n, const int32_t* __restrict__ inc_tmp,
+                          unsigned long long* __restrict__ key, unsigned char* __restrict__ region) {
+  constexpr unsigned long long E_MASK = (1ull << 30) - 1;
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n_chunks;
+       c += (long long)gridDim.x * blockDim.x) {
+    const int r0 = chunk_row[c];
+    const int p0 = chunk_pair[c], P = chunk_pair[c + 1] - p0;
+    unsigned char* reg = region + chunk_off[c];
+    uint16_t* cls = reinterpret_cast<uint16_t*>(reg);
+    int32_t* pr = reinterpret_cast<int32_t*>(reg + region_cls_bytes(n));
+    unsigned long long* kk = key + p0;
+    // key (i1, row - r0, e) of each pair (i1 < 64, row - r0 < 2^16, e < 2^30), by insertion
+    for (int j = 0; j < P; ++j) {
+      const int t = inc_tmp[p0 + j];
+      const unsigned long long kv = (static_cast<unsigned long long>(t % n) << 58) |
+                                    (static_cast<unsigned long long>(dofmap[t] - r0) << 30) |
+                                    static_cast<unsigned long long>(t / n);
+      int q = j;
+      while (q > 0 && kk[q - 1] > kv) {
+        kk[q] = kk[q - 1];
+        --q;
       }
-      uint16_t q = 0xFFFF;
-      if (lo < rp1 && col[lo] == cj) q = uint16_t(lo - rp0);
-      else atomicOr(err, PLAN_MISSING);
-      pos[(long long)k0 * n + it] = q;
+      kk[q] = kv;
     }
-    __syncwarp();
+    // class offsets
+    int cnt = 0;
+    for (int i = 0; i <= n; ++i) {
+      while (cnt < P && int(kk[cnt] >> 58) < i) ++cnt;
+      cls[i] = uint16_t(cnt);
+    }
+    // within each class: the pairs of a row get ranks 0, 1, ...; emit by (rank, row, e)
+    for (int i = 0; i < n; ++i) {
+      const int a = cls[i], b = cls[i + 1];
+      int out = a;
+      for (int rank = 0; out < b; ++rank) {
+        int rr = -1, run = 0;
+        for (int j = a; j < b; ++j) {
+          const int row = int((kk[j] >> 30) & 0xFFFFull);
+          run = (row == rr) ? run + 1 : 0;
+          rr = row;
+          if (run == rank) pr[out++] = int32_t((kk[j] & E_MASK) * n + i);
+        }
+      }
+    }
+  }
+}
+
+// One CTA per chunk: the chunk-relative position of every contribution (pair k, column
+// i2): binary search of column dofmap[e][i2] in the sorted columns of row dofmap[e][i1].
+__global__ void plan_positions(const int32_t* __restrict__ dofmap, int n, const int64_t* __restrict__ row_ptr,
+                               const int32_t* __restrict__ col, const int32_t* __restrict__ chunk_row,
+                               const int32_t* __restrict__ chunk_pair, const int64_t* __restrict__ chunk_off,
+                               long long n_chunks, unsigned char* __restrict__ region, unsigned* err) {
+  for (long long c = blockIdx.x; c < n_chunks; c += gridDim.x) {
+    const int r0 = chunk_row[c], r1 = chunk_row[c + 1];
+    const int P = chunk_pair[c + 1] - chunk_pair[c];
+    const long long base = row_ptr[r0];
+    unsigned char* reg = region + chunk_off[c];
+    const int32_t* pr = reinterpret_cast<const int32_t*>(reg + region_cls_bytes(n));
+    uint16_t* pos = reinterpret_cast<uint16_t*>(reg + region_cls_bytes(n) + 4ll * P);
+    for (int w = threadIdx.x; w < P * n; w += blockDim.x) {
+      const int k = w / n, i2 = w - k * n;
+      const int t = pr[k];
+      const int e = t / n, i1 = t - e * n;
+      const int r = dofmap[(long long)e * n + i1];
+      const int cj = dofmap[(long long)e * n + i2];
+      uint16_t q = 0;
+      if (r < r0 || r >= r1) {
+        atomicOr(err, PLAN_MISSING);
+      } else {
+        long long lo = row_ptr[r], hi = row_ptr[r + 1];
+        const long long end = hi;
+        while (lo < hi) {
+          const long long mid = (lo + hi) >> 1;
+          if (col[mid] < cj) lo = mid + 1;
+          else hi = mid;
+        }
+        if (lo < end && col[lo] == cj) q = uint16_t(lo - base);
+        else atomicOr(err, PLAN_MISSING);
+      }
+      pos[w] = q;
+    }
   }
 }
 
 // ---------------------------------------------------------------- fixed point
 
-// 2^eb >= 4 * bnd for a bound bnd >= 0 (denormal and zero bounds give the smallest eb)
-__device__ __forceinline__ int bound_exponent(float b) { return int((__float_as_uint(b) >> 23) & 0xffu) - 124; }
+// smallest eb with 2^(eb-1) >= b for a bound b >= 0 (zero and denormal bounds give the
+// smallest exponent of the type)
+__device__ __forceinline__ int bound_exponent(float b) { return int((__float_as_uint(b) >> 23) & 0xffu) - 125; }
 __device__ __forceinline__ int bound_exponent(double b) {
-  return int((static_cast<unsigned long long>(__double_as_longlong(b)) >> 52) & 0x7ffull) - 1020;
+  return int((static_cast<unsigned long long>(__double_as_longlong(b)) >> 52) & 0x7ffull) - 1021;
 }
 
 // 1.5 * 2^e as a float, for -126 <= e <= 127
 __device__ __forceinline__ float one_and_half_pow2(int e) { return __int_as_float(((e + 127) << 23) | (1 << 22)); }
 
-// x / 2^(eb - 64) for an FP32 x with |x| <= 2^(eb - 2), as three digits on the grids
-// 2^(eb-22), 2^(eb-43), 2^(eb-64), each found by rounding to the grid with an added
-// constant; valid for -85 <= eb <= 126, where the constants are normal floats.
-struct FixedSplit {
-  float c1, c2, c3;
-  int b1, b2, b3;
-  __device__ __forceinline__ void init(int eb) {
-    c1 = one_and_half_pow2(eb + 1);
-    c2 = one_and_half_pow2(eb - 20);
-    c3 = one_and_half_pow2(eb - 41);
-    b1 = __float_as_int(c1);
-    b2 = __float_as_int(c2);
-    b3 = __float_as_int(c3);
-  }
-  __device__ __forceinline__ long long operator()(float x) const {
-    const float t1 = __fadd_rn(x, c1);
-    const float r1 = __fsub_rn(x, __fsub_rn(t1, c1));
-    const float t2 = __fadd_rn(r1, c2);
-    const float r2 = __fsub_rn(r1, __fsub_rn(t2, c2));
-    const float t3 = __fadd_rn(r2, c3);
-    return static_cast<long long>(__float_as_int(t1) - b1) * (1ll << 42) +
-           static_cast<long long>(__float_as_int(t2) - b2) * (1ll << 21) + (__float_as_int(t3) - b3);
-  }
-};
-
-// x / 2^(eb - 62), truncated toward zero; |x| <= 2^eb keeps it below 2^62
-__device__ __forceinline__ long long to_fixed(float x, int eb) {
+// x / 2^ulog truncated toward zero, for |x| / 2^ulog < 2^62 (integer arithmetic only)
+__device__ __forceinline__ long long to_fixed(float x, int ulog) {
   const unsigned b = __float_as_uint(x);
   const int ex = int((b >> 23) & 0xffu);
   unsigned m = b & 0x7fffffu;
@@ -261,14 +318,14 @@ __device__ __forceinline__ long long to_fixed(float x, int eb) {
     m |= 0x800000u;
     ee = ex;
   }
-  const int sh = ee - 88 - eb;  // x = m 2^(ee - 150)
+  const int sh = ee - 150 - ulog;  // x = m 2^(ee - 150)
   unsigned long long f;
   if (sh >= 0) f = static_cast<unsigned long long>(m) << (sh < 63 ? sh : 63);
   else f = -sh < 32 ? static_cast<unsigned long long>(m >> -sh) : 0ull;
   return (b >> 31) ? -static_cast<long long>(f) : static_cast<long long>(f);
 }
 
-__device__ __forceinline__ long long to_fixed(double x, int eb) {
+__device__ __forceinline__ long long to_fixed(double x, int ulog) {
   const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
   const int ex = int((b >> 52) & 0x7ffull);
   unsigned long long m = b & 0xFFFFFFFFFFFFFull;
@@ -277,64 +334,148 @@ __device__ __forceinline__ long long to_fixed(double x, int eb) {
     m |= 1ull << 52;
     ee = ex;
   }
-  const int sh = ee - 1013 - eb;  // x = m 2^(ee - 1075)
+  const int sh = ee - 1075 - ulog;  // x = m 2^(ee - 1075)
   unsigned long long f;
   if (sh >= 0) f = m << (sh < 63 ? sh : 63);
   else f = -sh < 64 ? (m >> -sh) : 0ull;
   return (b >> 63) ? -static_cast<long long>(f) : static_cast<long long>(f);
 }
 
-// v * 2^(eb - 62) rounded to the nearest double (ties to even), in integer arithmetic (the
-// hardware int64 -> FP64 conversion runs on GB300's narrow FP64 pipe and was slower);
-// results outside the normal range (not reached by the bounds of FP32 values) use scalbn.
-__device__ __forceinline__ double fixed_to_double(long long v, int eb) {
-  if (v == 0) return 0.0;
+__device__ __noinline__ double scaled_to_double(long long v, int ulog) { return scalbn(static_cast<double>(v), ulog); }
+
+// v * 2^ulog rounded to the nearest double (ties to even), in integer arithmetic (the
+// hardware int64 -> FP64 conversion runs on GB300's narrow FP64 pipe): the magnitude is
+// normalised to a leading one at bit 63, its top 53 bits are added to (exponent - 1) << 52
+// (the leading one completes the exponent field, and a carry out of the significand on
+// rounding moves the value to the next binade by itself). Zero is a select; results
+// outside the normal range (bounds far from 1) take a called slow path, so the common
+// path never issues FP64 instructions.
+__device__ __forceinline__ double fixed_to_double(long long v, int ulog) {
   const unsigned long long sign = static_cast<unsigned long long>(v) & (1ull << 63);
-  unsigned long long m = v < 0 ? 0ull - static_cast<unsigned long long>(v) : static_cast<unsigned long long>(v);
+  unsigned long long m = sign ? 0ull - static_cast<unsigned long long>(v) : static_cast<unsigned long long>(v);
   const int lz = __clzll(static_cast<long long>(m));
-  m <<= lz;  // leading one at bit 63: value = 1.f * 2^(eb + 1 - lz)
-  int e = eb + 1 - lz + 1023;
-  unsigned long long mant = (m >> 11) & ((1ull << 52) - 1);
-  const unsigned rb = unsigned(m & 0x7ffull);
-  if (rb > 0x400u || (rb == 0x400u && (mant & 1ull))) {
-    if (++mant == (1ull << 52)) {
-      mant = 0;
-      ++e;
-    }
-  }
-  if (e <= 0 || e >= 2047) return scalbn(static_cast<double>(v), eb - 62);
-  return __longlong_as_double(static_cast<long long>(sign | (static_cast<unsigned long long>(e) << 52) | mant));
+  m <<= (lz & 63);
+  const int e = 63 - lz + ulog + 1023;
+  const unsigned long long sig = m >> 11, rb = m & 0x7ffull;
+  const unsigned long long up = (rb > 0x400ull) | ((rb == 0x400ull) & sig & 1ull);
+  unsigned long long bits = sign | ((static_cast<unsigned long long>(e - 1) << 52) + sig + up);
+  if (m == 0) bits = sign;
+  if (m != 0 && (e <= 0 || e >= 2047)) return scaled_to_double(v, ulog);
+  return __longlong_as_double(static_cast<long long>(bits));
 }
 
-// ---------------------------------------------------------------- geometry and rows
+// v * 2^ulog for |v| < 2^53, which a double holds exactly: the magnitude's leading one is
+// placed at bit 52 and (exponent - 1) << 52 added (the leading one completes the exponent
+// field); no rounding step. Zero is a select; results outside the normal range take the
+// called slow path.
+__device__ __forceinline__ double fixed_to_double_exact(long long v, int ulog) {
+  const unsigned long long sign = static_cast<unsigned long long>(v) & (1ull << 63);
+  unsigned long long m = sign ? 0ull - static_cast<unsigned long long>(v) : static_cast<unsigned long long>(v);
+  const int lz = __clzll(static_cast<long long>(m));  // >= 11
+  const int e = 63 - lz + ulog + 1023;
+  m <<= ((lz - 11) & 63);
+  unsigned long long bits = sign | ((static_cast<unsigned long long>(e - 1) << 52) + m);
+  if (m == 0) bits = sign;
+  if (m != 0 && (e <= 0 || e >= 2047)) return scaled_to_double(v, ulog);
+  return __longlong_as_double(static_cast<long long>(bits));
+}
+
+// The digits of one contribution for |x| <= 2^(eb-1): NDIG = 3 on the grids 2^(eb-20),
+// 2^(eb-41), 2^(eb-62) (unit u = 2^(eb-62)); NDIG = 2 on the first two (u = 2^(eb-41)).
+// `magic`: the FP32 rounding constants are normal floats (-87 <= eb <= 124); otherwise
+// the integer conversion.
+template <int NDIG>
+struct Digits {
+  float c1, c2, c3;
+  int b1, b2, b3, ulog;
+  bool magic;
+  __device__ __forceinline__ void init(int eb) {
+    magic = eb >= -87 && eb <= 124;
+    const int e = magic ? eb : 0;
+    c1 = one_and_half_pow2(e + 3);
+    c2 = one_and_half_pow2(e - 18);
+    c3 = one_and_half_pow2(e - 39);
+    b1 = __float_as_int(c1);
+    b2 = __float_as_int(c2);
+    b3 = __float_as_int(c3);
+    ulog = NDIG == 3 ? eb - 62 : eb - 41;
+  }
+  // MAGIC: the FP32 rounding constants (valid when `magic`); otherwise the integer conversion
+  template <bool MAGIC>
+  __device__ __forceinline__ void split(float x, int (&d)[NDIG]) const {
+    if constexpr (MAGIC) {
+      const float t1 = __fadd_rn(x, c1);
+      const float r1 = __fsub_rn(x, __fsub_rn(t1, c1));
+      const float t2 = __fadd_rn(r1, c2);
+      d[0] = __float_as_int(t1) - b1;
+      d[1] = __float_as_int(t2) - b2;
+      if constexpr (NDIG == 3) {
+        const float r2 = __fsub_rn(r1, __fsub_rn(t2, c2));
+        const float t3 = __fadd_rn(r2, c3);
+        d[2] = __float_as_int(t3) - b3;
+      }
+    } else {
+      split_int(to_fixed(x, ulog), d);
+    }
+  }
+  template <bool MAGIC>
+  __device__ __forceinline__ void split(double x, int (&d)[NDIG]) const {
+    split_int(to_fixed(x, ulog), d);
+  }
+  __device__ __forceinline__ static void split_int(long long f, int (&d)[NDIG]) {
+    if constexpr (NDIG == 3) {
+      d[2] = int(f & 0x1FFFFFll);
+      d[1] = int((f >> 21) & 0x1FFFFFll);
+      d[0] = int(f >> 42);
+    } else {
+      d[1] = int(f & 0x1FFFFFll);
+      d[0] = int(f >> 21);
+    }
+  }
+  // the 2-digit value v * 2^ulog through the FP64 pipe's int64 -> double conversion (exact:
+  // |v| < 2^53) and an exponent add for 2^ulog; for chunks whose results stay normal
+  // (fp64_ok), so the other lanes' integer conversions and this one use different pipes
+  __device__ __forceinline__ bool fp64_ok() const { return ulog >= -1022 && ulog <= 980; }
+  __device__ __forceinline__ double value_fp64(const int (&s)[NDIG]) const {
+    static_assert(NDIG == 2, "FP64-pipe conversion of the 42-bit sums");
+    const long long v = static_cast<long long>(s[0]) * (1ll << 21) + s[1];
+    const long long bits = __double_as_longlong(static_cast<double>(v)) + (static_cast<long long>(ulog) << 52);
+    return __longlong_as_double(v == 0 ? 0ll : bits);
+  }
+  // the entry's value from its digit sums, rounded once to FP64
+  __device__ __forceinline__ double value(const int (&s)[NDIG]) const {
+    if constexpr (NDIG == 3) {
+      const long long v = static_cast<long long>(s[0]) * (1ll << 42) + static_cast<long long>(s[1]) * (1ll << 21) + s[2];
+      return fixed_to_double(v, ulog);
+    } else {  // |v| < 2^52: exact in a double
+      return fixed_to_double_exact(static_cast<long long>(s[0]) * (1ll << 21) + s[1], ulog);
+    }
+  }
+};
+
+// ---------------------------------------------------------------- geometry
+
+// Form codes of the row kernels: FFC_MASS, FFC_POISSON, or the (mass, Poisson) pair.
+constexpr int ROWS_PAIR = FFC_PAIR_MASS_POISSON;
 
 template <int D, int FORM>
 struct RowsGeo {
-  static constexpr int NAK = FORM == FFC_POISSON ? D * (D + 1) / 2 : 1;  // G_K entries (symmetric Poisson G)
-  static constexpr int GS = FORM == FFC_POISSON ? (D == 3 ? 8 : 4) : 2;   // stored per cell: G, sum|G|, pad
+  static constexpr int NF = FORM == ROWS_PAIR ? 2 : 1;        // matrices
+  static constexpr int NP = D * (D + 1) / 2;                  // symmetric Poisson G_K entries
+  static constexpr int NAK = FORM == FFC_POISSON ? NP : 1;    // G entries of a single form
+  // stored per cell: mass [|det|, |det|]; Poisson [G (NP), sum|G|, pad to 8];
+  // pair [|det|, G (NP), pad, sum|G| in slot 7]
+  static constexpr int GS = FORM == FFC_MASS ? 2 : 8;
+  // G_K slots of the contribution bounds' sums: |G| of a single form, and for the pair the
+  // mass's |det J| (slot 0) and the Poisson sum|G| (slot 7)
+  static constexpr int SUM_A = FORM == ROWS_PAIR ? 0 : (FORM == FFC_POISSON ? NP : 1);
+  static constexpr int SUM_B = 7;
 };
 
-template <typename T, int GS>
-__device__ __forceinline__ void load_g(const T* __restrict__ src, T (&g)[GS]) {
-  constexpr int BYTES = GS * int(sizeof(T));
-  if constexpr (BYTES % 16 == 0) {
-#pragma unroll
-    for (int j = 0; j < BYTES / 16; ++j) {
-      const float4 v = __ldg(reinterpret_cast<const float4*>(src) + j);
-      memcpy(reinterpret_cast<char*>(g) + 16 * j, &v, 16);
-    }
-  } else {
-#pragma unroll
-    for (int j = 0; j < BYTES / 8; ++j) {
-      const float2 v = __ldg(reinterpret_cast<const float2*>(src) + j);
-      memcpy(reinterpret_cast<char*>(g) + 8 * j, &v, 8);
-    }
-  }
-}
-
-// One thread per cell: G_K exactly as the CUDA-core element-tensor kernels form it (FP32:
-// FP64 adjugate and determinant, K and G in FP32; FP64: everything in FP64), followed by
-// sum|G_K| for the row bounds.
+// One thread per cell: G_K exactly as the fused CUDA-core element-tensor kernels form it
+// (FP32: mass |det J| from the FP64 determinant; Poisson the FP64 adjugate and
+// determinant, K and the symmetric G in FP32; FP64: everything in FP64), and the sums
+// of |G_K| for the bounds.
 template <int D, int FORM, typename T>
 __global__ void __launch_bounds__(256) rows_geometry(const int32_t* __restrict__ cells,
                                                      const double* __restrict__ vertices, long long n_vert,
@@ -345,24 +486,32 @@ __global__ void __launch_bounds__(256) rows_geometry(const int32_t* __restrict__
     T g[C::GS];
 #pragma unroll
     for (int a = 0; a < C::GS; ++a) g[a] = T(0);
-    bool degenerate, bad_index;
-    if constexpr (FORM == FFC_MASS) {
+    bool degenerate = false, bad_index = false;
+    if constexpr (FORM == FFC_MASS || FORM == ROWS_PAIR) {
       double det;
       cell_det<D>(cells, vertices, n_vert, e, det, degenerate, bad_index);
       g[0] = T(det);
-    } else if constexpr (sizeof(T) == 4) {
-      float K[D][D], det;
-      cell_geometry_f32<D>(cells, vertices, n_vert, e, K, det, degenerate, bad_index);
-      geometry_tensor_f32<D, FORM, 1, true>(K, det, nullptr, 0.0, 0.0, reinterpret_cast<float*>(g));
-    } else {
-      double K[D][D], det;
-      cell_geometry<D>(cells, vertices, n_vert, e, K, det, degenerate, bad_index);
-      geometry_tensor_k<D, FORM, 1>(K, det, nullptr, 0.0, 0.0, [&](int a, double v) { g[a] = T(v); });
+      if constexpr (FORM == FFC_MASS) g[1] = fabs(g[0]);
     }
-    T s = T(0);
+    if constexpr (FORM == FFC_POISSON || FORM == ROWS_PAIR) {
+      constexpr int o = FORM == ROWS_PAIR ? 1 : 0;
+      bool dg, bi;
+      if constexpr (sizeof(T) == 4) {
+        float K[D][D], det;
+        cell_geometry_f32<D>(cells, vertices, n_vert, e, K, det, dg, bi);
+        geometry_tensor_f32<D, FFC_POISSON, 1, true>(K, det, nullptr, 0.0, 0.0, reinterpret_cast<float*>(g) + o);
+      } else {
+        double K[D][D], det;
+        cell_geometry<D>(cells, vertices, n_vert, e, K, det, dg, bi);
+        geometry_tensor_k<D, FFC_POISSON, 1>(K, det, nullptr, 0.0, 0.0, [&](int a, double v) { g[o + a] = T(v); });
+      }
+      T s = T(0);
 #pragma unroll
-    for (int a = 0; a < C::NAK; ++a) s += fabs(g[a]);
-    g[C::NAK] = s;
+      for (int a = 0; a < C::NP; ++a) s += fabs(g[o + a]);
+      g[FORM == ROWS_PAIR ? C::SUM_B : C::NP] = s;
+      degenerate |= dg;
+      bad_index |= bi;
+    }
     T* dst = G + e * C::GS;
 #pragma unroll
     for (int a = 0; a < C::GS; ++a) dst[a] = g[a];
@@ -371,246 +520,515 @@ __global__ void __launch_bounds__(256) rows_geometry(const int32_t* __restrict__
   }
 }
 
-struct RowsParams {
-  const int64_t* row_ptr;
-  const int32_t* inc_ptr;
-  const int32_t* inc;
-  const uint16_t* pos;
-  const void* G;
-  const void* a0;  // [N*N][NAK] in T
-  double* csr_val;
-  long long n_dof;
-  int lmax;        // accumulator entries per warp (longest row)
-  int max_inc;     // most incidences of one row
-  int warp_bytes;  // shared memory of one warp
-  unsigned* status;
-};
-
-template <int D, int FORM, int Q, typename T>
-struct RowsCfg {
-  static constexpr int N = nscalar(D, Q);
-  static constexpr int NAK = RowsGeo<D, FORM>::NAK;
-  static constexpr int GS = RowsGeo<D, FORM>::GS;
-  static constexpr size_t A0_BYTES = (size_t(N) * N * NAK * sizeof(T) + size_t(N) * sizeof(T) + 15) / 16 * 16;
-};
-
-// Per-warp shared memory: the row accumulator, two staging buffers for the positions and
-// two for the incidences of a row (filled by cp.async, 16-byte chunks from an aligned-down
-// start, hence the 32 bytes of slack), and the G_K of the row's cells.
-struct WarpLayout {
-  int acc, pos, inc, g, bytes;  // offsets of acc, pos[0], inc[0], g; pos[1] = pos + pb, inc[1] = inc + ib
-  int pb, ib;
-  __host__ __device__ WarpLayout(int lmax, int max_inc, int n, int g_bytes) {
-    pb = (max_inc * n * 2 + 32 + 15) / 16 * 16;
-    ib = (max_inc * 4 + 32 + 15) / 16 * 16;
-    acc = 0;
-    pos = (lmax * 8 + 15) / 16 * 16;
-    inc = pos + 2 * pb;
-    g = inc + 2 * ib;
-    bytes = g + (max_inc * g_bytes + 15) / 16 * 16;
-  }
-};
+// ---------------------------------------------------------------- assembly
 
 __device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc) {
   const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(smem_dst));
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gsrc) : "memory");
 }
+__device__ __forceinline__ void cp_async8(void* smem_dst, const void* gsrc) {
+  const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(smem_dst));
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(gsrc) : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int PENDING>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(PENDING) : "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
-// Copies bytes [b0, b1) of `src` (a 16-byte aligned array padded by 16 bytes) into `dst` as
-// 16-byte chunks starting at b0 rounded down to 16; the data of b0 lands at dst + (b0 & 15).
-__device__ __forceinline__ void stage_range(unsigned char* dst, const unsigned char* src, long long b0, long long b1,
-                                            int lane) {
-  const long long a0 = b0 & ~15ll;
-  const int chunks = int((b1 - a0 + 15) >> 4);
-  for (int j = lane; j < chunks; j += 32) cp_async16(dst + 16 * j, src + a0 + 16 * j);
+struct RowsParams {
+  const int64_t* chunk_off;
+  const int32_t* chunk_pair;
+  const int64_t* chunk_val;
+  const int32_t* chunk_inc;
+  const unsigned char* region;
+  const void* G;
+  const void* a0a;  // mass or single-form reference tensor [N][NAK][N] in T
+  const void* a0b;  // pair: the Poisson reference tensor [N][NP][N]
+  double* out_a;
+  double* out_b;
+  long long n_chunks;
+  int meta_off;  // byte offset of the chunk-extent ring in shared memory
+  int pmax;   // pairs of the largest chunk
+  int rmax;   // bytes of the largest chunk region
+  unsigned* status;
+};
+
+__host__ __device__ constexpr int gcd_c(int a, int b) { return b == 0 ? a : gcd_c(b, a % b); }
+
+template <int D, int FORM, int Q>
+struct RowsCfg {
+  static constexpr int N = nscalar(D, Q);
+  static constexpr bool MAIN = N >= 32;              // lane l takes column l of every pair
+  static constexpr int W = MAIN ? N - 32 : N;        // columns spread over the lanes in order
+  static constexpr int I0 = MAIN ? 32 : 0;           // first of those columns
+  static constexpr int PER = W > 0 ? W / gcd_c(32, W) : 1;  // steps after which a lane's column repeats
+  static constexpr int UMAX = N <= 6 ? 32 : 16;      // pairs of one work unit
+  static constexpr int NP = D * (D + 1) / 2;
+  static constexpr int NA = FORM == ROWS_PAIR ? 1 + NP : (FORM == FFC_POISSON ? NP : 1);  // A0 values per entry
+  static constexpr int NG = FORM == FFC_MASS ? 1 : 8;  // G_K values read per pair (vector loads)
+  static constexpr int TB = 256;        // items of one task of the columns beyond the first 32
+  static constexpr int WB = 256;        // values of one write-out task
+};
+
+// A0 entry (i1, i2) of the kernel's form(s), in the order the contraction uses, from the
+// [i1][alpha][i2] copies (lanes of consecutive i2 read consecutive words)
+template <int FORM, int N, int NA, int NP, typename T>
+__device__ __forceinline__ void load_a0(const T* __restrict__ A0a, const T* __restrict__ A0b, int i1, int i2,
+                                        T (&a)[NA]) {
+  if constexpr (FORM == ROWS_PAIR) {
+    a[0] = __ldg(A0a + i1 * N + i2);
+#pragma unroll
+    for (int j = 0; j < NP; ++j) a[1 + j] = __ldg(A0b + (i1 * NP + j) * N + i2);
+  } else {
+#pragma unroll
+    for (int j = 0; j < NA; ++j) a[j] = __ldg(A0a + (i1 * NA + j) * N + i2);
+  }
 }
 
-// A warp per global row (grid-stride over rows), software-pipelined: while row r is
-// summed, cp.async stages the positions and incidences of the warp's next row, and the
-// row offsets of the one after are loaded. Per row: G_K of the row's cells (one gather
-// from L2) with the bound, fixed-point accumulation of the contributions in the warp's
-// shared-memory row (shared 64-bit atomics: contributions of different cells may hit one
-// entry), one rounding per entry and a coalesced streaming store.
+// the first NG values of a pair's G_K from shared memory (16-byte aligned rows for NG = 8)
+template <int NG, typename T>
+__device__ __forceinline__ void load_gk(const T* gs, T (&g)[NG]) {
+  if constexpr (NG == 1) {
+    g[0] = gs[0];
+  } else if constexpr (sizeof(T) == 4) {
+    const float4 x = reinterpret_cast<const float4*>(gs)[0], y = reinterpret_cast<const float4*>(gs)[1];
+    g[0] = x.x, g[1] = x.y, g[2] = x.z, g[3] = x.w, g[4] = y.x, g[5] = y.y, g[6] = y.z, g[7] = y.w;
+  } else {
+#pragma unroll
+    for (int j = 0; j < NG / 2; ++j) {
+      const double2 x = reinterpret_cast<const double2*>(gs)[j];
+      g[2 * j] = x.x;
+      g[2 * j + 1] = x.y;
+    }
+  }
+}
+
+// the contributions of one element-tensor entry: sum_alpha G_K[alpha] A0[i1][i2][alpha]
+// (FMA order as in the fused element-tensor kernels, so FP32 values agree bit for bit)
+template <int FORM, int NA, int NG, int NF, typename T>
+__device__ __forceinline__ void contract(const T (&g)[NG], const T (&a)[NA], T (&v)[NF]) {
+  if constexpr (FORM == ROWS_PAIR) {
+    v[0] = fma(g[0], a[0], T(0));
+    T s = T(0);
+#pragma unroll
+    for (int j = 1; j < NA; ++j) s = fma(g[j], a[j], s);
+    v[1] = s;
+  } else {
+    T s = T(0);
+#pragma unroll
+    for (int j = 0; j < NA; ++j) s = fma(g[j], a[j], s);
+    v[0] = s;
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_max(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// Adds one entry's contributions (digits) at chunk position q; acc is [NF][NDIG][ROWS_VMAX].
+template <bool MAGIC, int NF, int NDIG, typename T>
+__device__ __forceinline__ void add_digits(int* acc, const Digits<NDIG> (&dig)[NF], const T (&v)[NF], int q) {
+#pragma unroll
+  for (int f = 0; f < NF; ++f) {
+    int d[NDIG];
+    dig[f].template split<MAGIC>(v[f], d);
+    int* a = acc + f * NDIG * ROWS_VMAX + q;
+#pragma unroll
+    for (int j = 0; j < NDIG; ++j) atomicAdd(a + j * ROWS_VMAX, d[j]);
+  }
+}
+
+// One work unit (class i1, pairs [k0, k1)) of a chunk, by one warp: for n >= 32 lane l takes
+// column l of every pair (the A0 column in registers), for n < 32 the unit's (pair, column)
+// items in order. Returns true if a position was out of range.
+template <class K, int FORM, int NF, int GS, bool MAGIC, int NDIG, typename T>
+__device__ __forceinline__ bool unit_task(unsigned ud, const T* gs, const uint16_t* pos, int* acc,
+                                          const Digits<NDIG> (&dig)[NF], const T* A0a, const T* A0b, int V) {
+  constexpr int N = K::N, NA = K::NA, NG = K::NG;
+  const int lane = threadIdx.x & 31;
+  const int i1 = int(ud & 127u), k0 = int((ud >> 7) & 4095u), k1 = int(ud >> 19);
+  bool bad = false;
+  if constexpr (K::MAIN) {
+    T am[NA];
+    load_a0<FORM, N, NA, K::NP, T>(A0a, A0b, i1, lane, am);
+    const uint16_t* pl = pos + lane;
+#pragma unroll 2
+    for (int k = k0; k < k1; ++k) {
+      T g[NG];
+      load_gk<NG, T>(gs + k * GS, g);
+      const int q = pl[k * N];
+      T v[NF];
+      contract<FORM, NA, NG, NF, T>(g, am, v);
+      bad |= q >= V;
+      add_digits<MAGIC, NF, NDIG, T>(acc, dig, v, q < V ? q : 0);
+    }
+  } else {
+    T af[K::PER][NA];
+#pragma unroll
+    for (int s = 0; s < K::PER; ++s) load_a0<FORM, N, NA, K::NP, T>(A0a, A0b, i1, (lane + 32 * s) % K::W, af[s]);
+    const int total = (k1 - k0) * K::W;
+    for (int f0 = 0; f0 < total; f0 += 32 * K::PER) {
+#pragma unroll
+      for (int s = 0; s < K::PER; ++s) {
+        const int f = f0 + 32 * s + lane;
+        if (f < total) {
+          const int kk = k0 + f / K::W;
+          const int i2 = K::I0 + f % K::W;
+          T g[NG];
+          load_gk<NG, T>(gs + kk * GS, g);
+          const int q = pos[kk * N + i2];
+          T v[NF];
+          contract<FORM, NA, NG, NF, T>(g, af[s], v);
+          bad |= q >= V;
+          add_digits<MAGIC, NF, NDIG, T>(acc, dig, v, q < V ? q : 0);
+        }
+      }
+    }
+  }
+  return bad;
+}
+
+// Items [b * TB, (b + 1) * TB) of the columns beyond the first 32 (n > 32), packed over
+// the lanes: item f is pair f / W, column 32 + f % W.
+template <class K, int FORM, int NF, int GS, bool MAGIC, int NDIG, typename T>
+__device__ __forceinline__ bool tail_task(int b, int P, const int32_t* pr, const T* gs, const uint16_t* pos, int* acc,
+                                          const Digits<NDIG> (&dig)[NF], const T* A0a, const T* A0b, int V) {
+  constexpr int N = K::N, NA = K::NA, NG = K::NG;
+  bool bad = false;
+  if constexpr (K::MAIN && K::W > 0) {
+    const int total = P * K::W, end = min(total, (b + 1) * K::TB);
+    for (int f = b * K::TB + (threadIdx.x & 31); f < end; f += 32) {
+      const int k = f / K::W, i2 = 32 + f % K::W;
+      const int i1 = pr[k] % N;
+      T a[NA], g[NG];
+      load_a0<FORM, N, NA, K::NP, T>(A0a, A0b, i1, i2, a);
+      load_gk<NG, T>(gs + k * GS, g);
+      const int q = pos[k * N + i2];
+      T v[NF];
+      contract<FORM, NA, NG, NF, T>(g, a, v);
+      bad |= q >= V;
+      add_digits<MAGIC, NF, NDIG, T>(acc, dig, v, q < V ? q : 0);
+    }
+  }
+  return bad;
+}
+
+// Per-chunk state prepared one iteration ahead (three slots, by chunk index mod 3).
+struct RowsSlot {
+  int eb[2];      // fixed-point exponent of each form
+  int finite[2];  // the form's bound is finite
+  int n_units;
+};
+
+// The chunks of this CTA are c_i = blockIdx.x + i * gridDim.x. Iteration i is one queue of
+// independent warp tasks, handed out by a shared counter: four staging tasks (chunk i + 3's
+// plan region, chunk i + 2's geometry gather, chunk i + 5's extents, chunk i + 1's bounds
+// and work units), then the work units of chunk i (into accumulator buffer i % 2)
+// interleaved with the write-out blocks of chunk i - 1 (from the other buffer, which they
+// clear). Copies go through cp.async and are complete at the iteration's end, where one
+// CTA-wide barrier closes the iteration. Staging depths: regions 4 buffers (i .. i + 3),
+// geometry 3 (i .. i + 2), extents a ring of 8.
+// One CTA per SM: 32 warps for FP32 (64 registers a thread), 16 for FP64.
 template <int D, int FORM, int Q, typename T>
-__global__ void __launch_bounds__(512, 1) rows_assemble(RowsParams p) {
-  using C = RowsCfg<D, FORM, Q, T>;
-  constexpr int N = C::N, NAK = C::NAK, GS = C::GS;
+__global__ void __launch_bounds__(sizeof(T) == 4 ? 1024 : 512, 1) rows_assemble(RowsParams p) {
+  using C = RowsGeo<D, FORM>;
+  using K = RowsCfg<D, FORM, Q>;
+  constexpr int N = K::N, NF = C::NF, GS = C::GS, TH = sizeof(T) == 4 ? 1024 : 512;
+  constexpr int NDIG = sizeof(T) == 4 ? 2 : 3;  // digits: 42-bit fixed point for FP32, 63-bit for FP64
+  constexpr int CB = region_cls_bytes(N);
+  constexpr int ACC = NF * NDIG * ROWS_VMAX;    // ints of one accumulator buffer
+  constexpr int NSPECIAL = 4;
   extern __shared__ __align__(16) unsigned char smem[];
-  T* a0s = reinterpret_cast<T*>(smem);  // [N*N][NAK]
-  T* a0max = a0s + N * N * NAK;         // [N]: max |A0[i1][.][.]|
-  const T* A0 = static_cast<const T*>(p.a0);
-  for (int k = threadIdx.x; k < N * N * NAK; k += blockDim.x) a0s[k] = A0[k];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const WarpLayout lay(p.lmax, p.max_inc, N, GS * int(sizeof(T)));
-  unsigned char* wbase = smem + C::A0_BYTES + size_t(w) * p.warp_bytes;
-  unsigned long long* acc = reinterpret_cast<unsigned long long*>(wbase + lay.acc);
-  T* gbuf = reinterpret_cast<T*>(wbase + lay.g);
-  for (int j = lane; j < p.lmax; j += 32) acc[j] = 0ull;
-  __syncthreads();
-  for (int i1 = threadIdx.x; i1 < N; i1 += blockDim.x) {
+  int* acc = reinterpret_cast<int*>(smem);                                   // [2][NF][NDIG][ROWS_VMAX]
+  unsigned char* rbuf = smem + size_t(2) * ACC * 4;                          // [4][rmax] plan regions
+  T* gbuf = reinterpret_cast<T*>(rbuf + 4 * size_t(p.rmax));                 // [3][pmax][GS]
+  T* a0max = gbuf + 3 * size_t(p.pmax) * GS;                                 // [NF][N]
+  unsigned* units = reinterpret_cast<unsigned*>(a0max + NF * N);             // [3][ROWS_PMAX]
+  RowsSlot* slot = reinterpret_cast<RowsSlot*>(units + 3 * ROWS_PMAX);       // [3]
+  int* tq = reinterpret_cast<int*>(slot + 3);                                // [2] task counters
+  long long* meta = reinterpret_cast<long long*>(smem + p.meta_off);          // [8][8]: chunk extents
+  const T* A0a = static_cast<const T*>(p.a0a);
+  const T* A0b = static_cast<const T*>(p.a0b);
+  const T* Gall = static_cast<const T*>(p.G);
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  const T big = sizeof(T) == 4 ? T(FLT_MAX) : T(DBL_MAX);
+  const long long G1 = gridDim.x;
+  const long long n_iter = blockIdx.x < p.n_chunks ? (p.n_chunks - blockIdx.x + G1 - 1) / G1 : 0;
+  // largest |A0| entry of each reference-tensor row i1 (the contribution bound's factor)
+  for (int i = t; i < NF * N; i += TH) {
+    const int f = i / N, i1 = i - f * N;
+    const int na = (FORM == ROWS_PAIR && f == 1) ? C::NP : C::NAK;
+    const T* A = (FORM == ROWS_PAIR && f == 1) ? A0b : A0a;
     T m = T(0);
-    for (int k = 0; k < N * NAK; ++k) m = fmax(m, fabs(a0s[i1 * N * NAK + k]));
-    a0max[i1] = m;
+    for (int k = 0; k < N * na; ++k) m = fmax(m, fabs(A[size_t(i1) * N * na + k]));
+    a0max[i] = m;
   }
+  for (int i = 4 * t; i < 2 * ACC; i += 4 * TH) *reinterpret_cast<int4*>(acc + i) = make_int4(0, 0, 0, 0);
+  if (t < 2) tq[t] = 0;
+  // extents of the chunk of iteration i, ring slot i % 8: pairs [0] .. [1), region bytes
+  // [2] .. [3), CSR values [4] .. [5), most pairs of a row [6]
+  auto meta_at = [&](long long i) { return meta + (i & 7) * 8; };
+  auto meta_task = [&](long long i) {  // one warp
+    const long long c = blockIdx.x + i * G1;
+    if (i < n_iter && lane < 7) {
+      long long v;
+      if (lane < 2) v = p.chunk_pair[c + lane];
+      else if (lane < 4) v = p.chunk_off[c + lane - 2];
+      else if (lane < 6) v = p.chunk_val[c + lane - 4];
+      else v = p.chunk_inc[c];
+      meta_at(i)[lane] = v;
+    }
+  };
+  auto region_at = [&](long long i) { return rbuf + size_t(i & 3) * p.rmax; };
+  // the plan region of chunk i (a multiple of 16 bytes, at most rmax) into buffer i % 4
+  auto region_task = [&](long long i) {  // one warp
+    const long long* m = meta_at(i);
+    const unsigned char* src = p.region + m[2];
+    unsigned char* dst = region_at(i);
+    const int nb = int(m[3] - m[2]);
+    for (int o = 16 * lane; o < nb; o += 512) cp_async16(dst + o, src + o);
+  };
+  // gather of the pairs' geometry tensors of chunk i into buffer i % 3 (one warp; the
+  // chunk's region is staged)
+  auto geometry_task = [&](long long i) {
+    const long long* m = meta_at(i);
+    const int P = int(m[1] - m[0]);
+    const int32_t* pr = reinterpret_cast<const int32_t*>(region_at(i) + CB);
+    T* gs = gbuf + size_t(i % 3) * p.pmax * GS;
+    for (int k = lane; k < P; k += 32) {
+      const T* src = Gall + (long long)(pr[k] / N) * GS;
+      if constexpr (GS * sizeof(T) == 8) {
+        cp_async8(gs + k * GS, src);
+      } else {
+#pragma unroll
+        for (int x = 0; x < int(GS * sizeof(T)) / 16; ++x)
+          cp_async16(reinterpret_cast<unsigned char*>(gs + k * GS) + 16 * x,
+                     reinterpret_cast<const unsigned char*>(src) + 16 * x);
+      }
+    }
+  };
+  // bounds (largest pair bound times the most pairs of a row) and work units of chunk i
+  auto prepare_task = [&](long long i) {  // one warp
+    const long long* m = meta_at(i);
+    const int P = int(m[1] - m[0]);
+    const unsigned char* reg = region_at(i);
+    const uint16_t* cls = reinterpret_cast<const uint16_t*>(reg);
+    const int32_t* pr = reinterpret_cast<const int32_t*>(reg + CB);
+    const T* gs = gbuf + size_t(i % 3) * p.pmax * GS;
+    RowsSlot& sl = slot[i % 3];
+    T pb[NF];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) pb[f] = T(0);
+    for (int k = lane; k < P; k += 32) {
+      const int i1 = pr[k] % N;
+#pragma unroll
+      for (int f = 0; f < NF; ++f) {
+        const T x = a0max[f * N + i1] * fabs(gs[k * GS + (f == 0 ? C::SUM_A : C::SUM_B)]);
+        pb[f] = fmax(pb[f], x == x ? x : big * T(2));  // NaN -> inf
+      }
+    }
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+      const T bnd = warp_max(pb[f]) * T(m[6]);
+      if (lane == 0) {
+        sl.finite[f] = bnd <= big;
+        sl.eb[f] = bnd <= big ? bound_exponent(bnd) : 0;
+      }
+    }
+    // work units: pieces of at most UMAX pairs of one class (lane: classes lane, lane + 32)
+    int cnt[2], first[2], n_u = 0;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int ii = lane + 32 * h;
+      first[h] = ii < N ? int(cls[ii]) : 0;
+      const int mm = ii < N ? int(cls[ii + 1]) - first[h] : 0;
+      cnt[h] = (mm + K::UMAX - 1) / K::UMAX;
+      n_u += cnt[h];
+    }
+    int incl = n_u;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    int u = incl - n_u;
+    unsigned* un = units + (i % 3) * ROWS_PMAX;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int ii = lane + 32 * h;
+      if (ii < N) {
+        const int end = int(cls[ii + 1]);
+        for (int j = 0; j < cnt[h]; ++j, ++u) {
+          const int k0 = first[h] + j * K::UMAX;
+          un[u] = unsigned(ii) | (unsigned(k0) << 7) | (unsigned(min(k0 + K::UMAX, end)) << 19);
+        }
+      }
+    }
+    if (lane == 31) sl.n_units = incl;
+  };
+  // values [b * WB, (b + 1) * WB) of chunk i from accumulator buffer i % 2 (cleared), one
+  // warp; lanes take consecutive pairs of values (16-byte stores) from the first 16-byte
+  // boundary, the value before it goes with block 0
+  auto write_task = [&](long long i, int b) {
+    const long long* m = meta_at(i);
+    const long long v0 = m[4];
+    const int V = int(m[5] - v0);
+    const RowsSlot& sl = slot[i % 3];
+    int* ab = acc + (i & 1) * ACC;
+    const double nan = __longlong_as_double(0x7ff8000000000000ll);
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+      Digits<NDIG> dg;
+      dg.init(sl.eb[f]);
+      const bool fin = sl.finite[f] != 0;
+      double* out = (f == 0 ? p.out_a : p.out_b) + v0;
+      int* a = ab + f * NDIG * ROWS_VMAX;
+      // the second value of each pair goes through the FP64 pipe where that is exact
+      const bool split_pipes = NDIG == 2 && fin && dg.fp64_ok();
+      auto value = [&](int j, bool fp64) {
+        int sd[NDIG];
+#pragma unroll
+        for (int d = 0; d < NDIG; ++d) {
+          sd[d] = a[j + d * ROWS_VMAX];
+          a[j + d * ROWS_VMAX] = 0;
+        }
+        if constexpr (NDIG == 2)
+          if (fp64 && split_pipes) return dg.value_fp64(sd);
+        return fin ? dg.value(sd) : nan;
+      };
+      const int j0 = int((reinterpret_cast<uintptr_t>(out) >> 3) & 1);
+      if (b == 0 && lane == 0 && j0 == 1 && V > 0) __stcs(out, value(0, false));
+      const int end = min(V, j0 + (b + 1) * K::WB);
+#pragma unroll 2
+      for (int j = j0 + b * K::WB + 2 * lane; j < end; j += 64) {
+        const double x = value(j, false);
+        if (j + 1 < end) {
+          const double y = value(j + 1, true);
+          __stcs(reinterpret_cast<double2*>(out + j), make_double2(x, y));
+        } else {
+          __stcs(out + j, x);
+        }
+      }
+    }
+  };
+  // ---- prologue: extents of iterations 0..4; regions of chunks 0..2; geometry of chunks
+  // 0..1; chunk 0 prepared
+  if (w < 5) meta_task(w);
   __syncthreads();
-  const T* G = static_cast<const T*>(p.G);
-  const unsigned char* pos_bytes = reinterpret_cast<const unsigned char*>(p.pos);
-  const unsigned char* inc_bytes = reinterpret_cast<const unsigned char*>(p.inc);
-  const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
-  long long r = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
-  // row offsets of this row and the next: (base, end, k0, k1)
-  long long m_base = 0, m_end = 0, n_base = 0, n_end = 0;
-  int m_k0 = 0, m_k1 = 0, n_k0 = 0, n_k1 = 0;
-  if (r < p.n_dof) {
-    m_base = p.row_ptr[r];
-    m_end = p.row_ptr[r + 1];
-    m_k0 = p.inc_ptr[r];
-    m_k1 = p.inc_ptr[r + 1];
-    stage_range(wbase + lay.pos, pos_bytes, 2ll * m_k0 * N, 2ll * m_k1 * N, lane);
-    stage_range(wbase + lay.inc, inc_bytes, 4ll * m_k0, 4ll * m_k1, lane);
-  }
+  if (w < 3 && w < n_iter) region_task(w);
   cp_async_commit();
-  if (r + warps < p.n_dof) {
-    n_base = p.row_ptr[r + warps];
-    n_end = p.row_ptr[r + warps + 1];
-    n_k0 = p.inc_ptr[r + warps];
-    n_k1 = p.inc_ptr[r + warps + 1];
-  }
-  int buf = 0;
-  for (; r < p.n_dof; r += warps) {
-    // stage the next row, load the offsets of the one after
-    const long long rn = r + warps, rnn = rn + warps;
-    if (rn < p.n_dof) {
-      stage_range(wbase + lay.pos + (buf ^ 1) * lay.pb, pos_bytes, 2ll * n_k0 * N, 2ll * n_k1 * N, lane);
-      stage_range(wbase + lay.inc + (buf ^ 1) * lay.ib, inc_bytes, 4ll * n_k0, 4ll * n_k1, lane);
+  cp_async_wait_all();
+  __syncthreads();
+  if (w < 2 && w < n_iter) geometry_task(w);
+  cp_async_commit();
+  cp_async_wait_all();
+  __syncthreads();
+  if (w == 0 && n_iter > 0) prepare_task(0);
+  __syncthreads();
+  bool bad = false;
+  for (long long i = 0; i <= n_iter; ++i) {
+    if (t == 0) tq[(i + 1) & 1] = 0;  // the next iteration's queue (last used two iterations ago)
+    // this iteration's work: units (and column tails) of chunk i, write-out blocks of chunk i - 1
+    int nI = 0, nU = 0, nW = 0, P = 0, V = 0;
+    if (i < n_iter) {
+      const long long* m = meta_at(i);
+      P = int(m[1] - m[0]);
+      V = int(m[5] - m[4]);
+      nU = slot[i % 3].n_units;
+      nI = nU + (K::MAIN && K::W > 0 ? (P * K::W + K::TB - 1) / K::TB : 0);
+    }
+    if (i >= 1) {
+      const long long* m = meta_at(i - 1);
+      nW = (int(m[5] - m[4]) + K::WB - 1) / K::WB + 1;  // one more for the value before the 16-byte boundary
+    }
+    const int nMix = 2 * min(nI, nW), n_tasks = NSPECIAL + nI + nW;
+    const unsigned char* reg = region_at(i);
+    const int32_t* pr = reinterpret_cast<const int32_t*>(reg + CB);
+    const uint16_t* pos = reinterpret_cast<const uint16_t*>(reg + CB + 4 * P);
+    const T* gs = gbuf + size_t(i % 3) * p.pmax * GS;
+    int* ab = acc + (i & 1) * ACC;
+    Digits<NDIG> dig[NF];
+    bool magic = sizeof(T) == 4;
+    if (i < n_iter) {
+#pragma unroll
+      for (int f = 0; f < NF; ++f) {
+        dig[f].init(slot[i % 3].eb[f]);
+        magic = magic && dig[f].magic;
+      }
+    }
+    for (;;) {
+      int k = 0;
+      if (lane == 0) k = atomicAdd(tq + (i & 1), 1);
+      k = __shfl_sync(0xffffffffu, k, 0);
+      if (k >= n_tasks) break;
+      if (k < NSPECIAL) {
+        if (k == 0 && i + 3 < n_iter) region_task(i + 3);
+        if (k == 1 && i + 2 < n_iter) geometry_task(i + 2);
+        if (k == 2) meta_task(i + 5);
+        if (k == 3 && i + 1 < n_iter) prepare_task(i + 1);
+        continue;
+      }
+      k -= NSPECIAL;
+      // items and write-out blocks alternate while both last
+      bool item;
+      int j;
+      if (k < nMix) {
+        item = (k & 1) == 0;
+        j = k >> 1;
+      } else {
+        item = nI > nW;
+        j = k - nMix / 2;
+      }
+      if (item) {
+        if (j < nU) {
+          const unsigned ud = units[(i % 3) * ROWS_PMAX + j];
+          bad |= magic ? unit_task<K, FORM, NF, GS, true, NDIG, T>(ud, gs, pos, ab, dig, A0a, A0b, V)
+                       : unit_task<K, FORM, NF, GS, false, NDIG, T>(ud, gs, pos, ab, dig, A0a, A0b, V);
+        } else {
+          bad |= magic ? tail_task<K, FORM, NF, GS, true, NDIG, T>(j - nU, P, pr, gs, pos, ab, dig, A0a, A0b, V)
+                       : tail_task<K, FORM, NF, GS, false, NDIG, T>(j - nU, P, pr, gs, pos, ab, dig, A0a, A0b, V);
+        }
+      } else {
+        write_task(i - 1, j);
+      }
     }
     cp_async_commit();
-    long long nn_base = 0, nn_end = 0;
-    int nn_k0 = 0, nn_k1 = 0;
-    if (rnn < p.n_dof) {
-      nn_base = p.row_ptr[rnn];
-      nn_end = p.row_ptr[rnn + 1];
-      nn_k0 = p.inc_ptr[rnn];
-      nn_k1 = p.inc_ptr[rnn + 1];
-    }
-    cp_async_wait<1>();  // this row's copies are done (the next row's may still fly)
-    __syncwarp();
-    const long long base = m_base, Ll = m_end - m_base;
-    const int k0 = m_k0, c = m_k1 - m_k0;
-    const uint16_t* pos_s = reinterpret_cast<const uint16_t*>(wbase + lay.pos + buf * lay.pb + ((2ll * k0 * N) & 15));
-    int* inc_s = reinterpret_cast<int*>(wbase + lay.inc + buf * lay.ib + ((4ll * k0) & 15));
-    if (Ll < 0 || Ll > p.lmax || c < 0 || c > p.max_inc) {
-      if (lane == 0) atomicOr(p.status, FFC_FLAG_BOUNDS);
-    } else {
-      const int L = int(Ll);
-      // G_K of the row's cells into shared memory (local index i1 replaces the incidence),
-      // and the bound on the row's sum of |contributions|
-      T bnd = T(0);
-      for (int j = lane; j < c; j += 32) {
-        const int t = inc_s[j];
-        const int e = t / N, i1 = t - e * N;
-        T g[GS];
-        load_g<T, GS>(G + (long long)e * GS, g);
-#pragma unroll
-        for (int a = 0; a < GS; ++a) gbuf[j * GS + a] = g[a];
-        inc_s[j] = i1;
-        bnd += a0max[i1] * g[NAK];
-      }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) bnd += __shfl_xor_sync(0xffffffffu, bnd, o);
-      __syncwarp();
-      const T big = sizeof(T) == 4 ? T(FLT_MAX) : T(DBL_MAX);
-      if (!(bnd <= big)) {  // a non-finite G_K (degenerate cell, flagged by the geometry kernel)
-        for (int j = lane; j < L; j += 32) p.csr_val[base + j] = __longlong_as_double(0x7ff8000000000000ll);
-      } else {
-        const int eb = bound_exponent(bnd);
-        const bool split_ok = sizeof(T) == 4 && eb >= -85 && eb <= 126;  // uniform over the warp
-        FixedSplit split;
-        split.init(split_ok ? eb : 0);
-        const int items = c * N;
-        for (int it = lane; it < items; it += 32) {
-          const int k = it / N, i2 = it - k * N;
-          const int i1 = inc_s[k];
-          const int q = pos_s[it];
-          const T* g = gbuf + k * GS;
-          const T* a = a0s + (i1 * N + i2) * NAK;
-          T v = T(0);
-#pragma unroll
-          for (int al = 0; al < NAK; ++al) v = fma(g[al], a[al], v);
-          long long f;
-          if constexpr (sizeof(T) == 4) f = split_ok ? split(v) : to_fixed(v, eb - 2);
-          else f = to_fixed(v, eb - 2);
-          if (q < L) atomicAdd(acc + q, static_cast<unsigned long long>(f));
-          else atomicOr(p.status, FFC_FLAG_BOUNDS);
-        }
-        __syncwarp();
-        for (int j = lane; j < L; j += 32) {
-          const long long f = static_cast<long long>(acc[j]);
-          acc[j] = 0ull;
-          __stcs(p.csr_val + base + j, fixed_to_double(f, eb - 2));
-        }
-      }
-    }
-    __syncwarp();  // this row's buffers are free for the copy issued next iteration
-    buf ^= 1;
-    m_base = n_base;
-    m_end = n_end;
-    m_k0 = n_k0;
-    m_k1 = n_k1;
-    n_base = nn_base;
-    n_end = nn_end;
-    n_k0 = nn_k0;
-    n_k1 = nn_k1;
+    cp_async_wait_all();  // this thread's copies (region i + 3, geometry i + 2)
+    __syncthreads();
   }
-  cp_async_wait<0>();
+  if (bad) atomicOr(p.status, FFC_FLAG_BOUNDS);
 }
 
 template <int D, int FORM, int Q, typename T>
-int launch_rows_t(const ffc_row_plan* plan, const void* a0, double* csr_val, unsigned* status,
-                  cudaStream_t s) {
-  using C = RowsCfg<D, FORM, Q, T>;
-  int dev = 0, sms = 0, smem_max = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  const int lmax = plan->max_row > 0 ? plan->max_row : 1;
-  const int max_inc = plan->max_incidence > 0 ? plan->max_incidence : 1;
-  const WarpLayout lay(lmax, max_inc, C::N, C::GS * int(sizeof(T)));
+int launch_rows_t(const ffc_row_plan* plan, const void* a0a, const void* a0b, double* out_a, double* out_b,
+                  unsigned* status, cudaStream_t s) {
+  using C = RowsGeo<D, FORM>;
+  constexpr int N = nscalar(D, Q);
+  const int pmax = std::max(plan->max_pairs, 1);
+  using K = RowsCfg<D, FORM, Q>;
+  constexpr int NDIG = sizeof(T) == 4 ? 2 : 3;
+  const int rmax = std::max(plan->max_region, 16);
+  const size_t meta_off = (2 * size_t(C::NF) * NDIG * ROWS_VMAX * 4 + 4 * size_t(rmax) +
+                           (3 * size_t(pmax) * C::GS + size_t(C::NF) * N) * sizeof(T) + 3 * ROWS_PMAX * 4 +
+                           3 * sizeof(RowsSlot) + 2 * 4 + 15) / 16 * 16;
+  const size_t smem = meta_off + 8 * 8 * sizeof(long long);
   auto kern = rows_assemble<D, FORM, Q, T>;
-  // warps per block: the count that keeps the most warps resident per SM
-  int best_nw = 0, best_warps = 0;
-  size_t best_smem = 0;
-  for (int nw : {16, 12, 8, 6, 4, 2, 1}) {
-    const size_t smem = C::A0_BYTES + size_t(nw) * lay.bytes;
-    if (smem > size_t(smem_max)) continue;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
-    int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, nw * 32, smem);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
-    if (per_sm * nw > best_warps) {
-      best_warps = per_sm * nw;
-      best_nw = nw;
-      best_smem = smem;
-    }
-  }
-  if (best_nw == 0) {
-    set_error("row assembly: the longest row does not fit in shared memory");
-    return FFC_EUNSUPPORTED;
-  }
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(best_smem));
-  if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
-  long long blocks = (long long)sms * (best_warps / best_nw);
-  const long long need = (plan->n_dof + best_nw - 1) / best_nw;
-  if (blocks > need) blocks = need;
-  if (blocks < 1) blocks = 1;
-  RowsParams prm{plan->row_ptr, plan->inc_ptr, plan->inc, plan->pos, plan->geom, a0, csr_val,
-                 (long long)plan->n_dof, lmax, max_inc, lay.bytes, status};
-  kern<<<unsigned(blocks), best_nw * 32, best_smem, s>>>(prm);
-  e = cudaGetLastError();
+  int dev = 0, smem_optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (smem > size_t(smem_optin)) return FFC_EUNSUPPORTED;  // the pair then runs as two single passes
+  int sms = 0, per_sm = 1;
+  constexpr int TH = sizeof(T) == 4 ? 1024 : 512;
+  if (launch_config(reinterpret_cast<const void*>(kern), TH, smem, -1, &sms, &per_sm) != FFC_OK)
+    return FFC_ECUDA;
+  long long blocks = (long long)sms * per_sm;
+  if (blocks > plan->n_chunks) blocks = plan->n_chunks;
+  if (blocks < 1) return FFC_OK;
+  RowsParams prm{plan->chunk_off, plan->chunk_pair, plan->chunk_val, plan->chunk_inc, plan->region, plan->geom,
+                 a0a, a0b, out_a, out_b, (long long)plan->n_chunks, int(meta_off), pmax, rmax, status};
+  kern<<<unsigned(blocks), TH, smem, s>>>(prm);
+  const cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? FFC_OK : cuda_fail(e, "rows_assemble launch");
 }
 
@@ -618,9 +1036,9 @@ template <int D, int FORM, typename T>
 int launch_rows_geometry(const ffc_row_plan* plan, const int32_t* cells, const double* vertices, int64_t n_vert,
                          unsigned* status, cudaStream_t s) {
   if (plan->n_elem == 0) return FFC_OK;
-  int dev = 0, sms = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  int sms = 0;
+  if (launch_config(reinterpret_cast<const void*>(rows_geometry<D, FORM, T>), 256, 0, -1, &sms, nullptr) != FFC_OK)
+    return FFC_ECUDA;
   long long blocks = (plan->n_elem + 255) / 256;
   if (blocks > (long long)sms * 8) blocks = (long long)sms * 8;
   rows_geometry<D, FORM, T><<<unsigned(blocks), 256, 0, s>>>(cells, vertices, n_vert, plan->n_elem,
@@ -631,27 +1049,35 @@ int launch_rows_geometry(const ffc_row_plan* plan, const int32_t* cells, const d
 
 template <int D, int FORM, typename T>
 int launch_rows_q(const ffc_row_plan* plan, int q, const int32_t* cells, const double* vertices, int64_t n_vert,
-                  const void* a0, double* csr_val, unsigned* status, cudaStream_t s) {
+                  const void* a0a, const void* a0b, double* out_a, double* out_b, unsigned* status,
+                  cudaStream_t s) {
   int rc = launch_rows_geometry<D, FORM, T>(plan, cells, vertices, n_vert, status, s);
   if (rc != FFC_OK) return rc;
   switch (q) {
-    case 1: return launch_rows_t<D, FORM, 1, T>(plan, a0, csr_val, status, s);
-    case 2: return launch_rows_t<D, FORM, 2, T>(plan, a0, csr_val, status, s);
-    case 3: return launch_rows_t<D, FORM, 3, T>(plan, a0, csr_val, status, s);
-    case 4: return launch_rows_t<D, FORM, 4, T>(plan, a0, csr_val, status, s);
+    case 1: return launch_rows_t<D, FORM, 1, T>(plan, a0a, a0b, out_a, out_b, status, s);
+    case 2: return launch_rows_t<D, FORM, 2, T>(plan, a0a, a0b, out_a, out_b, status, s);
+    case 3: return launch_rows_t<D, FORM, 3, T>(plan, a0a, a0b, out_a, out_b, status, s);
+    case 4: return launch_rows_t<D, FORM, 4, T>(plan, a0a, a0b, out_a, out_b, status, s);
     default: return FFC_EUNSUPPORTED;
   }
 }
 
 template <typename T>
-int launch_rows_form(const ffc_form* f, const ffc_row_plan* plan, const int32_t* cells, const double* vertices,
-                     int64_t n_vert, const void* a0, double* csr_val, unsigned* status, cudaStream_t s) {
-  if (f->d == 3) {
-    if (f->kind == FFC_MASS) return launch_rows_q<3, FFC_MASS, T>(plan, f->q, cells, vertices, n_vert, a0, csr_val, status, s);
-    return launch_rows_q<3, FFC_POISSON, T>(plan, f->q, cells, vertices, n_vert, a0, csr_val, status, s);
+int launch_rows_form(int form, int d, int q, const ffc_row_plan* plan, const int32_t* cells, const double* vertices,
+                     int64_t n_vert, const void* a0a, const void* a0b, double* out_a, double* out_b,
+                     unsigned* status, cudaStream_t s) {
+  if (d == 3) {
+    if (form == FFC_MASS)
+      return launch_rows_q<3, FFC_MASS, T>(plan, q, cells, vertices, n_vert, a0a, a0b, out_a, out_b, status, s);
+    if (form == FFC_POISSON)
+      return launch_rows_q<3, FFC_POISSON, T>(plan, q, cells, vertices, n_vert, a0a, a0b, out_a, out_b, status, s);
+    return launch_rows_q<3, ROWS_PAIR, T>(plan, q, cells, vertices, n_vert, a0a, a0b, out_a, out_b, status, s);
   }
-  if (f->kind == FFC_MASS) return launch_rows_q<2, FFC_MASS, T>(plan, f->q, cells, vertices, n_vert, a0, csr_val, status, s);
-  return launch_rows_q<2, FFC_POISSON, T>(plan, f->q, cells, vertices, n_vert, a0, csr_val, status, s);
+  if (form == FFC_MASS)
+    return launch_rows_q<2, FFC_MASS, T>(plan, q, cells, vertices, n_vert, a0a, a0b, out_a, out_b, status, s);
+  if (form == FFC_POISSON)
+    return launch_rows_q<2, FFC_POISSON, T>(plan, q, cells, vertices, n_vert, a0a, a0b, out_a, out_b, status, s);
+  return launch_rows_q<2, ROWS_PAIR, T>(plan, q, cells, vertices, n_vert, a0a, a0b, out_a, out_b, status, s);
 }
 
 void free_plan(ffc_row_plan* p) {
@@ -660,9 +1086,12 @@ void free_plan(ffc_row_plan* p) {
   cudaGetDevice(&cur);
   cudaSetDevice(p->device);
   cudaFree(p->row_ptr);
-  cudaFree(p->inc_ptr);
-  cudaFree(p->inc);
-  cudaFree(p->pos);
+  cudaFree(p->chunk_row);
+  cudaFree(p->chunk_pair);
+  cudaFree(p->chunk_off);
+  cudaFree(p->chunk_val);
+  cudaFree(p->chunk_inc);
+  cudaFree(p->region);
   cudaFree(p->geom);
   cudaSetDevice(cur);
   delete p;
@@ -674,6 +1103,37 @@ int dev_alloc(T** p, size_t count) {
   return e == cudaSuccess ? FFC_OK : cuda_fail(e, "cudaMalloc");
 }
 
+// Common checks of the row assemblies; fills the device tensors of the form(s).
+int rows_checks(const char* who, const ffc_form* f, const ffc_row_plan* plan, const int32_t* cells,
+                const double* vertices, int64_t n_vert, const double* out, int precision) {
+  if (!f || !plan || n_vert < 0 || (precision != FFC_FP64 && precision != FFC_FP32)) {
+    set_error(std::string(who) + ": invalid argument");
+    return FFC_EINVAL;
+  }
+  if ((f->kind != FFC_MASS && f->kind != FFC_POISSON) || f->rank != 2) {
+    set_error(std::string(who) + ": mass and Poisson forms only");
+    return FFC_EUNSUPPORTED;
+  }
+  if (f->n != plan->n_local) {
+    set_error(std::string(who) + ": the plan was built for another number of local dofs");
+    return FFC_EINVAL;
+  }
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev != plan->device) {
+    set_error(std::string(who) + ": the plan lives on another device");
+    return FFC_EINVAL;
+  }
+  if (plan->nnz == 0) return FFC_OK;
+  if (!out || (reinterpret_cast<uintptr_t>(out) & 7) ||
+      (plan->n_elem > 0 && (!cells || !vertices || n_vert == 0 || (reinterpret_cast<uintptr_t>(cells) & 15) ||
+                            (reinterpret_cast<uintptr_t>(vertices) & 7)))) {
+    set_error(std::string(who) + ": null or misaligned pointer");
+    return FFC_EINVAL;
+  }
+  return FFC_OK;
+}
+
 }  // namespace
 }  // namespace ffc
 
@@ -683,9 +1143,9 @@ extern "C" {
 
 int ffc_row_plan_create(int64_t n_elem, int n_local, const int32_t* dofmap, int64_t n_dof, const int64_t* row_ptr,
                         const int32_t* col, int64_t nnz, void* stream, ffc_row_plan** out) {
-  if (!out || n_elem < 0 || n_local < 1 || n_local > 4096 || n_dof < 1 || n_dof >= INT32_MAX || nnz < 0 ||
+  if (!out || n_elem < 0 || n_local < 2 || n_local > ROWS_MAX_LOCAL || n_dof < 1 || n_dof >= INT32_MAX || nnz < 0 ||
       !row_ptr || (n_elem > 0 && !dofmap) || (nnz > 0 && !col)) {
-    set_error("ffc_row_plan_create: invalid argument");
+    set_error("ffc_row_plan_create: invalid argument (2 <= n_local <= 64)");
     return FFC_EINVAL;
   }
   if (n_elem * (long long)n_local >= INT32_MAX) {
@@ -707,67 +1167,158 @@ int ffc_row_plan_create(int64_t n_elem, int n_local, const int32_t* dofmap, int6
   p->nnz = nnz;
   const long long total = n_elem * (long long)n_local;
   const long long nb = (n_dof + 1 + SCAN_CHUNK - 1) / SCAN_CHUNK;
-  int32_t *inc_tmp = nullptr, *fill = nullptr, *sums = nullptr;
-  int* meta = nullptr;  // err, max_row, max_incidence
+  int32_t *inc_ptr = nullptr, *inc_tmp = nullptr, *fill = nullptr, *sums = nullptr;
+  unsigned long long* key = nullptr;
+  unsigned* err = nullptr;
   int rc = FFC_OK;
   cudaError_t e = cudaSuccess;
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device);
   const unsigned grid = unsigned(sms > 0 ? sms * 8 : 1024);
-  int host_meta[3] = {0, 0, 0};
-  if ((rc = dev_alloc(&p->row_ptr, size_t(n_dof) + 1)) || (rc = dev_alloc(&p->inc_ptr, size_t(n_dof) + 1)) ||
-      (rc = dev_alloc(&p->inc, size_t(total) + 4)) || (rc = dev_alloc(&p->pos, size_t(total) * n_local + 8)) ||
-      (rc = dev_alloc(reinterpret_cast<double**>(&p->geom), size_t(n_elem) * 8)) ||
+  unsigned host_err = 0;
+  std::vector<int64_t> h_row_ptr(size_t(n_dof) + 1);
+  std::vector<int32_t> h_inc_ptr(size_t(n_dof) + 1);
+  std::vector<int32_t> h_chunk_row, h_chunk_pair, h_chunk_inc;
+  std::vector<int64_t> h_chunk_off, h_chunk_val;
+  if ((rc = dev_alloc(&p->row_ptr, size_t(n_dof) + 1)) || (rc = dev_alloc(&inc_ptr, size_t(n_dof) + 1)) ||
       (rc = dev_alloc(&inc_tmp, size_t(total))) || (rc = dev_alloc(&fill, size_t(n_dof))) ||
-      (rc = dev_alloc(&sums, size_t(nb))) || (rc = dev_alloc(&meta, 3)))
+      (rc = dev_alloc(&sums, size_t(nb))) || (rc = dev_alloc(&err, 1)) ||
+      (rc = dev_alloc(reinterpret_cast<double**>(&p->geom), size_t(n_elem) * 12)))
     goto fail;
   if ((e = cudaMemcpyAsync(p->row_ptr, row_ptr, (size_t(n_dof) + 1) * sizeof(int64_t), cudaMemcpyDeviceToDevice,
                            s)) != cudaSuccess ||
-      (e = cudaMemsetAsync(p->inc_ptr, 0, (size_t(n_dof) + 1) * sizeof(int32_t), s)) != cudaSuccess ||
+      (e = cudaMemsetAsync(inc_ptr, 0, (size_t(n_dof) + 1) * sizeof(int32_t), s)) != cudaSuccess ||
       (e = cudaMemsetAsync(fill, 0, size_t(n_dof) * sizeof(int32_t), s)) != cudaSuccess ||
-      (e = cudaMemsetAsync(meta, 0, 3 * sizeof(int), s)) != cudaSuccess) {
+      (e = cudaMemsetAsync(err, 0, sizeof(unsigned), s)) != cudaSuccess) {
     rc = cuda_fail(e, "ffc_row_plan_create: memset");
     goto fail;
   }
-  if (total > 0) plan_count<<<grid, 256, 0, s>>>(dofmap, total, n_dof, p->inc_ptr, reinterpret_cast<unsigned*>(meta));
-  scan_chunks<<<unsigned(nb), SCAN_T, 0, s>>>(p->inc_ptr, n_dof + 1, sums);
+  if (total > 0) plan_count<<<grid, 256, 0, s>>>(dofmap, total, n_dof, inc_ptr, err);
+  scan_chunks<<<unsigned(nb), SCAN_T, 0, s>>>(inc_ptr, n_dof + 1, sums);
   scan_sums<<<1, SCAN_T, 0, s>>>(sums, int(nb));
-  scan_add<<<unsigned(nb), SCAN_T, 0, s>>>(p->inc_ptr, n_dof + 1, sums);
-  if (total > 0) plan_fill<<<grid, 256, 0, s>>>(dofmap, total, n_dof, p->inc_ptr, fill, inc_tmp);
-  plan_rows<<<grid, 256, 0, s>>>(dofmap, n_local, n_dof, p->row_ptr, col, nnz, p->inc_ptr, inc_tmp, p->inc, p->pos,
-                                 meta + 1, meta + 2, reinterpret_cast<unsigned*>(meta));
-  if ((e = cudaGetLastError()) != cudaSuccess || (e = cudaMemcpyAsync(host_meta, meta, sizeof(host_meta),
-                                                                      cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+  scan_add<<<unsigned(nb), SCAN_T, 0, s>>>(inc_ptr, n_dof + 1, sums);
+  if (total > 0) plan_fill<<<grid, 256, 0, s>>>(dofmap, total, n_dof, inc_ptr, fill, inc_tmp);
+  if ((e = cudaGetLastError()) != cudaSuccess ||
+      (e = cudaMemcpyAsync(h_row_ptr.data(), row_ptr, h_row_ptr.size() * sizeof(int64_t), cudaMemcpyDeviceToHost,
+                           s)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(h_inc_ptr.data(), inc_ptr, h_inc_ptr.size() * sizeof(int32_t), cudaMemcpyDeviceToHost,
+                           s)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(&host_err, err, sizeof(unsigned), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
       (e = cudaStreamSynchronize(s)) != cudaSuccess) {
     rc = cuda_fail(e, "ffc_row_plan_create");
     goto fail;
   }
-  if (host_meta[0] & int(PLAN_LONG_ROW | PLAN_BAD_ROW_PTR)) {  // a malformed pattern comes first
-    set_error(host_meta[0] & int(PLAN_BAD_ROW_PTR) ? "ffc_row_plan_create: row_ptr is not monotone within [0, nnz]"
-                                                    : "ffc_row_plan_create: a row has more than 65535 entries");
-    rc = FFC_EINVAL;
-    goto fail;
-  }
-  if (host_meta[0] & int(PLAN_BAD_DOF | PLAN_MISSING)) {
-    set_error(host_meta[0] & int(PLAN_BAD_DOF) ? "ffc_row_plan_create: dof id out of range"
-                                                : "ffc_row_plan_create: a (row, col) pair is not in the pattern");
+  if (host_err & PLAN_BAD_DOF) {
+    set_error("ffc_row_plan_create: dof id out of range");
     rc = FFC_EBOUNDS;
     goto fail;
   }
-  p->max_row = host_meta[1];
-  p->max_incidence = host_meta[2];
+  {
+    // rows -> chunks (host, one pass): consecutive rows while the chunk holds at most
+    // ROWS_VMAX values, ROWS_PMAX pairs and 65536 rows
+    if (h_row_ptr[0] != 0 || h_row_ptr[n_dof] != nnz) host_err |= PLAN_BAD_ROW_PTR;
+    int32_t cur_v = 0, cur_p = 0, cur_inc = 0, r_start = 0;
+    int64_t off = 0;
+    auto close_chunk = [&](int64_t r) {
+      const int64_t bytes = region_bytes(n_local, cur_p);
+      off += bytes;
+      h_chunk_inc.push_back(cur_inc);
+      p->vmax = std::max(p->vmax, int(cur_v));
+      p->max_pairs = std::max(p->max_pairs, int(cur_p));
+      p->max_region = std::max(p->max_region, int(bytes));
+      h_chunk_row.push_back(int32_t(r));
+      h_chunk_pair.push_back(h_inc_ptr[r]);
+      h_chunk_off.push_back(off);
+      h_chunk_val.push_back(h_row_ptr[r]);
+      cur_v = cur_p = cur_inc = 0;
+      r_start = int32_t(r);
+    };
+    h_chunk_row.push_back(0);
+    h_chunk_pair.push_back(0);
+    h_chunk_off.push_back(0);
+    h_chunk_val.push_back(0);
+    for (int64_t r = 0; r < n_dof && !(host_err & PLAN_BAD_ROW_PTR); ++r) {
+      const int64_t L = h_row_ptr[r + 1] - h_row_ptr[r];
+      const int32_t c = h_inc_ptr[r + 1] - h_inc_ptr[r];
+      if (L < 0 || h_row_ptr[r + 1] > nnz) {
+        host_err |= PLAN_BAD_ROW_PTR;
+        break;
+      }
+      if (L > ROWS_VMAX || c > ROWS_PMAX || c > ROWS_MAX_INCIDENCE) {
+        set_error("ffc_row_plan_create: row " + std::to_string(r) + " has " + std::to_string(L) + " entries and " +
+                  std::to_string(c) + " (cell, local dof) pairs; at most " + std::to_string(ROWS_VMAX) + " and " +
+                  std::to_string(std::min(ROWS_PMAX, ROWS_MAX_INCIDENCE)) + " are supported");
+        rc = FFC_EINVAL;
+        goto fail;
+      }
+      if (r > r_start && (cur_v + L > ROWS_VMAX || cur_p + c > ROWS_PMAX || r - r_start >= 65536)) close_chunk(r);
+      cur_v += int32_t(L);
+      cur_p += c;
+      cur_inc = std::max(cur_inc, c);
+      p->max_row = std::max(p->max_row, int(L));
+      p->max_incidence = std::max(p->max_incidence, int(c));
+    }
+    if (host_err & PLAN_BAD_ROW_PTR) {
+      set_error("ffc_row_plan_create: row_ptr is not monotone within [0, nnz]");
+      rc = FFC_EINVAL;
+      goto fail;
+    }
+    close_chunk(n_dof);
+    p->n_chunks = int64_t(h_chunk_inc.size());
+    p->region_total = off;
+  }
+  if ((rc = dev_alloc(&p->chunk_row, h_chunk_row.size())) || (rc = dev_alloc(&p->chunk_pair, h_chunk_pair.size())) ||
+      (rc = dev_alloc(&p->chunk_off, h_chunk_off.size())) || (rc = dev_alloc(&p->chunk_val, h_chunk_val.size())) ||
+      (rc = dev_alloc(&p->chunk_inc, h_chunk_inc.size())) ||
+      (rc = dev_alloc(&p->region, size_t(p->region_total) + 16)) ||
+      (rc = dev_alloc(&key, size_t(total))))
+    goto fail;
+  if ((e = cudaMemcpyAsync(p->chunk_row, h_chunk_row.data(), h_chunk_row.size() * 4, cudaMemcpyHostToDevice, s)) !=
+          cudaSuccess ||
+      (e = cudaMemcpyAsync(p->chunk_pair, h_chunk_pair.data(), h_chunk_pair.size() * 4, cudaMemcpyHostToDevice, s)) !=
+          cudaSuccess ||
+      (e = cudaMemcpyAsync(p->chunk_off, h_chunk_off.data(), h_chunk_off.size() * 8, cudaMemcpyHostToDevice, s)) !=
+          cudaSuccess ||
+      (e = cudaMemcpyAsync(p->chunk_val, h_chunk_val.data(), h_chunk_val.size() * 8, cudaMemcpyHostToDevice, s)) !=
+          cudaSuccess ||
+      (e = cudaMemcpyAsync(p->chunk_inc, h_chunk_inc.data(), h_chunk_inc.size() * 4, cudaMemcpyHostToDevice, s)) !=
+          cudaSuccess ||
+      (e = cudaMemsetAsync(p->region, 0, size_t(p->region_total) + 16, s)) != cudaSuccess) {
+    rc = cuda_fail(e, "ffc_row_plan_create: chunk table");
+    goto fail;
+  }
+  plan_sort<<<unsigned((p->n_chunks + 127) / 128), 128, 0, s>>>(dofmap, p->chunk_row, p->chunk_pair, p->chunk_off,
+                                                                p->n_chunks, n_local, inc_tmp, key, p->region);
+  if (total > 0)
+    plan_positions<<<grid, 256, 0, s>>>(dofmap, n_local, p->row_ptr, col, p->chunk_row, p->chunk_pair, p->chunk_off,
+                                        p->n_chunks, p->region, err);
+  if ((e = cudaGetLastError()) != cudaSuccess ||
+      (e = cudaMemcpyAsync(&host_err, err, sizeof(unsigned), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(s)) != cudaSuccess) {
+    rc = cuda_fail(e, "ffc_row_plan_create");
+    goto fail;
+  }
+  if (host_err & PLAN_MISSING) {
+    set_error("ffc_row_plan_create: a (row, col) pair of a cell is not in the pattern");
+    rc = FFC_EBOUNDS;
+    goto fail;
+  }
+  cudaFree(inc_ptr);
   cudaFree(inc_tmp);
   cudaFree(fill);
   cudaFree(sums);
-  cudaFree(meta);
+  cudaFree(err);
+  cudaFree(key);
   *out = p;
   return FFC_OK;
 fail:
   cudaStreamSynchronize(s);
+  cudaFree(inc_ptr);
   cudaFree(inc_tmp);
   cudaFree(fill);
   cudaFree(sums);
-  cudaFree(meta);
+  cudaFree(err);
+  cudaFree(key);
   free_plan(p);
   return rc;
 }
@@ -781,47 +1332,80 @@ int ffc_row_plan_info(const ffc_row_plan* p, int64_t* n_dof, int64_t* nnz, int* 
   return FFC_OK;
 }
 
+int ffc_row_plan_layout(const ffc_row_plan* p, int64_t* n_chunks, int* max_chunk_values, int* max_chunk_pairs,
+                        int* max_region_bytes, int64_t* device_bytes) {
+  if (!p) return FFC_EINVAL;
+  if (n_chunks) *n_chunks = p->n_chunks;
+  if (max_chunk_values) *max_chunk_values = p->vmax;
+  if (max_chunk_pairs) *max_chunk_pairs = p->max_pairs;
+  if (max_region_bytes) *max_region_bytes = p->max_region;
+  if (device_bytes)
+    *device_bytes = (p->n_dof + 1) * 8 + (p->n_chunks + 1) * (4 + 4 + 8 + 8) + p->n_chunks * 4 +
+                    p->region_total + 16 + p->n_elem * 96;
+  return FFC_OK;
+}
+
 void ffc_row_plan_destroy(ffc_row_plan* p) { free_plan(p); }
 
 int ffc_assemble_rows(const ffc_form* f, const ffc_row_plan* plan, const int32_t* cells, const double* vertices,
                       int64_t n_vert, double* csr_val, int precision, void* stream) {
-  if (!f || !plan || n_vert < 0 || (precision != FFC_FP64 && precision != FFC_FP32)) {
-    set_error("ffc_assemble_rows: invalid argument");
-    return FFC_EINVAL;
-  }
-  if ((f->kind != FFC_MASS && f->kind != FFC_POISSON) || f->rank != 2) {
-    set_error("ffc_assemble_rows: mass and Poisson forms only");
-    return FFC_EUNSUPPORTED;
-  }
-  if (f->n != plan->n_local) {
-    set_error("ffc_assemble_rows: the plan was built for another number of local dofs");
-    return FFC_EINVAL;
-  }
-  int dev = 0;
-  cudaGetDevice(&dev);
-  if (dev != plan->device) {
-    set_error("ffc_assemble_rows: the plan lives on another device");
-    return FFC_EINVAL;
-  }
-  if (plan->nnz == 0) return FFC_OK;
-  if (!csr_val || (reinterpret_cast<uintptr_t>(csr_val) & 7) ||
-      (plan->n_elem > 0 && (!cells || !vertices || n_vert == 0 || (reinterpret_cast<uintptr_t>(cells) & 15) ||
-                            (reinterpret_cast<uintptr_t>(vertices) & 7)))) {
-    set_error("ffc_assemble_rows: null or misaligned pointer");
-    return FFC_EINVAL;
-  }
+  int rc = rows_checks("ffc_assemble_rows", f, plan, cells, vertices, n_vert, csr_val, precision);
+  if (rc != FFC_OK || plan->nnz == 0) return rc;
   DeviceTensors* t = nullptr;
-  int rc = ensure_device_tensors(const_cast<ffc_form*>(f), &t);
-  if (rc != FFC_OK) return rc;
+  if ((rc = ensure_device_tensors(const_cast<ffc_form*>(f), &t)) != FFC_OK) return rc;
   uint32_t* st = status_word();
   if (!st) {
     set_error("status word allocation failed");
     return FFC_ECUDA;
   }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if (precision == FFC_FP32)
-    return launch_rows_form<float>(f, plan, cells, vertices, n_vert, t->a0_f32, csr_val, st, s);
-  return launch_rows_form<double>(f, plan, cells, vertices, n_vert, t->a0_f64, csr_val, st, s);
+  rc = precision == FFC_FP32 ? launch_rows_form<float>(f->kind, f->d, f->q, plan, cells, vertices, n_vert, t->a0s_f32,
+                                                       nullptr, csr_val, nullptr, st, s)
+                             : launch_rows_form<double>(f->kind, f->d, f->q, plan, cells, vertices, n_vert,
+                                                        t->a0s_f64, nullptr, csr_val, nullptr, st, s);
+  if (rc == FFC_EUNSUPPORTED) set_error("ffc_assemble_rows: the plan's chunks need more shared memory than a CTA has");
+  return rc;
+}
+
+int ffc_assemble_rows_pair(const ffc_form* fa, const ffc_form* fb, const ffc_row_plan* plan, const int32_t* cells,
+                           const double* vertices, int64_t n_vert, double* csr_val_a, double* csr_val_b,
+                           int precision, void* stream) {
+  int rc = rows_checks("ffc_assemble_rows_pair", fa, plan, cells, vertices, n_vert, csr_val_a, precision);
+  if (rc != FFC_OK) return rc;
+  if ((rc = rows_checks("ffc_assemble_rows_pair", fb, plan, cells, vertices, n_vert, csr_val_b, precision)) != FFC_OK)
+    return rc;
+  if (fa->d != fb->d || fa->q != fb->q || csr_val_a == csr_val_b) {
+    set_error("ffc_assemble_rows_pair: two forms on one space, two distinct matrices");
+    return FFC_EINVAL;
+  }
+  if (plan->nnz == 0) return FFC_OK;
+  if (fa->kind == fb->kind) {  // not the (mass, Poisson) pair: two single passes
+    if ((rc = ffc_assemble_rows(fa, plan, cells, vertices, n_vert, csr_val_a, precision, stream)) != FFC_OK) return rc;
+    return ffc_assemble_rows(fb, plan, cells, vertices, n_vert, csr_val_b, precision, stream);
+  }
+  const ffc_form* fm = fa->kind == FFC_MASS ? fa : fb;
+  const ffc_form* fp = fa->kind == FFC_MASS ? fb : fa;
+  double* vm = fa->kind == FFC_MASS ? csr_val_a : csr_val_b;
+  double* vp = fa->kind == FFC_MASS ? csr_val_b : csr_val_a;
+  DeviceTensors *tm = nullptr, *tp = nullptr;
+  if ((rc = ensure_device_tensors(const_cast<ffc_form*>(fm), &tm)) != FFC_OK ||
+      (rc = ensure_device_tensors(const_cast<ffc_form*>(fp), &tp)) != FFC_OK)
+    return rc;
+  uint32_t* st = status_word();
+  if (!st) {
+    set_error("status word allocation failed");
+    return FFC_ECUDA;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (precision == FFC_FP32) {
+    rc = launch_rows_form<float>(ROWS_PAIR, fm->d, fm->q, plan, cells, vertices, n_vert, tm->a0s_f32, tp->a0s_f32, vm,
+                                 vp, st, s);
+    if (rc != FFC_EUNSUPPORTED) return rc;
+  }
+  // FP64 (whose double-buffered 63-bit accumulators of two matrices exceed the shared
+  // memory), and chunks too large for one pass: two single passes
+  if ((rc = ffc_assemble_rows(fm, plan, cells, vertices, n_vert, vm, precision, stream)) != FFC_OK) return rc;
+  return ffc_assemble_rows(fp, plan, cells, vertices, n_vert, vp, precision, stream);
 }
 
 }  // extern "C"
