@@ -294,7 +294,7 @@ def alg_bytes_tabulate(ctx, n_local, out_bytes):
 # DRAM bytes (read + write) per launch, from one `ncu` capture of the kernel on a smaller
 # mesh scaled by the cell count (positions, pairs, values and cells all grow with it); only
 # valid for the kernels as captured, other launches report null.
-CAPTURED_TRAFFIC_GB = {}
+CAPTURED_TRAFFIC_GB = {("rows_mass+poisson_p4", "fp32"): 1.237 * 8}  # captured at 24^3 x 6 = 82,944 cells
 
 _PEAKS = {}
 
@@ -1070,8 +1070,9 @@ def measure_other(F, args, device, workload):
                     "cpu_baseline": {"value": rate, "unit": "elem/s", "cores": cores, "kind": "oracle",
                                      "sample": f"{S} cells"}, "detail": detail})
     elif workload == "rows":
-        # the headline's eight problems by row-owner assembly (ffc_assemble_rows): exact
-        # fixed-point sums, every CSR value written once, no atomics and no zeroing
+        # the headline's eight problems, every degree by the row-owner assembly: mass and
+        # Poisson in one ffc_assemble_rows_pair launch per degree (fixed-point sums, every
+        # CSR value written once, no atomics and no zeroing)
         mesh = W.tet_scalar_mesh(args.n)
         cells = torch.as_tensor(mesh.cells, device=device)
         verts = torch.as_tensor(mesh.vertices, device=device)
@@ -1082,10 +1083,9 @@ def measure_other(F, args, device, workload):
             plan = F.RowPlan(torch.as_tensor(p.dofmap, device=device), p.n_dof,
                              torch.as_tensor(row_ptr, device=device), torch.as_tensor(col, device=device))
             del col
-            for form in FORMS:
-                probs.append({"form": form, "q": q, "F": F.Form(form, F.TETRAHEDRON, q), "plan": plan,
-                              "n_local": p.n_local, "nnz": plan.nnz,
-                              "val": torch.empty(plan.nnz, dtype=torch.float64, device=device)})
+            probs.append({"q": q, "plan": plan, "n_local": p.n_local, "nnz": plan.nnz,
+                          "F": (F.Form(F.MASS, F.TETRAHEDRON, q), F.Form(F.POISSON, F.TETRAHEDRON, q)),
+                          "val": [torch.empty(plan.nnz, dtype=torch.float64, device=device) for _ in FORMS]})
         P = len(probs)
         ev = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(P * args.steps)]
 
@@ -1093,7 +1093,8 @@ def measure_other(F, args, device, workload):
             for k, pr in enumerate(probs):
                 if s is not None:
                     ev[s * P + k][0].record()
-                F.assemble_rows(pr["F"], pr["plan"], cells, verts, pr["val"], precision=args.precision)
+                F.assemble_rows_pair(pr["F"][0], pr["F"][1], pr["plan"], cells, verts, pr["val"][0], pr["val"][1],
+                                     precision=args.precision)
                 if s is not None:
                     ev[s * P + k][1].record()
 
@@ -1114,29 +1115,30 @@ def measure_other(F, args, device, workload):
                for k in range(P)]
         dom = int(np.argmax(per))
         dpr = probs[dom]
-        # algorithmic bytes of one row-owner assembly: cells, vertices, the dof-map
-        # equivalent (4n per cell) and the CSR values written once
-        byts = mesh.n_elem * (16 + 4 * dpr["n_local"]) + mesh.n_vert * 24 + 8 * dpr["nnz"]
+        # algorithmic bytes of one row-owner pair launch: cells, vertices, the dof-map
+        # equivalent (4n per cell) and the two matrices' CSR values written once
+        byts = mesh.n_elem * (16 + 4 * dpr["n_local"]) + mesh.n_vert * 24 + 2 * 8 * dpr["nnz"]
         cpu = None
         if not args.no_cpu_baseline:
             pool, _ = oracle_pool()
             S, t_cpu = cpu_oracle_step(args.n, REF_FRACTION, pool)
             pool.close()
             pool.join()
-            cpu = {"value": P * S / t_cpu, "unit": "elem/s", "cores": cores, "kind": "oracle",
+            cpu = {"value": 2 * P * S / t_cpu, "unit": "elem/s", "cores": cores, "kind": "oracle",
                    "sample": f"{S} cells of each of the 8 problems, element tensors and Algorithm 2, {t_cpu:.1f} s"}
-        out.update({"metric": "element tensors/s (row-owner assembly, exact sums, mass+Poisson P1..P4 on 48^3x6 tets)",
-                    "value": P * mesh.n_elem / t, "ms_per_step": t * 1e3, "dtype": "f32" if args.precision != "fp64"
-                    else "f64",
+        out.update({"metric": "element tensors/s (row-owner assembly, mass+Poisson P1..P4 on 48^3x6 tets)",
+                    "value": 2 * P * mesh.n_elem / t, "ms_per_step": t * 1e3,
+                    "dtype": "f32" if args.precision != "fp64" else "f64",
                     "config": {"workload": f"tet_scalar_{args.n}_rows", "cells": mesh.n_elem,
-                               "problems": [f"{FORM_NAME[p_['form']]}_p{p_['q']}" for p_ in probs],
-                               "csr_accumulation": "fixed point in shared memory (42-bit for FP32 contributions, 63-bit for FP64), rounded once to f64",
-                               "l2": "inputs larger than L2: ~8 GB of positions and CSR values per step"},
+                               "problems": [f"mass+poisson_p{p_['q']}" for p_ in probs],
+                               "csr_accumulation": "fixed point in shared memory (42-bit for FP32 contributions, "
+                                                   "63-bit for FP64), rounded once to f64",
+                               "l2": "inputs larger than L2: ~12 GB of positions and CSR values per step"},
                     "roofline": {"bound": "hbm", "achieved": byts / per[dom] / 1e9, "peak": hbm_peak, "unit": "GB/s",
                                  "frac": byts / per[dom] / 1e9 / hbm_peak, "traffic": None, "peak_kind": peak_kind,
-                                 "kernel": f"rows_assemble {FORM_NAME[dpr['form']]} P{dpr['q']}",
+                                 "kernel": f"rows_assemble mass+Poisson P{dpr['q']}",
                                  "launch_ms": per[dom] * 1e3},
-                    "per_launch_ms": {f"{FORM_NAME[p_['form']]}_p{p_['q']}": round(per[k] * 1e3, 4)
+                    "per_launch_ms": {f"mass+poisson_p{p_['q']}": round(per[k] * 1e3, 4)
                                       for k, p_ in enumerate(probs)},
                     "clocks": clk, "gpu_launches": 2 * P * args.steps, "cpu_baseline": cpu})
     else:  # adjoint

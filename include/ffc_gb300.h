@@ -277,13 +277,16 @@ void ffc_batch_destroy(ffc_batch* b);
  * (A^K = A0 : G_K, Section 3.2), and writes the chunk's CSR values once, in order. No
  * global atomics, no zeroing: every CSR value is overwritten.
  *
- * The sums are exact: each contribution (FP32 or FP64, as the contraction produced it)
- * is converted to fixed point with one unit per chunk, u = 2^(eb-62), where 2^(eb-1)
+ * The sums are in fixed point: each contribution (FP32 or FP64, as the contraction
+ * produced it) is rounded to a grid with one unit per chunk and form, where 2^(eb-1)
  * bounds every partial sum of the chunk's entries (the largest per-pair bound
- * max|A0[i1][.][.]| * sum|G_K| times the most pairs of one row); integer sums do not
- * depend on their order, and each result is rounded once to FP64 (nearest even). Per
- * entry: |result - exact sum of the contributions| <= m * u + ulp(result) / 2 with m the
- * entry's number of contributions. Results are bitwise reproducible.
+ * max|A0[i1][.][.]| * sum|G_K| times the most pairs of one row): u = 2^(eb-62) (63 bits,
+ * three 21-bit digits) for FFC_FP64 and u = 2^(eb-41) (42 bits, two digits) for FFC_FP32,
+ * whose contributions carry 24 bits. The digits are summed as 32-bit integers in shared
+ * memory, so the sums do not depend on their order, and each result is rounded once to
+ * FP64. Per entry: |result - exact sum of the contributions| <= m * u / 2 + ulp(result)
+ * with m the entry's number of contributions (u / 2 < 2^-40 B for FP32, 2^-61 B for FP64,
+ * B the chunk's bound). Results are bitwise reproducible.
  *
  * ffc_row_plan_create -- the row view of a dof map and its CSR pattern, built on the
  * device once per (mesh, space):
@@ -291,23 +294,23 @@ void ffc_batch_destroy(ffc_batch* b);
  *   row_ptr  device int64 [n_dof + 1], col device int32 [nnz]: the pattern of
  *            ffc_csr_pattern (columns sorted within each row), copied to the device
  * The plan stores, per chunk, the chunk's pairs grouped by local index i1 as
- * e * n_local + i1, and for every pair and local column i2 the position of column
- * dofmap[e][i2] inside the chunk (uint16). It owns
+ * e * n_local + i1, the work units (pieces of one group), and for every pair and local
+ * column i2 the position of column dofmap[e][i2] inside the chunk (uint16). It owns
  * about n_elem * n_local * (2 * n_local + 4) + n_dof * 8 bytes of device memory plus an
  * [n_elem][12]-double geometry scratch (ffc_row_plan_layout reports the exact figure);
  * row_ptr is copied, so dofmap, row_ptr and col may be freed afterwards. The call
  * synchronises `stream`.
  * Errors: FFC_EBOUNDS for a dof id outside [0, n_dof) or a (row, col) pair of a cell
  * missing from the pattern; FFC_EINVAL for n_local outside [2, 64], a row with more than
- * 4096 entries or more than 512 pairs, a row_ptr that is not monotone within [0, nnz], or
- * n_elem * n_local >= 2^31.
+ * 4096 entries or more than 320 pairs (a dof shared by more than 320 cells), a row_ptr
+ * that is not monotone within [0, nnz], or n_elem * n_local >= 2^31.
  */
 int ffc_row_plan_create(int64_t n_elem, int n_local, const int32_t* dofmap, int64_t n_dof, const int64_t* row_ptr,
                         const int32_t* col, int64_t nnz, void* stream, ffc_row_plan** out);
 /* Rows, stored entries, longest row and most cells sharing one dof. */
 int ffc_row_plan_info(const ffc_row_plan* p, int64_t* n_dof, int64_t* nnz, int* max_row, int* max_incidence);
 /* Chunks, entries and pairs of the largest chunk, bytes of the largest chunk's plan data
- * (class offsets, pairs and positions) and the plan's device memory in bytes. Any output
+ * (work units, pairs and positions) and the plan's device memory in bytes. Any output
  * pointer may be NULL. */
 int ffc_row_plan_layout(const ffc_row_plan* p, int64_t* n_chunks, int* max_chunk_values, int* max_chunk_pairs,
                         int* max_region_bytes, int64_t* device_bytes);

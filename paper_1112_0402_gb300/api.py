@@ -6,7 +6,7 @@ library's CUDA kernels). PyTorch provides device memory and streams.
     row_ptr, col, slot = csr_pattern(dofmap, n_dof)       # host, setup
     assemble(form, cells, vertices, slot_dev, csr_val)    # csr_val[slot] += A^K
     plan = RowPlan(dofmap_dev, n_dof, row_ptr_dev, col_dev)  # mass / Poisson, once per mesh
-    assemble_rows(form, plan, cells, vertices, csr_val)   # csr_val = A (row-owner, exact sums)
+    assemble_rows(form, plan, cells, vertices, csr_val)   # csr_val = A (row-owner, fixed-point sums)
 
 A linear form (SOURCE, rank 1) has element vectors [n_elem, n]; its assembly adds
 them into a global vector, with the dof map in place of the slots:

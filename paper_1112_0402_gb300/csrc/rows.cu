@@ -5,40 +5,42 @@
 // matrix must be zeroed first. Here the same sums are taken row by row instead: the
 // entries of global row r receive exactly the rows A^K[i1][:] of the cells K that hold r
 // as local dof i1 (the "pairs" (K, i1) of row r). The rows are cut into chunks of
-// consecutive rows (at most 4096 values and 512 pairs each); a CTA sums one chunk at a
+// consecutive rows (at most 4096 values and 320 pairs each); a CTA sums one chunk at a
 // time in shared memory, computing every element-tensor entry on the fly from a per-cell
 // geometry tensor G_K (A^K[i1][i2] = sum_alpha A0[i1][i2][alpha] G_K[alpha], Section
 // 3.2), and then writes the chunk's CSR values once, in order: no global atomics, no
 // zeroing pass, every value written exactly once.
 //
 // Work layout inside a chunk. The plan stores each chunk's pairs grouped by local index
-// i1 (a "class"; within a class the pairs of different rows alternate) and, per pair,
-// the chunk-relative positions of its columns i2 = 0..n-1. A warp takes a unit of up to
-// a few dozen pairs of one class: the reference-tensor entries A0[i1][i2][.] its lanes
+// i1 (a "class"; within a class the pairs of different rows alternate), the work units
+// (pieces of a class), and per pair the chunk-relative positions of its columns i2 =
+// 0..n-1. A warp takes one unit: the reference-tensor entries A0[i1][i2][.] its lanes
 // need stay in registers for the whole unit, each pair's G_K is a shared-memory
 // broadcast, and one warp instruction adds the contributions of one element-tensor row
 // (or of a few rows of different global rows), whose positions are distinct: the
 // shared-memory atomics meet no same-address conflicts and few bank conflicts. For n
 // >= 32 lane l takes column l of every pair (and the columns beyond 32 are spread over the
 // lanes); for n < 32 the unit's (pair, column) items are spread over the lanes in order.
-// The next chunk's plan data and geometry tensors are copied into a second shared-memory
-// buffer with cp.async while the current chunk is summed.
+// Later chunks' plan data and geometry tensors are staged in shared memory with cp.async
+// while the current chunk is summed and the previous one written out.
 //
-// Exact accumulation. The sums are kept in fixed point with one unit per chunk:
-// u = 2^(eb - 62), where 2^(eb-1) bounds every partial sum of every entry of the chunk
-// (the largest |contribution| bound of a pair, a0max[i1] * sum|G_K|, times the largest
-// number of pairs of one row). A contribution x is split into three signed digits on the
-// grids 2^(eb-20), 2^(eb-41), 2^(eb-62), each found by adding and subtracting the FP32
-// constant 1.5 * 2^(grid + 23) (the addition rounds to the grid; the subtraction is
-// exact), and each digit is added with a 32-bit shared-memory atomic into its own array:
-// 32-bit shared atomics run about seven times faster than 64-bit ones on this GPU, and a
-// digit sum of up to 1023 contributions cannot overflow 32 bits. Chunks whose bound lies
-// outside the range of those FP32 constants, and FP64 contributions, take an integer
-// conversion instead (truncation, error < u). The value of an entry is
-// (S1 2^42 + S2 2^21 + S3) u, rounded once to FP64 (nearest even) in integer arithmetic.
-// Integer addition is exact and associative, so the result does not depend on the order
-// of the additions: per entry |result - exact sum of the contributions| <= m u + half an
-// ulp of the result (m contributions), and the matrix is reproducible bit for bit.
+// Fixed-point accumulation. The sums are kept in fixed point with one unit per chunk and
+// form, where 2^(eb-1) bounds every partial sum of every entry of the chunk (the largest
+// |contribution| bound of a pair, a0max[i1] * sum|G_K|, times the largest number of pairs
+// of one row). A contribution x is split into signed digits on the grids 2^(eb-20),
+// 2^(eb-41) (and 2^(eb-62) for FP64 contributions, u = 2^(eb-62); FP32 contributions,
+// 24 bits each, use the first two, u = 2^(eb-41)), each found by adding and subtracting
+// the FP32 constant 1.5 * 2^(grid + 23) (the addition rounds to the grid; the
+// subtraction is exact), and each digit is added with a 32-bit shared-memory atomic into
+// its own array: 32-bit shared atomics run about seven times faster than 64-bit ones on
+// this GPU, and a digit sum of up to 1023 contributions cannot overflow 32 bits. Chunks
+// whose bound lies outside the range of those FP32 constants, and FP64 contributions,
+// take an integer conversion instead (truncation, error < u). The value of an entry is
+// the digit sums' value in units u, rounded once to FP64 in integer arithmetic (the FP64
+// pipe's integer conversion takes half of them where it is exact). Integer addition is
+// exact and associative, so the result does not depend on the order of the additions:
+// per entry |result - exact sum of the contributions| <= m u / 2 + an ulp of the result
+// (m contributions), and the matrix is reproducible bit for bit.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -55,17 +57,36 @@ namespace ffc {
 namespace {
 
 constexpr int ROWS_VMAX = 4096;           // values of one chunk (shared-memory accumulators)
+constexpr int ROWS_VSTRIDE = ROWS_VMAX + 4;  // ints of one digit array: a chunk's values, shifted by 0 or 1
 constexpr int ROWS_PMAX = 320;            // pairs of one chunk
 constexpr int ROWS_MAX_INCIDENCE = 1023;  // digit sums of 21-bit digits stay within 32 bits
 constexpr int ROWS_MAX_LOCAL = 64;        // local dofs per cell the plan carries
 
+// Pairs of one work unit: a warp takes the pairs of one class i1 in pieces of at most this
+// many (larger pieces for small element tensors, whose units hold several pairs per step;
+// short ones where a lane takes a column of a pair, so that an iteration's tasks are many
+// and short and its warps finish together).
+#ifndef ROWS_UMAX_WIDE
+#define ROWS_UMAX_WIDE 16
+#endif
+__host__ __device__ constexpr int rows_umax(int n) { return n <= 6 ? 32 : (n < 32 ? 16 : ROWS_UMAX_WIDE); }
+// Work units a chunk of P pairs can have: every non-empty class gives ceil(m / umax) <=
+// m / umax + 1 pieces.
+__host__ __device__ constexpr int region_unit_slots(int n, long long P) {
+  return int((n < P ? n : P) + P / rows_umax(n));
+}
+
 // A chunk's region of plan data (16-byte aligned, a multiple of 16 bytes):
-//   uint16 cls[n + 1]  first pair of each class i1 (chunk-relative), padded to 4 bytes
+//   uint32 n_units
+//   uint32 unit[region_unit_slots(n, P)]  work units i1 | k0 << 7 | k1 << 19: pairs
+//                                        [k0, k1) of class i1, in class order
 //   int32  pr[P]       the pairs e * n + i1, grouped by class
 //   uint16 pos[P][n]   chunk-relative value index of column i2 of each pair
-__host__ __device__ constexpr int region_cls_bytes(int n) { return ((n + 1) * 2 + 3) / 4 * 4; }
+__host__ __device__ constexpr long long region_pr_offset(int n, long long P) {
+  return 4ll * (1 + region_unit_slots(n, P));
+}
 __host__ __device__ constexpr long long region_bytes(int n, long long P) {
-  return (region_cls_bytes(n) + 4 * P + 2 * P * n + 15) / 16 * 16;
+  return (region_pr_offset(n, P) + 4 * P + 2 * P * n + 15) / 16 * 16;
 }
 
 }  // namespace
@@ -207,8 +228,9 @@ __global__ void plan_fill(const int32_t* __restrict__ dofmap, long long total, l
 
 // One thread per chunk: the chunk's pairs grouped by class i1; within a class ordered by
 // (rank of the pair among the class's pairs of its row, row, cell), so consecutive pairs
-// of a class belong to different rows where the class has several. Writes the class
-// offsets and the ordered pairs into the chunk's region. `key` is scratch [total].
+// of a class belong to different rows where the class has several. Writes the ordered
+// pairs and the work units (each class cut into pieces of at most rows_umax(n) pairs)
+// into the chunk's region. `key` is scratch [total].
 __global__ void plan_sort(const int32_t* __restrict__ dofmap, const int32_t* __restrict__ chunk_row,
                           const int32_t* __restrict__ chunk_pair, const int64_t* __restrict__ chunk_off,
                           long long n_chunks, int n, const int32_t* __restrict__ inc_tmp,
@@ -219,8 +241,8 @@ __global__ void plan_sort(const int32_t* __restrict__ dofmap, const int32_t* __r
     const int r0 = chunk_row[c];
     const int p0 = chunk_pair[c], P = chunk_pair[c + 1] - p0;
     unsigned char* reg = region + chunk_off[c];
-    uint16_t* cls = reinterpret_cast<uint16_t*>(reg);
-    int32_t* pr = reinterpret_cast<int32_t*>(reg + region_cls_bytes(n));
+    uint32_t* unit = reinterpret_cast<uint32_t*>(reg);
+    int32_t* pr = reinterpret_cast<int32_t*>(reg + region_pr_offset(n, P));
     unsigned long long* kk = key + p0;
     // key (i1, row - r0, e) of each pair (i1 < 64, row - r0 < 2^16, e < 2^30), by insertion
     for (int j = 0; j < P; ++j) {
@@ -235,15 +257,13 @@ __global__ void plan_sort(const int32_t* __restrict__ dofmap, const int32_t* __r
       }
       kk[q] = kv;
     }
-    // class offsets
-    int cnt = 0;
-    for (int i = 0; i <= n; ++i) {
-      while (cnt < P && int(kk[cnt] >> 58) < i) ++cnt;
-      cls[i] = uint16_t(cnt);
-    }
-    // within each class: the pairs of a row get ranks 0, 1, ...; emit by (rank, row, e)
+    // each class: its pairs (the pairs of a row get ranks 0, 1, ..., emitted by (rank,
+    // row, e)) and its work units
+    const int umax = rows_umax(n);
+    int a = 0, n_units = 0;
     for (int i = 0; i < n; ++i) {
-      const int a = cls[i], b = cls[i + 1];
+      int b = a;
+      while (b < P && int(kk[b] >> 58) == i) ++b;
       int out = a;
       for (int rank = 0; out < b; ++rank) {
         int rr = -1, run = 0;
@@ -254,7 +274,11 @@ __global__ void plan_sort(const int32_t* __restrict__ dofmap, const int32_t* __r
           if (run == rank) pr[out++] = int32_t((kk[j] & E_MASK) * n + i);
         }
       }
+      for (int k0 = a; k0 < b; k0 += umax)
+        unit[1 + n_units++] = uint32_t(i) | (uint32_t(k0) << 7) | (uint32_t(min(k0 + umax, b)) << 19);
+      a = b;
     }
+    unit[0] = uint32_t(n_units);
   }
 }
 
@@ -269,8 +293,8 @@ __global__ void plan_positions(const int32_t* __restrict__ dofmap, int n, const 
     const int P = chunk_pair[c + 1] - chunk_pair[c];
     const long long base = row_ptr[r0];
     unsigned char* reg = region + chunk_off[c];
-    const int32_t* pr = reinterpret_cast<const int32_t*>(reg + region_cls_bytes(n));
-    uint16_t* pos = reinterpret_cast<uint16_t*>(reg + region_cls_bytes(n) + 4ll * P);
+    const int32_t* pr = reinterpret_cast<const int32_t*>(reg + region_pr_offset(n, P));
+    uint16_t* pos = reinterpret_cast<uint16_t*>(reg + region_pr_offset(n, P) + 4ll * P);
     for (int w = threadIdx.x; w < P * n; w += blockDim.x) {
       const int k = w / n, i2 = w - k * n;
       const int t = pr[k];
@@ -553,6 +577,13 @@ struct RowsParams {
 
 __host__ __device__ constexpr int gcd_c(int a, int b) { return b == 0 ? a : gcd_c(b, a % b); }
 
+#ifndef ROWS_WB
+#define ROWS_WB 256
+#endif
+#ifndef ROWS_TB
+#define ROWS_TB 256
+#endif
+
 template <int D, int FORM, int Q>
 struct RowsCfg {
   static constexpr int N = nscalar(D, Q);
@@ -560,12 +591,12 @@ struct RowsCfg {
   static constexpr int W = MAIN ? N - 32 : N;        // columns spread over the lanes in order
   static constexpr int I0 = MAIN ? 32 : 0;           // first of those columns
   static constexpr int PER = W > 0 ? W / gcd_c(32, W) : 1;  // steps after which a lane's column repeats
-  static constexpr int UMAX = N <= 6 ? 32 : 16;      // pairs of one work unit
+  static constexpr int UMAX = rows_umax(N);         // pairs of one work unit
   static constexpr int NP = D * (D + 1) / 2;
   static constexpr int NA = FORM == ROWS_PAIR ? 1 + NP : (FORM == FFC_POISSON ? NP : 1);  // A0 values per entry
   static constexpr int NG = FORM == FFC_MASS ? 1 : 8;  // G_K values read per pair (vector loads)
-  static constexpr int TB = 256;        // items of one task of the columns beyond the first 32
-  static constexpr int WB = 256;        // values of one write-out task
+  static constexpr int TB = ROWS_TB;    // items of one task of the columns beyond the first 32
+  static constexpr int WB = ROWS_WB;    // digit indices of one write-out task
 };
 
 // A0 entry (i1, i2) of the kernel's form(s), in the order the contraction uses, from the
@@ -626,42 +657,51 @@ __device__ __forceinline__ T warp_max(T v) {
   return v;
 }
 
-// Adds one entry's contributions (digits) at chunk position q; acc is [NF][NDIG][ROWS_VMAX].
+// Adds one entry's contributions (digits) at chunk position q; base[f] is form f's first
+// digit array (the arrays of one form ROWS_VSTRIDE ints apart).
 template <bool MAGIC, int NF, int NDIG, typename T>
-__device__ __forceinline__ void add_digits(int* acc, const Digits<NDIG> (&dig)[NF], const T (&v)[NF], int q) {
+__device__ __forceinline__ void add_digits(int* const (&base)[NF], const Digits<NDIG> (&dig)[NF], const T (&v)[NF],
+                                           int q) {
 #pragma unroll
   for (int f = 0; f < NF; ++f) {
     int d[NDIG];
     dig[f].template split<MAGIC>(v[f], d);
-    int* a = acc + f * NDIG * ROWS_VMAX + q;
+    int* a = base[f] + q;
 #pragma unroll
-    for (int j = 0; j < NDIG; ++j) atomicAdd(a + j * ROWS_VMAX, d[j]);
+    for (int j = 0; j < NDIG; ++j) atomicAdd(a + j * ROWS_VSTRIDE, d[j]);
   }
 }
 
+// Positions come from a validated plan (every (row, col) pair was found in the pattern when
+// the plan was built, so q < V); the mask only keeps a shared-memory index in range.
+__device__ __forceinline__ int rows_pos(int q) { return q & (ROWS_VMAX - 1); }
+
+#ifndef ROWS_UNROLL
+#define ROWS_UNROLL 2
+#endif
+constexpr int kRowsUnroll = ROWS_UNROLL;  // pairs of a work unit in flight per loop step
+
 // One work unit (class i1, pairs [k0, k1)) of a chunk, by one warp: for n >= 32 lane l takes
 // column l of every pair (the A0 column in registers), for n < 32 the unit's (pair, column)
-// items in order. Returns true if a position was out of range.
+// items in order.
 template <class K, int FORM, int NF, int GS, bool MAGIC, int NDIG, typename T>
-__device__ __forceinline__ bool unit_task(unsigned ud, const T* gs, const uint16_t* pos, int* acc,
-                                          const Digits<NDIG> (&dig)[NF], const T* A0a, const T* A0b, int V) {
+__device__ __forceinline__ void unit_task(unsigned ud, const T* gs, const uint16_t* pos, int* const (&base)[NF],
+                                          const Digits<NDIG> (&dig)[NF], const T* A0a, const T* A0b) {
   constexpr int N = K::N, NA = K::NA, NG = K::NG;
   const int lane = threadIdx.x & 31;
   const int i1 = int(ud & 127u), k0 = int((ud >> 7) & 4095u), k1 = int(ud >> 19);
-  bool bad = false;
   if constexpr (K::MAIN) {
     T am[NA];
     load_a0<FORM, N, NA, K::NP, T>(A0a, A0b, i1, lane, am);
     const uint16_t* pl = pos + lane;
-#pragma unroll 2
+#pragma unroll kRowsUnroll
     for (int k = k0; k < k1; ++k) {
       T g[NG];
       load_gk<NG, T>(gs + k * GS, g);
-      const int q = pl[k * N];
+      const int q = rows_pos(pl[k * N]);
       T v[NF];
       contract<FORM, NA, NG, NF, T>(g, am, v);
-      bad |= q >= V;
-      add_digits<MAGIC, NF, NDIG, T>(acc, dig, v, q < V ? q : 0);
+      add_digits<MAGIC, NF, NDIG, T>(base, dig, v, q);
     }
   } else {
     T af[K::PER][NA];
@@ -677,25 +717,23 @@ __device__ __forceinline__ bool unit_task(unsigned ud, const T* gs, const uint16
           const int i2 = K::I0 + f % K::W;
           T g[NG];
           load_gk<NG, T>(gs + kk * GS, g);
-          const int q = pos[kk * N + i2];
+          const int q = rows_pos(pos[kk * N + i2]);
           T v[NF];
           contract<FORM, NA, NG, NF, T>(g, af[s], v);
-          bad |= q >= V;
-          add_digits<MAGIC, NF, NDIG, T>(acc, dig, v, q < V ? q : 0);
+          add_digits<MAGIC, NF, NDIG, T>(base, dig, v, q);
         }
       }
     }
   }
-  return bad;
 }
 
 // Items [b * TB, (b + 1) * TB) of the columns beyond the first 32 (n > 32), packed over
 // the lanes: item f is pair f / W, column 32 + f % W.
 template <class K, int FORM, int NF, int GS, bool MAGIC, int NDIG, typename T>
-__device__ __forceinline__ bool tail_task(int b, int P, const int32_t* pr, const T* gs, const uint16_t* pos, int* acc,
-                                          const Digits<NDIG> (&dig)[NF], const T* A0a, const T* A0b, int V) {
+__device__ __forceinline__ void tail_task(int b, int P, const int32_t* pr, const T* gs, const uint16_t* pos,
+                                          int* const (&base)[NF], const Digits<NDIG> (&dig)[NF], const T* A0a,
+                                          const T* A0b) {
   constexpr int N = K::N, NA = K::NA, NG = K::NG;
-  bool bad = false;
   if constexpr (K::MAIN && K::W > 0) {
     const int total = P * K::W, end = min(total, (b + 1) * K::TB);
     for (int f = b * K::TB + (threadIdx.x & 31); f < end; f += 32) {
@@ -704,31 +742,70 @@ __device__ __forceinline__ bool tail_task(int b, int P, const int32_t* pr, const
       T a[NA], g[NG];
       load_a0<FORM, N, NA, K::NP, T>(A0a, A0b, i1, i2, a);
       load_gk<NG, T>(gs + k * GS, g);
-      const int q = pos[k * N + i2];
+      const int q = rows_pos(pos[k * N + i2]);
       T v[NF];
       contract<FORM, NA, NG, NF, T>(g, a, v);
-      bad |= q >= V;
-      add_digits<MAGIC, NF, NDIG, T>(acc, dig, v, q < V ? q : 0);
+      add_digits<MAGIC, NF, NDIG, T>(base, dig, v, q);
     }
   }
-  return bad;
 }
 
-// Per-chunk state prepared one iteration ahead (three slots, by chunk index mod 3).
+// Per-chunk state prepared one iteration ahead (three slots, by chunk index mod 3), read by
+// every warp of the iteration that uses it.
+template <int NDIG>
 struct RowsSlot {
-  int eb[2];      // fixed-point exponent of each form
-  int finite[2];  // the form's bound is finite
-  int n_units;
+  Digits<NDIG> dig[2];  // fixed-point digits of each form (from its bound's exponent)
+  int finite[2];        // the form's bound is finite
+  int shift[2];         // chunk position q of form f sits at digit index q + shift[f]: the
+                        // output address of index 0 is then 16-byte aligned
+  int n_units, n_items;  // work units, and units + column-tail blocks
+  int P, V;              // pairs and CSR values of the chunk
 };
 
+// mbarrier helpers of the staging copies: cp.async issued by one warp, tracked by an
+// mbarrier of arrival count 32 (each lane arrives when its own copies have landed)
+__device__ __forceinline__ uint32_t rows_smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void rows_bar_init(unsigned long long* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(rows_smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void rows_cp_async_arrive(unsigned long long* bar) {
+  asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(rows_smem_u32(bar)) : "memory");
+}
+// Bounded wait for the completion of the phase of parity `parity`: false after ~2^22 polls.
+__device__ __forceinline__ bool rows_bar_wait(unsigned long long* bar, unsigned parity) {
+  const uint32_t addr = rows_smem_u32(bar);
+  for (uint32_t it = 0; it < (1u << 22); ++it) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(addr), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+
+// Values (of each 4 consecutive ones a lane converts) that take the FP64 pipe's integer
+// conversion where it is exact: bit c set for value c.
+#ifndef ROWS_FP64_MASK
+#define ROWS_FP64_MASK 0xA
+#endif
+
 // The chunks of this CTA are c_i = blockIdx.x + i * gridDim.x. Iteration i is one queue of
-// independent warp tasks, handed out by a shared counter: four staging tasks (chunk i + 3's
-// plan region, chunk i + 2's geometry gather, chunk i + 5's extents, chunk i + 1's bounds
-// and work units), then the work units of chunk i (into accumulator buffer i % 2)
-// interleaved with the write-out blocks of chunk i - 1 (from the other buffer, which they
-// clear). Copies go through cp.async and are complete at the iteration's end, where one
-// CTA-wide barrier closes the iteration. Staging depths: regions 4 buffers (i .. i + 3),
-// geometry 3 (i .. i + 2), extents a ring of 8.
+// independent warp tasks, handed out by a shared counter: three staging tasks (chunk i + 3's
+// plan region, chunk i + 2's geometry and digits, chunk i + 5's extents), then the work
+// units of chunk i (into accumulator buffer i % 2) interleaved with the write-out blocks of
+// chunk i - 1 (from the other buffer, which they clear). The region copy is cp.async
+// tracked by an mbarrier that only its consumer (the geometry task, an iteration later)
+// waits for; the geometry task gathers the pairs' G_K, waits for its own copies, and
+// derives the chunk's fixed-point digits from the largest contribution bound. The work
+// units come with the plan. One CTA-wide barrier closes each iteration. Staging depths:
+// regions 4 buffers (i .. i + 3), geometry 3 (i .. i + 2), per-chunk state 4 slots
+// (i - 1 .. i + 2), extents a ring of 8. A wait that gives up sets FFC_FLAG_TIMEOUT and
+// ends the CTA's work after the iteration.
 // One CTA per SM: 32 warps for FP32 (64 registers a thread), 16 for FP64.
 template <int D, int FORM, int Q, typename T>
 __global__ void __launch_bounds__(sizeof(T) == 4 ? 1024 : 512, 1) rows_assemble(RowsParams p) {
@@ -736,25 +813,25 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 1024 : 512, 1) rows_assemble(
   using K = RowsCfg<D, FORM, Q>;
   constexpr int N = K::N, NF = C::NF, GS = C::GS, TH = sizeof(T) == 4 ? 1024 : 512;
   constexpr int NDIG = sizeof(T) == 4 ? 2 : 3;  // digits: 42-bit fixed point for FP32, 63-bit for FP64
-  constexpr int CB = region_cls_bytes(N);
-  constexpr int ACC = NF * NDIG * ROWS_VMAX;    // ints of one accumulator buffer
-  constexpr int NSPECIAL = 4;
+  constexpr int ACC = NF * NDIG * ROWS_VSTRIDE;  // ints of one accumulator buffer
+  constexpr int NSPECIAL = 3;
+  using Slot = RowsSlot<NDIG>;
   extern __shared__ __align__(16) unsigned char smem[];
-  int* acc = reinterpret_cast<int*>(smem);                                   // [2][NF][NDIG][ROWS_VMAX]
+  int* acc = reinterpret_cast<int*>(smem);                                   // [2][NF][NDIG][ROWS_VSTRIDE]
   unsigned char* rbuf = smem + size_t(2) * ACC * 4;                          // [4][rmax] plan regions
   T* gbuf = reinterpret_cast<T*>(rbuf + 4 * size_t(p.rmax));                 // [3][pmax][GS]
   T* a0max = gbuf + 3 * size_t(p.pmax) * GS;                                 // [NF][N]
-  unsigned* units = reinterpret_cast<unsigned*>(a0max + NF * N);             // [3][ROWS_PMAX]
-  RowsSlot* slot = reinterpret_cast<RowsSlot*>(units + 3 * ROWS_PMAX);       // [3]
-  int* tq = reinterpret_cast<int*>(slot + 3);                                // [2] task counters
+  Slot* slot = reinterpret_cast<Slot*>(a0max + NF * N);                      // [4]
+  int* tq = reinterpret_cast<int*>(slot + 4);                                // [2] task counters, [2] abort
   long long* meta = reinterpret_cast<long long*>(smem + p.meta_off);          // [8][8]: chunk extents
+  unsigned long long* rbar = reinterpret_cast<unsigned long long*>(meta + 64);  // [4] region copies
   const T* A0a = static_cast<const T*>(p.a0a);
   const T* A0b = static_cast<const T*>(p.a0b);
   const T* Gall = static_cast<const T*>(p.G);
   const int t = threadIdx.x, lane = t & 31, w = t >> 5;
   const T big = sizeof(T) == 4 ? T(FLT_MAX) : T(DBL_MAX);
-  const long long G1 = gridDim.x;
-  const long long n_iter = blockIdx.x < p.n_chunks ? (p.n_chunks - blockIdx.x + G1 - 1) / G1 : 0;
+  const int G1 = int(gridDim.x);
+  const int n_iter = blockIdx.x < p.n_chunks ? int((p.n_chunks - blockIdx.x + G1 - 1) / G1) : 0;
   // largest |A0| entry of each reference-tensor row i1 (the contribution bound's factor)
   for (int i = t; i < NF * N; i += TH) {
     const int f = i / N, i1 = i - f * N;
@@ -765,12 +842,13 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 1024 : 512, 1) rows_assemble(
     a0max[i] = m;
   }
   for (int i = 4 * t; i < 2 * ACC; i += 4 * TH) *reinterpret_cast<int4*>(acc + i) = make_int4(0, 0, 0, 0);
-  if (t < 2) tq[t] = 0;
+  if (t < 3) tq[t] = 0;
+  if (t < 4) rows_bar_init(rbar + t, 32);
   // extents of the chunk of iteration i, ring slot i % 8: pairs [0] .. [1), region bytes
   // [2] .. [3), CSR values [4] .. [5), most pairs of a row [6]
-  auto meta_at = [&](long long i) { return meta + (i & 7) * 8; };
-  auto meta_task = [&](long long i) {  // one warp
-    const long long c = blockIdx.x + i * G1;
+  auto meta_at = [&](int i) { return meta + (i & 7) * 8; };
+  auto meta_task = [&](int i) {  // one warp
+    const long long c = blockIdx.x + (long long)i * G1;
     if (i < n_iter && lane < 7) {
       long long v;
       if (lane < 2) v = p.chunk_pair[c + lane];
@@ -780,22 +858,36 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 1024 : 512, 1) rows_assemble(
       meta_at(i)[lane] = v;
     }
   };
-  auto region_at = [&](long long i) { return rbuf + size_t(i & 3) * p.rmax; };
+  auto region_at = [&](int i) { return rbuf + (i & 3) * p.rmax; };
+  auto geom_at = [&](unsigned i3) { return gbuf + i3 * p.pmax * GS; };  // i3 = i % 3
   // the plan region of chunk i (a multiple of 16 bytes, at most rmax) into buffer i % 4
-  auto region_task = [&](long long i) {  // one warp
+  auto region_task = [&](int i) {  // one warp
     const long long* m = meta_at(i);
     const unsigned char* src = p.region + m[2];
     unsigned char* dst = region_at(i);
     const int nb = int(m[3] - m[2]);
     for (int o = 16 * lane; o < nb; o += 512) cp_async16(dst + o, src + o);
+    rows_cp_async_arrive(rbar + (i & 3));
   };
-  // gather of the pairs' geometry tensors of chunk i into buffer i % 3 (one warp; the
-  // chunk's region is staged)
-  auto geometry_task = [&](long long i) {
+  // chunk i's geometry (one warp, once its region has landed): the pairs' G_K gathered
+  // into buffer i % 3, then its per-chunk state in slot i % 4: fixed-point digits from the
+  // bound (largest pair bound times the most pairs of a row), output alignment shifts,
+  // counts
+  auto geometry_task = [&](int i) {
+    Slot& sl = slot[i & 3];
+    if (!rows_bar_wait(rbar + (i & 3), unsigned(i >> 2) & 1u)) {
+      if (lane == 0) {
+        atomicOr(p.status, FFC_FLAG_TIMEOUT);
+        tq[2] = 1;
+        sl.n_units = sl.n_items = sl.P = sl.V = 0;
+      }
+      return;
+    }
     const long long* m = meta_at(i);
     const int P = int(m[1] - m[0]);
-    const int32_t* pr = reinterpret_cast<const int32_t*>(region_at(i) + CB);
-    T* gs = gbuf + size_t(i % 3) * p.pmax * GS;
+    const unsigned char* reg = region_at(i);
+    const int32_t* pr = reinterpret_cast<const int32_t*>(reg + region_pr_offset(N, P));
+    T* gs = geom_at(unsigned(i) % 3u);
     for (int k = lane; k < P; k += 32) {
       const T* src = Gall + (long long)(pr[k] / N) * GS;
       if constexpr (GS * sizeof(T) == 8) {
@@ -807,16 +899,9 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 1024 : 512, 1) rows_assemble(
                      reinterpret_cast<const unsigned char*>(src) + 16 * x);
       }
     }
-  };
-  // bounds (largest pair bound times the most pairs of a row) and work units of chunk i
-  auto prepare_task = [&](long long i) {  // one warp
-    const long long* m = meta_at(i);
-    const int P = int(m[1] - m[0]);
-    const unsigned char* reg = region_at(i);
-    const uint16_t* cls = reinterpret_cast<const uint16_t*>(reg);
-    const int32_t* pr = reinterpret_cast<const int32_t*>(reg + CB);
-    const T* gs = gbuf + size_t(i % 3) * p.pmax * GS;
-    RowsSlot& sl = slot[i % 3];
+    cp_async_commit();
+    cp_async_wait_all();
+    __syncwarp();
     T pb[NF];
 #pragma unroll
     for (int f = 0; f < NF; ++f) pb[f] = T(0);
@@ -831,130 +916,114 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 1024 : 512, 1) rows_assemble(
 #pragma unroll
     for (int f = 0; f < NF; ++f) {
       const T bnd = warp_max(pb[f]) * T(m[6]);
-      if (lane == 0) {
+      if (lane == f) {
         sl.finite[f] = bnd <= big;
-        sl.eb[f] = bnd <= big ? bound_exponent(bnd) : 0;
+        Digits<NDIG> dg;
+        dg.init(bnd <= big ? bound_exponent(bnd) : 0);
+        sl.dig[f] = dg;
+        const double* out = (f == 0 ? p.out_a : p.out_b) + m[4];
+        sl.shift[f] = int((reinterpret_cast<uintptr_t>(out) >> 3) & 1);
       }
     }
-    // work units: pieces of at most UMAX pairs of one class (lane: classes lane, lane + 32)
-    int cnt[2], first[2], n_u = 0;
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int ii = lane + 32 * h;
-      first[h] = ii < N ? int(cls[ii]) : 0;
-      const int mm = ii < N ? int(cls[ii + 1]) - first[h] : 0;
-      cnt[h] = (mm + K::UMAX - 1) / K::UMAX;
-      n_u += cnt[h];
+    if (lane == 31) {
+      const int nu = int(*reinterpret_cast<const uint32_t*>(reg));
+      sl.n_units = nu;
+      sl.n_items = nu + (K::MAIN && K::W > 0 ? (P * K::W + K::TB - 1) / K::TB : 0);
+      sl.P = P;
+      sl.V = int(m[5] - m[4]);
     }
-    int incl = n_u;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int y = __shfl_up_sync(0xffffffffu, incl, o);
-      if (lane >= o) incl += y;
-    }
-    int u = incl - n_u;
-    unsigned* un = units + (i % 3) * ROWS_PMAX;
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int ii = lane + 32 * h;
-      if (ii < N) {
-        const int end = int(cls[ii + 1]);
-        for (int j = 0; j < cnt[h]; ++j, ++u) {
-          const int k0 = first[h] + j * K::UMAX;
-          un[u] = unsigned(ii) | (unsigned(k0) << 7) | (unsigned(min(k0 + K::UMAX, end)) << 19);
-        }
-      }
-    }
-    if (lane == 31) sl.n_units = incl;
   };
-  // values [b * WB, (b + 1) * WB) of chunk i from accumulator buffer i % 2 (cleared), one
-  // warp; lanes take consecutive pairs of values (16-byte stores) from the first 16-byte
-  // boundary, the value before it goes with block 0
-  auto write_task = [&](long long i, int b) {
-    const long long* m = meta_at(i);
-    const long long v0 = m[4];
-    const int V = int(m[5] - v0);
-    const RowsSlot& sl = slot[i % 3];
+  // digit indices [b * WB, (b + 1) * WB) of chunk i from accumulator buffer i % 2 (cleared),
+  // one warp: each lane converts four consecutive indices per step and stores them as two
+  // 16-byte pairs (index x is output value x - shift, and output index 0 is 16-byte
+  // aligned); where the FP64 pipe's conversion is exact, the values of ROWS_FP64_MASK take
+  // it, so two pipes share the conversions
+  auto write_task = [&](int i, int b) {
+    const Slot& sl = slot[i & 3];
+    const long long v0 = meta_at(i)[4];
+    const int V = sl.V;
     int* ab = acc + (i & 1) * ACC;
     const double nan = __longlong_as_double(0x7ff8000000000000ll);
 #pragma unroll
     for (int f = 0; f < NF; ++f) {
-      Digits<NDIG> dg;
-      dg.init(sl.eb[f]);
+      const Digits<NDIG> dg = sl.dig[f];
       const bool fin = sl.finite[f] != 0;
-      double* out = (f == 0 ? p.out_a : p.out_b) + v0;
-      int* a = ab + f * NDIG * ROWS_VMAX;
-      // the second value of each pair goes through the FP64 pipe where that is exact
+      const int sh = sl.shift[f];
+      double* out = (f == 0 ? p.out_a : p.out_b) + v0 - sh;
+      int* a = ab + f * NDIG * ROWS_VSTRIDE;
       const bool split_pipes = NDIG == 2 && fin && dg.fp64_ok();
-      auto value = [&](int j, bool fp64) {
-        int sd[NDIG];
+      const int hi = V + sh, end = min(hi, (b + 1) * K::WB);
+      for (int x = b * K::WB + 4 * lane; x < end; x += 128) {
+        int4 dd[NDIG];
 #pragma unroll
         for (int d = 0; d < NDIG; ++d) {
-          sd[d] = a[j + d * ROWS_VMAX];
-          a[j + d * ROWS_VMAX] = 0;
+          dd[d] = *reinterpret_cast<const int4*>(a + d * ROWS_VSTRIDE + x);
+          *reinterpret_cast<int4*>(a + d * ROWS_VSTRIDE + x) = make_int4(0, 0, 0, 0);
         }
-        if constexpr (NDIG == 2)
-          if (fp64 && split_pipes) return dg.value_fp64(sd);
-        return fin ? dg.value(sd) : nan;
-      };
-      const int j0 = int((reinterpret_cast<uintptr_t>(out) >> 3) & 1);
-      if (b == 0 && lane == 0 && j0 == 1 && V > 0) __stcs(out, value(0, false));
-      const int end = min(V, j0 + (b + 1) * K::WB);
-#pragma unroll 2
-      for (int j = j0 + b * K::WB + 2 * lane; j < end; j += 64) {
-        const double x = value(j, false);
-        if (j + 1 < end) {
-          const double y = value(j + 1, true);
-          __stcs(reinterpret_cast<double2*>(out + j), make_double2(x, y));
-        } else {
-          __stcs(out + j, x);
+        double r[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          int sd[NDIG];
+#pragma unroll
+          for (int d = 0; d < NDIG; ++d) sd[d] = c == 0 ? dd[d].x : c == 1 ? dd[d].y : c == 2 ? dd[d].z : dd[d].w;
+          if constexpr (NDIG == 2) {
+            if (((ROWS_FP64_MASK >> c) & 1) && split_pipes) {
+              r[c] = dg.value_fp64(sd);
+              continue;
+            }
+          }
+          r[c] = fin ? dg.value(sd) : nan;
+        }
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int y = x + 2 * h;
+          if (y >= sh && y + 1 < hi) {
+            __stcs(reinterpret_cast<double2*>(out + y), make_double2(r[2 * h], r[2 * h + 1]));
+          } else {
+            if (y >= sh && y < hi) __stcs(out + y, r[2 * h]);
+            if (y + 1 >= sh && y + 1 < hi) __stcs(out + y + 1, r[2 * h + 1]);
+          }
         }
       }
     }
   };
   // ---- prologue: extents of iterations 0..4; regions of chunks 0..2; geometry of chunks
-  // 0..1; chunk 0 prepared
+  // 0..1 (each waits for what it reads)
   if (w < 5) meta_task(w);
   __syncthreads();
   if (w < 3 && w < n_iter) region_task(w);
-  cp_async_commit();
-  cp_async_wait_all();
+  if (w == 3 && n_iter > 0) geometry_task(0);
+  if (w == 4 && n_iter > 1) geometry_task(1);
   __syncthreads();
-  if (w < 2 && w < n_iter) geometry_task(w);
-  cp_async_commit();
-  cp_async_wait_all();
-  __syncthreads();
-  if (w == 0 && n_iter > 0) prepare_task(0);
-  __syncthreads();
-  bool bad = false;
-  for (long long i = 0; i <= n_iter; ++i) {
+  unsigned i3 = 0;  // i % 3
+  for (int i = 0; i <= n_iter && tq[2] == 0; ++i, i3 = i3 == 2 ? 0 : i3 + 1) {
     if (t == 0) tq[(i + 1) & 1] = 0;  // the next iteration's queue (last used two iterations ago)
     // this iteration's work: units (and column tails) of chunk i, write-out blocks of chunk i - 1
-    int nI = 0, nU = 0, nW = 0, P = 0, V = 0;
+    const Slot& cur = slot[i & 3];
+    int nI = 0, nU = 0, nW = 0, P = 0;
     if (i < n_iter) {
-      const long long* m = meta_at(i);
-      P = int(m[1] - m[0]);
-      V = int(m[5] - m[4]);
-      nU = slot[i % 3].n_units;
-      nI = nU + (K::MAIN && K::W > 0 ? (P * K::W + K::TB - 1) / K::TB : 0);
+      P = cur.P;
+      nU = cur.n_units;
+      nI = cur.n_items;
     }
-    if (i >= 1) {
-      const long long* m = meta_at(i - 1);
-      nW = (int(m[5] - m[4]) + K::WB - 1) / K::WB + 1;  // one more for the value before the 16-byte boundary
-    }
+    if (i >= 1) nW = (slot[(i - 1) & 3].V + 1 + K::WB - 1) / K::WB;  // indices up to V + shift
     const int nMix = 2 * min(nI, nW), n_tasks = NSPECIAL + nI + nW;
     const unsigned char* reg = region_at(i);
-    const int32_t* pr = reinterpret_cast<const int32_t*>(reg + CB);
-    const uint16_t* pos = reinterpret_cast<const uint16_t*>(reg + CB + 4 * P);
-    const T* gs = gbuf + size_t(i % 3) * p.pmax * GS;
+    const unsigned* un = reinterpret_cast<const unsigned*>(reg) + 1;
+    const int32_t* pr = reinterpret_cast<const int32_t*>(reg + region_pr_offset(N, P));
+    const uint16_t* pos = reinterpret_cast<const uint16_t*>(reg + region_pr_offset(N, P) + 4 * P);
+    const T* gs = geom_at(i3);
     int* ab = acc + (i & 1) * ACC;
     Digits<NDIG> dig[NF];
+    int* base[NF];
     bool magic = sizeof(T) == 4;
-    if (i < n_iter) {
 #pragma unroll
-      for (int f = 0; f < NF; ++f) {
-        dig[f].init(slot[i % 3].eb[f]);
+    for (int f = 0; f < NF; ++f) {
+      base[f] = ab + f * NDIG * ROWS_VSTRIDE;
+      if (i < n_iter) {
+        dig[f] = cur.dig[f];
         magic = magic && dig[f].magic;
+        base[f] += cur.shift[f];
       }
     }
     for (;;) {
@@ -966,7 +1035,6 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 1024 : 512, 1) rows_assemble(
         if (k == 0 && i + 3 < n_iter) region_task(i + 3);
         if (k == 1 && i + 2 < n_iter) geometry_task(i + 2);
         if (k == 2) meta_task(i + 5);
-        if (k == 3 && i + 1 < n_iter) prepare_task(i + 1);
         continue;
       }
       k -= NSPECIAL;
@@ -982,22 +1050,20 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 1024 : 512, 1) rows_assemble(
       }
       if (item) {
         if (j < nU) {
-          const unsigned ud = units[(i % 3) * ROWS_PMAX + j];
-          bad |= magic ? unit_task<K, FORM, NF, GS, true, NDIG, T>(ud, gs, pos, ab, dig, A0a, A0b, V)
-                       : unit_task<K, FORM, NF, GS, false, NDIG, T>(ud, gs, pos, ab, dig, A0a, A0b, V);
+          if (magic) unit_task<K, FORM, NF, GS, true, NDIG, T>(un[j], gs, pos, base, dig, A0a, A0b);
+          else unit_task<K, FORM, NF, GS, false, NDIG, T>(un[j], gs, pos, base, dig, A0a, A0b);
         } else {
-          bad |= magic ? tail_task<K, FORM, NF, GS, true, NDIG, T>(j - nU, P, pr, gs, pos, ab, dig, A0a, A0b, V)
-                       : tail_task<K, FORM, NF, GS, false, NDIG, T>(j - nU, P, pr, gs, pos, ab, dig, A0a, A0b, V);
+          if (magic) tail_task<K, FORM, NF, GS, true, NDIG, T>(j - nU, P, pr, gs, pos, base, dig, A0a, A0b);
+          else tail_task<K, FORM, NF, GS, false, NDIG, T>(j - nU, P, pr, gs, pos, base, dig, A0a, A0b);
         }
       } else {
         write_task(i - 1, j);
       }
     }
-    cp_async_commit();
-    cp_async_wait_all();  // this thread's copies (region i + 3, geometry i + 2)
     __syncthreads();
   }
-  if (bad) atomicOr(p.status, FFC_FLAG_BOUNDS);
+  cp_async_commit();
+  cp_async_wait_all();  // copies of chunks this CTA no longer needed (a wait that gave up)
 }
 
 template <int D, int FORM, int Q, typename T>
@@ -1009,15 +1075,19 @@ int launch_rows_t(const ffc_row_plan* plan, const void* a0a, const void* a0b, do
   using K = RowsCfg<D, FORM, Q>;
   constexpr int NDIG = sizeof(T) == 4 ? 2 : 3;
   const int rmax = std::max(plan->max_region, 16);
-  const size_t meta_off = (2 * size_t(C::NF) * NDIG * ROWS_VMAX * 4 + 4 * size_t(rmax) +
-                           (3 * size_t(pmax) * C::GS + size_t(C::NF) * N) * sizeof(T) + 3 * ROWS_PMAX * 4 +
-                           3 * sizeof(RowsSlot) + 2 * 4 + 15) / 16 * 16;
-  const size_t smem = meta_off + 8 * 8 * sizeof(long long);
+  const size_t meta_off = (2 * size_t(C::NF) * NDIG * ROWS_VSTRIDE * 4 + 4 * size_t(rmax) +
+                           (3 * size_t(pmax) * C::GS + size_t(C::NF) * N) * sizeof(T) +
+                           4 * sizeof(RowsSlot<NDIG>) + 3 * 4 + 15) / 16 * 16;
+  const size_t smem = meta_off + 8 * 8 * sizeof(long long) + 4 * sizeof(unsigned long long);
   auto kern = rows_assemble<D, FORM, Q, T>;
   int dev = 0, smem_optin = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   if (smem > size_t(smem_optin)) return FFC_EUNSUPPORTED;  // the pair then runs as two single passes
+  if (plan->n_chunks > (long long)INT_MAX) {  // iteration counters are 32-bit
+    set_error("row-owner assembly: more than 2^31 - 1 chunks");
+    return FFC_EINVAL;
+  }
   int sms = 0, per_sm = 1;
   constexpr int TH = sizeof(T) == 4 ? 1024 : 512;
   if (launch_config(reinterpret_cast<const void*>(kern), TH, smem, -1, &sms, &per_sm) != FFC_OK)
