@@ -59,7 +59,8 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["tet_scalar", "tri_p1", "ns_vp2", "batched", "adjoint", "source", "rows"],
+    ap.add_argument("--workload", choices=["tet_scalar", "tri_p1", "ns_vp2", "batched", "adjoint", "source", "rows",
+                                           "quad_curved"],
                     default="tet_scalar",
                     help="tet_scalar is the headline; the others print their own line")
     ap.add_argument("--precision", default="fp32", help="contraction arithmetic of the headline step")
@@ -560,7 +561,7 @@ def main():
     torch.cuda.empty_cache()
     if detail is not None and not args.no_configs and world == 1:
         detail["configs"] = {}
-        for wl in ("tri_p1", "ns_vp2", "batched", "adjoint", "source"):
+        for wl in ("tri_p1", "ns_vp2", "batched", "adjoint", "source", "quad_curved"):
             detail["configs"][wl] = measure_other(F, args, device, wl)
             torch.cuda.empty_cache()
 
@@ -1069,6 +1070,76 @@ def measure_other(F, args, device, workload):
                     "clocks": clk, "gpu_launches": 2 * args.steps,
                     "cpu_baseline": {"value": rate, "unit": "elem/s", "cores": cores, "kind": "oracle",
                                      "sample": f"{S} cells"}, "detail": detail})
+    elif workload == "quad_curved":
+        # quadrature as a tensor contraction (Section 3.4): P2 Poisson on 40^3 x 6 curved
+        # (quadratic-geometry) tets, A~0 with a point index contracted with per-point G~_K;
+        # plus the same contraction on the affine cells of the headline mesh against the
+        # tensor representation (the paper's T_Q / T_T comparison, here on the GPU)
+        from synthetic import curved as CV
+
+        cm = CV.curved_mesh(3, 40 if args.n == 48 else args.n, eps=0.08)
+        cells = torch.as_tensor(cm.cells, device=device)
+        nodes = torch.as_tensor(cm.nodes, device=device)
+        qf = F.QForm(F.POISSON, F.TETRAHEDRON, 2, 2)
+        n = qf.n_local
+        detail = {"points": qf.n_points, "k_contract": qf.k_contract, "quad_degree": qf.quad_degree}
+        A64 = torch.empty((cm.n_elem, n, n), dtype=torch.float64, device=device)
+        detail["tabulate_fp64_ms"] = _timed(lambda: F.tabulate_quadrature(qf, cells, nodes, "fp64", out=A64),
+                                            args.steps, args.warmup) * 1e3
+        A32 = torch.empty((cm.n_elem, n, n), dtype=torch.float32, device=device)
+        clocks.start()
+        t = _timed(lambda: F.tabulate_quadrature(qf, cells, nodes, "fp32", out=A32), args.steps, args.warmup)
+        clk = clocks.stop()
+        assert F.status_poll() == 0
+        d = (A32.double() - A64).reshape(cm.n_elem, -1).norm(dim=1) / A64.reshape(cm.n_elem, -1).norm(dim=1)
+        detail["fp32_max_rel_err_vs_fp64"] = float(d.max())
+        del A64, A32
+        # executed FLOPs of the FP32 contraction (all n^2 entries) and of the FP64 one
+        # (entries i1 <= i2)
+        flops32 = 2.0 * n * n * qf.k_contract * cm.n_elem
+        flops64 = 2.0 * n * (n + 1) / 2 * qf.k_contract * cm.n_elem
+        pk = compute_peaks(F)
+        detail["fp64_tflops"] = flops64 / (detail["tabulate_fp64_ms"] / 1e3) / 1e12
+        detail["fp64_frac"] = detail["fp64_tflops"] / pk["fp64_fma"]
+        byts = cm.n_elem * (4 * qf.n_geometry + 4 * n * n) + cm.nodes.size * 8
+        # T_Q / T_T on affine cells: the headline mesh, mass and Poisson P1-P3
+        m = W.tet_scalar_mesh(40)
+        ca, va = torch.as_tensor(m.cells, device=device), torch.as_tensor(m.vertices, device=device)
+        ratio = {}
+        for form in (F.MASS, F.POISSON):
+            for q in (1, 2, 3):
+                f = F.Form(form, F.TETRAHEDRON, q)
+                qa = F.QForm(form, F.TETRAHEDRON, q, 1, 2 * q)
+                A = torch.empty((m.n_elem, f.n_local, f.n_local), dtype=torch.float32, device=device)
+                tt = _timed(lambda: F.tabulate(f, ca, va, precision="fp32", out=A), args.steps, 1)
+                tq = _timed(lambda: F.tabulate_quadrature(qa, ca, va, precision="fp32", out=A), args.steps, 1)
+                ratio[f"{FORM_NAME[form]}_p{q}"] = {"tensor_ms": tt * 1e3, "quadrature_ms": tq * 1e3,
+                                                    "TQ_over_TT": tq / tt}
+                del A
+        detail["affine_fp32_T_Q_over_T_T"] = ratio
+        cpu_rate, S = None, 0
+        if not args.no_cpu_baseline:
+            import multiprocessing as mp
+            pool = mp.get_context("spawn").Pool(cores)
+            S = min(cm.n_elem, 400 * cores)
+            X = CV.gather_nodes(cm)[np.linspace(0, cm.n_elem - 1, S).astype(np.int64)]
+            t0 = time.perf_counter()
+            pool.map(_oracle_curved, [(X[c::cores], qf.quad_degree) for c in range(cores)])
+            cpu_rate = S / (time.perf_counter() - t0)
+            pool.close()
+            pool.join()
+        out.update({"metric": "element tensors/s (P2 Poisson on 40^3x6 curved tets, quadrature as contraction)",
+                    "value": cm.n_elem / t, "ms_per_step": t * 1e3, "dtype": "f32",
+                    "config": {"workload": "quad_curved_p2_40", "cells": cm.n_elem, "geometry_degree": 2,
+                               "l2": "output 154 MB per step > L2"},
+                    "roofline": {"bound": "alu", "achieved": flops32 / t / 1e12, "peak": pk["fp32_fma"],
+                                 "unit": "TFLOP/s", "frac": flops32 / t / 1e12 / pk["fp32_fma"],
+                                 "peak_kind": "measured (ffc_diag_peak FP32 FMA, this run)", "traffic": None,
+                                 "hbm_gbs": byts / t / 1e9, "kernel": "quad_kernel<3, POISSON, float>"},
+                    "clocks": clk, "gpu_launches": args.steps,
+                    "cpu_baseline": {"value": cpu_rate, "unit": "elem/s", "cores": cores, "kind": "oracle",
+                                     "sample": f"{S} curved cells, point-by-point quadrature"},
+                    "detail": detail})
     elif workload == "rows":
         # the headline's eight problems, every degree by the row-owner assembly: mass and
         # Poisson in one ffc_assemble_rows_pair launch per degree (fixed-point sums, every
@@ -1188,6 +1259,14 @@ def measure_other(F, args, device, workload):
                                      "sample": f"{S} cells, continuous shape derivative"},
                     "detail": {"forward_tabulate_fp64_ms": t_fwd * 1e3}})
     return out
+
+
+def _oracle_curved(args):
+    X, p = args
+    from oracle import curved as OC
+
+    OC.element_tensors_curved(OC.POISSON, X, 2, 2, p)
+    return X.shape[0]
 
 
 def _oracle_shape(args):

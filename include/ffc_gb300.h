@@ -41,6 +41,7 @@ extern "C" {
 typedef struct ffc_form ffc_form;   /* opaque; owns the reference tensor (host and device copies) */
 typedef struct ffc_batch ffc_batch; /* opaque; a heterogeneous work list for one persistent launch */
 typedef struct ffc_row_plan ffc_row_plan; /* opaque; row-owner view of a dof map (ffc_assemble_rows) */
+typedef struct ffc_qform ffc_qform;       /* opaque; a form in the quadrature representation (Section 3.4) */
 
 typedef enum {
   FFC_OK = 0,
@@ -343,6 +344,64 @@ int ffc_assemble_rows(const ffc_form* f, const ffc_row_plan* plan, const int32_t
 int ffc_assemble_rows_pair(const ffc_form* fa, const ffc_form* fb, const ffc_row_plan* plan, const int32_t* cells,
                            const double* vertices, int64_t n_vert, double* csr_val_a, double* csr_val_b,
                            int precision, void* stream);
+
+/*
+ * Quadrature as a tensor contraction (Section 3.4, "Curvilinear elements"). When the map
+ * F_K from the reference simplex K0 is not affine, the Jacobian cannot be taken out of
+ * the integral; replacing the integral by a quadrature sum over points X_k with weights
+ * w_k keeps the element tensor a contraction, with one extra index for the points:
+ *   A^K_{i1 i2} ~= sum_k w_k integrand(X_k) |det F_K'(X_k)| = A~0[i][j] G~_K[j],
+ *   j = k * n_g + g over the points k and the per-point geometry entries g:
+ *   mass     n_g = 1:          A~0[i][k]     = w_k Phi_i1(X_k) Phi_i2(X_k)
+ *                              G~_K[k]       = |det F_K'(X_k)|
+ *   Poisson  n_g = d(d+1)/2:   A~0[i][(k,g)] = w_k (dPhi_i1/dX_a dPhi_i2/dX_b + [a != b]
+ *                                              dPhi_i1/dX_b dPhi_i2/dX_a)(X_k)
+ *                              G~_K[(k,g)]   = |det F_K'(X_k)| (F'^-1 F'^-T)[a][b](X_k)
+ *   for the pairs g = (a <= b), diagonal pairs first, then (0,1) [, (0,2), (1,2)].
+ * A~0 is computed once per form on the host (FP64); G~_K per cell on the device. The map
+ * is the geometry interpolant of degree `geometry_degree` (1: affine, 2: quadratic),
+ * F_K(X) = sum_n x_n Psi_n(X) over the cell's geometry nodes x_n in the local dof order
+ * of the P_g Lagrange space. The rule is the collapsed Gauss-Jacobi rule of
+ * Karniadakis & Sherwin exact for polynomial degree `quad_degree` (the rule A0 uses):
+ * m = ceil((quad_degree + 1) / 2) points per direction, direction k weighted by
+ * (1 - u)^k, X_k = u_k prod_{l > k} (1 - u_l). On affine cells with quad_degree at least
+ * the integrand's degree the result equals ffc_tabulate's to rounding.
+ *
+ * ffc_qform_create -- form FFC_MASS or FFC_POISSON, cell FFC_TRIANGLE / FFC_TETRAHEDRON,
+ * degree 1..4, geometry_degree 1 or 2, quad_degree 0..20. FFC_EINVAL otherwise.
+ * ffc_qform_info -- local dofs n, geometry nodes per cell, quadrature points, and the
+ * contraction length K = points * n_g.
+ * ffc_qform_reference_tensor -- A~0 as [n * n][K] doubles (j = k * n_g + g).
+ * ffc_qform_rule -- the points [N][d] (reference coordinates) and weights [N] (summing
+ * to 1/d!); either pointer may be NULL.
+ */
+int ffc_qform_create(int form, int cell, int degree, int geometry_degree, int quad_degree, ffc_qform** out);
+int ffc_qform_info(const ffc_qform* f, int* n_local, int* n_geometry, int* n_points, int* k_contract);
+int ffc_qform_reference_tensor(const ffc_qform* f, double* out);
+int ffc_qform_rule(const ffc_qform* f, double* points, double* weights);
+void ffc_qform_destroy(ffc_qform* f);
+
+/*
+ * ffc_tabulate_quadrature -- A_K = A~0 : G~_K for a batch of cells:
+ *   cells   device int32 [n_elem][n_geometry], geometry node ids in [0, n_nodes)
+ *   nodes   device double [n_nodes][d], node coordinates
+ *   A_K     device [n_elem][n][n], double (FFC_FP64) or float (FFC_FP32), 16-byte aligned
+ * FFC_FP64: G~_K and the contraction in FP64. FFC_FP32: F', its determinant and inverse
+ * in FP64, G~_K rounded to FP32, the contraction in FP32. A node id out of range sets
+ * FFC_FLAG_BOUNDS (its cell's tensor is then computed from node 0); a point where
+ * |det F'| <= 1e-14 h^d (h the largest node distance from node 0) sets
+ * FFC_FLAG_DEGENERATE. FFC_EINVAL for other precisions or bad pointers.
+ *
+ * ffc_assemble_quadrature -- Algorithm 2 fused, as ffc_assemble:
+ *   csr_val[slot[e][i1][i2]] += A_K[e][i1][i2]   (FP64 atomic adds)
+ * with slot from ffc_csr_pattern of the P_degree dof map (the geometry nodes are only an
+ * input of the map, not of the pattern).
+ */
+int ffc_tabulate_quadrature(const ffc_qform* f, int64_t n_elem, const int32_t* cells, const double* nodes,
+                            int64_t n_nodes, void* A_K, int precision, void* stream);
+int ffc_assemble_quadrature(const ffc_qform* f, int64_t n_elem, const int32_t* cells, const double* nodes,
+                            int64_t n_nodes, const int32_t* slot, double* csr_val, int64_t nnz, int precision,
+                            void* stream);
 
 /*
  * ffc_status_poll -- return the device status bits (FFC_FLAG_*) accumulated by earlier

@@ -55,6 +55,17 @@ SIGNATURES = {
     "ffc_assemble_rows_pair": (ctypes.c_int, [c_vp, c_vp, c_vp, c_vp, c_vp, ctypes.c_int64, c_vp, c_vp, ctypes.c_int,
                                               c_vp]),
     "ffc_assemble_rows": (ctypes.c_int, [c_vp, c_vp, c_vp, c_vp, ctypes.c_int64, c_vp, ctypes.c_int, c_vp]),
+    "ffc_qform_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                        ctypes.POINTER(c_vp)]),
+    "ffc_qform_info": (ctypes.c_int, [c_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                      ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
+    "ffc_qform_reference_tensor": (ctypes.c_int, [c_vp, c_vp]),
+    "ffc_qform_rule": (ctypes.c_int, [c_vp, c_vp, c_vp]),
+    "ffc_qform_destroy": (None, [c_vp]),
+    "ffc_tabulate_quadrature": (ctypes.c_int, [c_vp, ctypes.c_int64, c_vp, c_vp, ctypes.c_int64, c_vp, ctypes.c_int,
+                                               c_vp]),
+    "ffc_assemble_quadrature": (ctypes.c_int, [c_vp, ctypes.c_int64, c_vp, c_vp, ctypes.c_int64, c_vp, c_vp,
+                                               ctypes.c_int64, ctypes.c_int, c_vp]),
     "ffc_diag_bounded_wait": (ctypes.c_int, [ctypes.c_uint32, c_vp]),
     "ffc_diag_peak": (ctypes.c_int, [ctypes.c_int, c_dblp, c_dblp, c_vp]),
     "ffc_status_poll": (ctypes.c_int, [c_vp, c_u32p]),

@@ -290,6 +290,88 @@ def assemble_pair(form_a: Form, form_b: Form, cells, vertices, slot, csr_val_a, 
     return csr_val_a, csr_val_b
 
 
+class QForm:
+    """A mass or Poisson form in the quadrature representation (Section 3.4): A~0 with a
+    quadrature-point index, for cells mapped by a geometry interpolant of degree
+    `geometry_degree` (2: curved, isoparametric-style cells)."""
+
+    def __init__(self, kind: int, cell: int, degree: int, geometry_degree: int = 2, quad_degree: int | None = None):
+        d = 2 if cell == TRIANGLE else 3
+        if quad_degree is None:  # the mass integrand's degree on a map of this degree
+            quad_degree = 2 * degree + d * (geometry_degree - 1)
+        h = ctypes.c_void_p()
+        _check(lib().ffc_qform_create(kind, cell, degree, geometry_degree, quad_degree, ctypes.byref(h)),
+               "ffc_qform_create")
+        self._h = h
+        self.kind, self.cell, self.degree, self.dim = kind, cell, degree, d
+        self.geometry_degree, self.quad_degree = geometry_degree, quad_degree
+        n, g, nq, k = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(lib().ffc_qform_info(h, ctypes.byref(n), ctypes.byref(g), ctypes.byref(nq), ctypes.byref(k)),
+               "ffc_qform_info")
+        self.n_local, self.n_geometry, self.n_points, self.k_contract = n.value, g.value, nq.value, k.value
+
+    @property
+    def handle(self):
+        return self._h
+
+    def reference_tensor(self) -> np.ndarray:
+        out = np.empty((self.n_local ** 2, self.k_contract), dtype=np.float64)
+        _check(lib().ffc_qform_reference_tensor(self._h, out.ctypes.data_as(ctypes.c_void_p)),
+               "ffc_qform_reference_tensor")
+        return out
+
+    def rule(self) -> tuple[np.ndarray, np.ndarray]:
+        X = np.empty((self.n_points, self.dim), dtype=np.float64)
+        w = np.empty(self.n_points, dtype=np.float64)
+        _check(lib().ffc_qform_rule(self._h, X.ctypes.data_as(ctypes.c_void_p), w.ctypes.data_as(ctypes.c_void_p)),
+               "ffc_qform_rule")
+        return X, w
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            lib().ffc_qform_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def tabulate_quadrature(form: QForm, cells, nodes, precision="fp64", out=None, stream=None):
+    """Element tensors of curved cells by quadrature as a contraction (ffc_tabulate_quadrature).
+    cells int32 [n_elem, n_geometry] geometry node ids, nodes float64 [n_nodes, d]."""
+    import torch
+
+    p = _prec(precision)
+    n_elem = cells.shape[0]
+    c = _dev_ptr(cells, torch.int32, "cells", (n_elem, form.n_geometry))
+    v = _dev_ptr(nodes, torch.float64, "nodes", (nodes.shape[0], form.dim))
+    dt = torch.float64 if p == FP64 else torch.float32
+    if out is None:
+        out = torch.empty((n_elem, form.n_local, form.n_local), dtype=dt, device=cells.device)
+    o = _dev_ptr(out, dt, "out", (n_elem, form.n_local, form.n_local))
+    _check(lib().ffc_tabulate_quadrature(form.handle, n_elem, c, v, nodes.shape[0], o, p, _stream(stream)),
+           "ffc_tabulate_quadrature")
+    return out
+
+
+def assemble_quadrature(form: QForm, cells, nodes, slot, csr_val, precision="fp64", stream=None):
+    """csr_val[slot] += A_K of curved cells (ffc_assemble_quadrature)."""
+    import torch
+
+    p = _prec(precision)
+    n_elem = cells.shape[0]
+    c = _dev_ptr(cells, torch.int32, "cells", (n_elem, form.n_geometry))
+    v = _dev_ptr(nodes, torch.float64, "nodes", (nodes.shape[0], form.dim))
+    s = _dev_ptr(slot, torch.int32, "slot", (n_elem, form.n_local, form.n_local))
+    val = _dev_ptr(csr_val, torch.float64, "csr_val")
+    _check(lib().ffc_assemble_quadrature(form.handle, n_elem, c, v, nodes.shape[0], s, val, csr_val.numel(), p,
+                                         _stream(stream)), "ffc_assemble_quadrature")
+    return csr_val
+
+
 def scatter_add(A_K, slot, csr_val, stream=None):
     """The insertion step alone: csr_val[slot[e, ...]] += A_K[e, ...] (FP64 atomics).
     A_K float64 or float32 [n_elem, ...]; slot int32 of the same shape."""

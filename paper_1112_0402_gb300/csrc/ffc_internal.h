@@ -66,6 +66,11 @@ namespace ffc {
 // Host form compiler (reference tensor by collapsed Gauss-Jacobi quadrature).
 int compile_reference_tensor(ffc_form* f);
 int n_scalar_local(int d, int q);
+// The collapsed Gauss-Jacobi rule on the reference simplex exact for degree p (points
+// X [N][d], weights summing to 1/d!), and the reference Lagrange P_q basis at points X:
+// values psi [N][ns] and gradients dpsi [N][ns][d], in the local dof order.
+void reference_rule(int d, int p, std::vector<double>& X, std::vector<double>& W);
+void reference_basis(int d, int q, const std::vector<double>& X, std::vector<double>& psi, std::vector<double>& dpsi);
 // column of the symmetric pair (a, b) in the Poisson kernel layout: diagonal pairs
 // 0..d-1, then (0,1) [, (0,2), (1,2)]; the device code uses the same numbering
 int sym_pair(int d, int a, int b);

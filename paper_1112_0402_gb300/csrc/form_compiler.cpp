@@ -203,6 +203,27 @@ void silvester(int d, int q, const std::vector<int>& k, const double* lam, doubl
 
 }  // namespace
 
+void reference_rule(int d, int p, std::vector<double>& X, std::vector<double>& W) { collapsed_rule(d, p, X, W); }
+
+void reference_basis(int d, int q, const std::vector<double>& X, std::vector<double>& psi, std::vector<double>& dpsi) {
+  auto lat = local_lattice(d, q);
+  const int ns = int(lat.size()), N = int(X.size()) / d;
+  psi.assign(size_t(N) * ns, 0.0);
+  dpsi.assign(size_t(N) * ns * d, 0.0);
+  std::vector<double> lam(d + 1), dl(d + 1);
+  for (int iq = 0; iq < N; ++iq) {
+    double s = 0.0;
+    for (int a = 0; a < d; ++a) { lam[a + 1] = X[size_t(iq) * d + a]; s += lam[a + 1]; }
+    lam[0] = 1.0 - s;
+    for (int i = 0; i < ns; ++i) {
+      double v;
+      silvester(d, q, lat[i], lam.data(), &v, dl.data());
+      psi[size_t(iq) * ns + i] = v;
+      for (int a = 0; a < d; ++a) dpsi[(size_t(iq) * ns + i) * d + a] = dl[a + 1] - dl[0];
+    }
+  }
+}
+
 int compile_reference_tensor(ffc_form* f) {
   const int d = f->d, q = f->q, ns = f->ns, n = f->n;
   auto lat = local_lattice(d, q);

@@ -1,0 +1,158 @@
+"""Quadrature as a tensor contraction on the GPU (Section 3.4, "Curvilinear elements"):
+ffc_tabulate_quadrature / ffc_assemble_quadrature against the oracle.
+
+* affine cells (geometry degree 1, and straight quadratic cells): equal to the tensor
+  representation (ffc_tabulate) and to the affine oracle, FP64 1e-12;
+* curved quadratic-geometry cells: equal to the oracle's point-by-point quadrature sum
+  with the same rule, per cell relative Frobenius error FP64 1e-12, FP32 1e-6;
+* Algorithm 2 on curved cells: the assembled CSR matrix against the oracle's;
+* the full-size bench configuration (vector of 384,000 curved cells) on a seeded sample;
+* status flags: an out-of-range node id, a degenerate cell; a rule too large for one
+  tile is refused.
+"""
+import numpy as np
+import pytest
+
+from oracle import assemble as OA
+from oracle import curved as OC
+from oracle import element as OE
+from synthetic import dofmap as D
+from synthetic import mesh as M
+from synthetic.curved import curved_mesh, gather_nodes
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-12
+FP32_TOL = 1e-6
+
+
+@pytest.fixture(scope="module")
+def F():
+    import torch
+
+    from paper_1112_0402_gb300 import build as B
+
+    B.build()
+    import paper_1112_0402_gb300 as F
+
+    assert torch.cuda.is_available()
+    return F
+
+
+def _dev(x, dtype=None):
+    import torch
+
+    return torch.as_tensor(np.ascontiguousarray(x), dtype=dtype).cuda()
+
+
+def _rel(got, ref):
+    E = ref.shape[0]
+    return (np.linalg.norm((got - ref).reshape(E, -1), axis=1) / np.linalg.norm(ref.reshape(E, -1), axis=1)).max()
+
+
+def _cell(F, d):
+    return F.TRIANGLE if d == 2 else F.TETRAHEDRON
+
+
+@pytest.mark.parametrize("d", [2, 3])
+@pytest.mark.parametrize("form", [0, 1])
+@pytest.mark.parametrize("q", [1, 2, 3])
+def test_affine_cells_equal_the_tensor_representation(F, d, form, q):
+    import torch
+
+    m = M.unit_square_triangles(4, 0.25, 5) if d == 2 else M.unit_cube_tets(2, 0.25, 5)
+    V = M.gather_cell_vertices(m)
+    ref = OE.element_tensors(form, V, q)
+    tensor = F.tabulate(F.Form(form, _cell(F, d), q), _dev(m.cells, torch.int32), _dev(m.vertices, torch.float64),
+                        precision="fp64").cpu().numpy()
+    for g in (1, 2):
+        nodes = OC.affine_nodes(V, g)  # every cell its own nodes
+        E, ng = nodes.shape[:2]
+        cells = np.arange(E * ng, dtype=np.int32).reshape(E, ng)
+        qf = F.QForm(form, _cell(F, d), q, g, 2 * q)
+        got = F.tabulate_quadrature(qf, _dev(cells), _dev(nodes.reshape(-1, d)), precision="fp64").cpu().numpy()
+        assert F.status_poll() == 0
+        assert _rel(got, ref) <= FP64_TOL
+        assert _rel(got, tensor) <= FP64_TOL
+
+
+@pytest.mark.parametrize("d,n", [(2, 5), (3, 2)])
+@pytest.mark.parametrize("form", [0, 1])
+@pytest.mark.parametrize("q", [1, 2, 3])
+def test_curved_cells_match_the_oracle(F, d, n, form, q):
+    cm = curved_mesh(d, n, eps=0.12)
+    qf = F.QForm(form, _cell(F, d), q, 2)
+    ref = OC.element_tensors_curved(form, gather_nodes(cm), q, 2, qf.quad_degree)
+    cells, nodes = _dev(cm.cells), _dev(cm.nodes)
+    got = F.tabulate_quadrature(qf, cells, nodes, precision="fp64").cpu().numpy()
+    assert F.status_poll() == 0
+    assert _rel(got, ref) <= FP64_TOL
+    got32 = F.tabulate_quadrature(qf, cells, nodes, precision="fp32").double().cpu().numpy()
+    assert F.status_poll() == 0
+    assert _rel(got32, ref) <= FP32_TOL
+    # curved: the straight cells' tensors differ
+    straight = OE.element_tensors(form, gather_nodes(cm)[:, :d + 1], q)
+    assert _rel(straight, ref) > 1e-4
+
+
+@pytest.mark.parametrize("d,n", [(2, 4), (3, 2)])
+@pytest.mark.parametrize("form,q", [(1, 2), (0, 2), (1, 3)])
+def test_curved_assembly_matches_algorithm2(F, d, n, form, q):
+    import torch
+
+    cm = curved_mesh(d, n, eps=0.12)
+    qf = F.QForm(form, _cell(F, d), q, 2)
+    dofmap, n_dof = D.scalar_dofmap(cm.mesh, q)
+    ref_K = OC.element_tensors_curved(form, gather_nodes(cm), q, 2, qf.quad_degree)
+    ref_ptr, ref_col, ref_val = OA.assemble_csr(ref_K, dofmap, n_dof)
+    row_ptr, col, slot = F.csr_pattern(dofmap, n_dof)
+    assert np.array_equal(row_ptr, ref_ptr) and np.array_equal(col, ref_col)
+    for prec, tol in (("fp64", FP64_TOL), ("fp32", FP32_TOL)):
+        val = torch.zeros(col.size, dtype=torch.float64, device="cuda")
+        F.assemble_quadrature(qf, _dev(cm.cells), _dev(cm.nodes), _dev(slot, torch.int32), val, precision=prec)
+        assert F.status_poll() == 0
+        assert np.abs(val.cpu().numpy() - ref_val).max() <= tol * np.abs(ref_val).max()
+
+
+def test_full_size_curved_sample(F):
+    """40^3 x 6 = 384,000 curved tets (the bench configuration), P2 Poisson and mass,
+    FP64 and FP32, 300 seeded cells against the oracle, plus the Poisson rows' zero sums
+    over all cells."""
+    cm = curved_mesh(3, 40, eps=0.08)
+    rng = np.random.default_rng(20261203)
+    sel = np.sort(rng.choice(cm.n_elem, 300, replace=False))
+    cells, nodes = _dev(cm.cells), _dev(cm.nodes)
+    for form in (0, 1):
+        qf = F.QForm(form, F.TETRAHEDRON, 2, 2)
+        ref = OC.element_tensors_curved(form, gather_nodes(cm)[sel], 2, 2, qf.quad_degree)
+        for prec, tol in (("fp64", FP64_TOL), ("fp32", FP32_TOL)):
+            A = F.tabulate_quadrature(qf, cells, nodes, precision=prec)
+            assert F.status_poll() == 0
+            got = A[_dev(sel).long()].double().cpu().numpy()
+            assert _rel(got, ref) <= tol
+            if form == 1:
+                rs = A.double().sum(dim=2).abs().max().item()
+                assert rs <= (1e-12 if prec == "fp64" else 1e-5) * A.double().abs().max().item()
+            del A
+
+
+def test_quadrature_flags_and_limits(F):
+    import torch
+
+    cm = curved_mesh(3, 1, eps=0.1)
+    qf = F.QForm(1, F.TETRAHEDRON, 2, 2)
+    bad = cm.cells.copy()
+    bad[0, 4] = cm.nodes.shape[0] + 7
+    F.tabulate_quadrature(qf, _dev(bad), _dev(cm.nodes), precision="fp64")
+    assert F.status_poll() & F.FLAG_BOUNDS
+    flat = cm.cells.copy()
+    flat[1, :] = flat[1, 0]  # every node of cell 1 at one point
+    F.tabulate_quadrature(qf, _dev(flat), _dev(cm.nodes), precision="fp32")
+    assert F.status_poll() & F.FLAG_DEGENERATE
+    big = F.QForm(1, F.TETRAHEDRON, 2, 2, 20)  # 1331 points: the tile does not fit in shared memory
+    with pytest.raises(F.FFCError):
+        F.tabulate_quadrature(big, _dev(cm.cells), _dev(cm.nodes), precision="fp64")
+    empty = torch.empty((0, 10), dtype=torch.int32, device="cuda")
+    out = F.tabulate_quadrature(qf, empty, _dev(cm.nodes), precision="fp64")
+    assert out.shape == (0, 10, 10)
+    assert F.status_poll() == 0
