@@ -12,13 +12,18 @@
 // cell's geometry nodes, so F'(X_k) = sum_n x_n grad Psi_n(X_k)^T with the gradients of
 // the geometry basis at the points tabulated on the host.
 //
-// Kernel: tiles of 16 cells per CTA (persistent). Phase 1 loads the tile's node
-// coordinates; phase 2 computes G~ for every (cell, point) in FP64 (F', its determinant
-// and adjugate) into shared memory, rounded to the contraction's type; phase 3 contracts:
-// a thread item is one element-tensor entry for 8 cells, streaming the entry's row of
-// A~0 (stored transposed, [K][entries], so a warp's loads are consecutive) against the 8
-// cells' G~ (shared-memory broadcasts). The FP64 kernels compute the entries i1 <= i2 of
-// these symmetric forms and store both (i1, i2) and (i2, i1); the FP32 ones all entries.
+// Kernel: a register-tiled GEMM, C[cell][entry] = sum_j G~[cell][j] A~0[j][entry], over
+// tiles of MC cells per CTA (persistent; 32 cells for FP32, 16 for FP64). Per tile: the
+// cells' geometry nodes relative to each cell's node 0 (differences in FP64, then rounded
+// to the contraction's type, so F' keeps that type's relative precision); G~ for every
+// (cell, point) in the contraction's type (F', its determinant and adjugate, one
+// reciprocal), stored K-major ([j][cell]); then, for each block of 128 entries (FP64: 64),
+// the K dimension in chunks of 32 rows of A~0 (stored transposed, [K][entries padded to
+// 16 bytes]) staged by cp.async into a double buffer. Warp w owns cells 4w..4w+3 (FP64: 2w, 2w+1) and lane l entries 4l..4l+3
+// of the block (FP64: 2l, 2l+1): each K step is one 16-byte shared load of G~ (a broadcast
+// within the warp), one of A~0 and 16 (4) FMAs into registers. The FP64 kernels compute the
+// entries i1 <= i2 of these symmetric forms and store both (i1, i2) and (i2, i1); the
+// FP32 ones all entries, four consecutive per 16-byte store where the row allows it.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -41,8 +46,8 @@ struct ffc_qform {
   std::vector<double> At;    // A~0 [n*n][K], j = k * ng + g
   std::vector<double> dgeo;  // geometry basis gradients [nq][ngeo][d]
   struct Dev {
-    double* at_f64 = nullptr;  // [K][n(n+1)/2], entries i1 <= i2
-    float* at_f32 = nullptr;   // [K][n*n]
+    double* at_f64 = nullptr;  // [K][ne64], entries i1 <= i2, padded to an even count
+    float* at_f32 = nullptr;   // [K][ne32], all entries, padded to a multiple of 4
     double* dgeo = nullptr;
     uint16_t* epair = nullptr;  // [n(n+1)/2]: i1 << 8 | i2
   };
@@ -53,8 +58,6 @@ struct ffc_qform {
 namespace ffc {
 namespace {
 
-constexpr int QT_CELLS = 16;  // cells of one tile
-constexpr int QT_GROUP = 8;   // cells of one thread item
 constexpr int QT_THREADS = 256;
 
 int cuda_fail(cudaError_t e, const char* what) {
@@ -104,17 +107,18 @@ int ensure_qdev(ffc_qform* f, ffc_qform::Dev** out) {
   ffc_qform::Dev& D = f->dev[dev];
   if (!D.at_f64) {
     const int n = f->n, K = f->K, nn = n * n, ns = n * (n + 1) / 2;
-    std::vector<double> a64(size_t(K) * ns);
-    std::vector<float> a32(size_t(K) * nn);
+    const int ns_pad = (ns + 1) / 2 * 2, nn_pad = (nn + 3) / 4 * 4;
+    std::vector<double> a64(size_t(K) * ns_pad, 0.0);
+    std::vector<float> a32(size_t(K) * nn_pad, 0.0f);
     std::vector<uint16_t> ep(ns);
     int u = 0;
     for (int i1 = 0; i1 < n; ++i1)
       for (int i2 = i1; i2 < n; ++i2, ++u) {
         ep[u] = uint16_t((i1 << 8) | i2);
-        for (int j = 0; j < K; ++j) a64[size_t(j) * ns + u] = f->At[(size_t(i1) * n + i2) * K + j];
+        for (int j = 0; j < K; ++j) a64[size_t(j) * ns_pad + u] = f->At[(size_t(i1) * n + i2) * K + j];
       }
     for (int i = 0; i < nn; ++i)
-      for (int j = 0; j < K; ++j) a32[size_t(j) * nn + i] = float(f->At[size_t(i) * K + j]);
+      for (int j = 0; j < K; ++j) a32[size_t(j) * nn_pad + i] = float(f->At[size_t(i) * K + j]);
     ffc_qform::Dev t;
     if ((e = cudaMalloc(&t.at_f64, a64.size() * sizeof(double))) != cudaSuccess ||
         (e = cudaMalloc(&t.at_f32, a32.size() * sizeof(float))) != cudaSuccess ||
@@ -138,7 +142,7 @@ int ensure_qdev(ffc_qform* f, ffc_qform::Dev** out) {
 }
 
 struct QParams {
-  int n, nn, ne, ngeo, nq, K;
+  int n, nn, ne, ne_pad, ngeo, nq, K;
   long long n_elem, n_nodes, nnz;
   const int32_t* cells;
   const double* nodes;
@@ -150,8 +154,8 @@ struct QParams {
   unsigned* status;
 };
 
-template <int D>
-__device__ __forceinline__ double det_adj(const double (&J)[D][D], double (&A)[D][D]) {
+template <int D, typename T>
+__device__ __forceinline__ T det_adj(const T (&J)[D][D], T (&A)[D][D]) {
   if constexpr (D == 2) {
     A[0][0] = J[1][1];
     A[0][1] = -J[0][1];
@@ -178,129 +182,229 @@ __device__ __forceinline__ int qsym(int a, int b) {
   return a == b ? a : (D == 2 ? 2 : (a == 0 ? (b == 1 ? 3 : 4) : 5));
 }
 
+__device__ __forceinline__ void q_cp_async16(void* smem_dst, const void* gsrc) {
+  const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(smem_dst));
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void q_cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void q_cp_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+__device__ __forceinline__ void q_cp_wait0() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+template <typename T>
+struct QTile {
+  static constexpr int TM = sizeof(T) == 4 ? 4 : 2;  // cells of a thread (one warp's cells)
+  static constexpr int TN = sizeof(T) == 4 ? 4 : 2;  // entries of a thread (FP64: short symmetric
+                                                     // rows keep the lanes busy)
+  static constexpr int MC = 8 * TM;                 // cells of a tile (8 warps)
+  static constexpr int NB = 32 * TN;                // entries of a block (32 lanes)
+  static constexpr int KC = 32;                     // rows of A~0 per staged chunk
+};
+
+// shared memory of one CTA: geometry gradients, node coordinates, G~ [K][MC] and the
+// double-buffered A~0 chunk [2][KC][NB]
+// shared memory of one CTA: geometry gradients [nq][ngeo][D] (T), node coordinates
+// relative to node 0 [MC][ngeo][D] (T), the cells' h^D [MC] (double), G~ [K][MC] (T) and the
+// double-buffered A~0 chunk [2][KC][NB] (T), each part 16-byte aligned
+template <int D, typename T>
+__host__ __device__ inline size_t quad_smem_bytes(int nq, int ngeo, int K) {
+  using Q = QTile<T>;
+  auto al = [](size_t b) { return (b + 15) / 16 * 16; };
+  return al(size_t(nq) * ngeo * D * sizeof(T)) + al(size_t(Q::MC) * ngeo * D * sizeof(T)) + al(size_t(Q::MC) * 8) +
+         al(size_t(K) * Q::MC * sizeof(T)) + size_t(2) * Q::KC * Q::NB * sizeof(T);
+}
+
 template <int D, int FORM, typename T, bool ASM, bool SYMM>
 __global__ void __launch_bounds__(QT_THREADS) quad_kernel(QParams p) {
+  using Q = QTile<T>;
   constexpr int NG = FORM == FFC_MASS ? 1 : D * (D + 1) / 2;
+  constexpr int TM = Q::TM, TN = Q::TN, MC = Q::MC, NB = Q::NB, KC = Q::KC;
   extern __shared__ __align__(16) unsigned char smem[];
-  double* dg = reinterpret_cast<double*>(smem);           // [nq][ngeo][D]
-  double* xs = dg + size_t(p.nq) * p.ngeo * D;            // [QT_CELLS][ngeo][D]
-  T* gt = reinterpret_cast<T*>(xs + QT_CELLS * p.ngeo * D);  // [QT_CELLS][K]
-  const int t = threadIdx.x, K = p.K, ngeo = p.ngeo;
-  for (int i = t; i < p.nq * ngeo * D; i += QT_THREADS) dg[i] = p.dgeo[i];
-  const long long n_tiles = (p.n_elem + QT_CELLS - 1) / QT_CELLS;
+  auto al = [](size_t x) { return (x + 15) / 16 * 16; };
+  T* dg = reinterpret_cast<T*>(smem);                                                      // [nq][ngeo][D]
+  T* xs = reinterpret_cast<T*>(smem + al(size_t(p.nq) * p.ngeo * D * sizeof(T)));          // [MC][ngeo][D]
+  double* hd = reinterpret_cast<double*>(reinterpret_cast<unsigned char*>(xs) + al(size_t(MC) * p.ngeo * D * sizeof(T)));
+  T* gt = reinterpret_cast<T*>(reinterpret_cast<unsigned char*>(hd) + al(size_t(MC) * 8));  // [K][MC]
+  T* ab = gt + size_t(p.K) * MC;                                                           // [2][KC][NB]
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5, K = p.K, ngeo = p.ngeo;
+  for (int i = t; i < p.nq * ngeo * D; i += QT_THREADS) dg[i] = T(p.dgeo[i]);
+  const T* At = static_cast<const T*>(p.At);
+  const long long n_tiles = (p.n_elem + MC - 1) / MC;
+  const int n_kc = (K + KC - 1) / KC;
   bool bad_node = false, degenerate = false;
   for (long long tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
-    const long long c0 = tile * QT_CELLS;
-    const int cells_here = int(min((long long)QT_CELLS, p.n_elem - c0));
+    const long long c0 = tile * MC;
+    const int cells_here = int(min((long long)MC, p.n_elem - c0));
     __syncthreads();  // the previous tile's G~ and nodes are no longer read
-    for (int idx = t; idx < QT_CELLS * ngeo; idx += QT_THREADS) {
-      const int e = idx / ngeo, nd = idx - e * ngeo;
-      long long id = 0;
+    // node coordinates relative to the cell's node 0, in FP64 then rounded to T (the
+    // differences are of the cell's size, so F' keeps T's relative precision), and the
+    // cell's h^D (h the largest distance from node 0 to the other vertices) in FP64
+    for (int e = w; e < MC; e += QT_THREADS / 32) {
+      long long id0 = 0;
       if (e < cells_here) {
-        id = p.cells[(c0 + e) * ngeo + nd];
-        if (id < 0 || id >= p.n_nodes) {
+        id0 = p.cells[(c0 + e) * ngeo];
+        if (id0 < 0 || id0 >= p.n_nodes) {
           bad_node = true;
-          id = 0;
+          id0 = 0;
         }
       }
+      double h2 = 0.0;
+      for (int nd = lane; nd < ngeo; nd += 32) {
+        long long id = id0;
+        if (e < cells_here) {
+          id = p.cells[(c0 + e) * ngeo + nd];
+          if (id < 0 || id >= p.n_nodes) {
+            bad_node = true;
+            id = id0;
+          }
+        }
+        double sq = 0.0;
 #pragma unroll
-      for (int a = 0; a < D; ++a) xs[idx * D + a] = p.nodes[id * D + a];
+        for (int a = 0; a < D; ++a) {
+          const double dx = p.nodes[id * D + a] - p.nodes[id0 * D + a];
+          xs[(e * ngeo + nd) * D + a] = T(dx);
+          sq = fma(dx, dx, sq);
+        }
+        if (nd >= 1 && nd <= D) h2 = fmax(h2, sq);
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) h2 = fmax(h2, __shfl_xor_sync(0xffffffffu, h2, o));
+      if (lane == 0) hd[e] = D == 2 ? h2 : h2 * sqrt(h2);
     }
     __syncthreads();
-    for (int idx = t; idx < QT_CELLS * p.nq; idx += QT_THREADS) {
-      const int e = idx / p.nq, k = idx - e * p.nq;
-      T* gout = gt + size_t(e) * K + k * NG;
+    for (int idx = t; idx < MC * p.nq; idx += QT_THREADS) {
+      const int k = idx / MC, e = idx - k * MC;
+      T* gout = gt + size_t(k) * NG * MC + e;  // G~[(k, g)][e]
       if (e >= cells_here) {
 #pragma unroll
-        for (int g = 0; g < NG; ++g) gout[g] = T(0);
+        for (int g = 0; g < NG; ++g) gout[g * MC] = T(0);
         continue;
       }
-      const double* xe = xs + e * ngeo * D;
-      const double* dk = dg + size_t(k) * ngeo * D;
-      double J[D][D];
+      const T* xe = xs + e * ngeo * D;
+      const T* dk = dg + size_t(k) * ngeo * D;
+      T J[D][D];
 #pragma unroll
       for (int a = 0; a < D; ++a)
 #pragma unroll
-        for (int b = 0; b < D; ++b) J[a][b] = 0.0;
-      for (int nd = 0; nd < ngeo; ++nd)
+        for (int b = 0; b < D; ++b) J[a][b] = T(0);
+      for (int nd = 1; nd < ngeo; ++nd)  // node 0 is the origin of the relative coordinates
 #pragma unroll
         for (int a = 0; a < D; ++a)
 #pragma unroll
           for (int b = 0; b < D; ++b) J[a][b] = fma(xe[nd * D + a], dk[nd * D + b], J[a][b]);
-      double A[D][D];
-      const double det = det_adj<D>(J, A);
-      // cell size: the largest distance from vertex node 0 to the other vertex nodes
-      double h2 = 0.0;
-      for (int v = 1; v <= D; ++v) {
-        double s = 0.0;
-#pragma unroll
-        for (int a = 0; a < D; ++a) {
-          const double dx = xe[v * D + a] - xe[a];
-          s = fma(dx, dx, s);
-        }
-        h2 = fmax(h2, s);
-      }
-      const double hd = D == 2 ? h2 : h2 * sqrt(h2);
-      if (!(fabs(det) > 1e-14 * hd)) degenerate = true;
-      const double ad = fabs(det);
+      T A[D][D];
+      const T det = det_adj<D, T>(J, A);
+      if (!(fabs(double(det)) > 1e-14 * hd[e])) degenerate = true;
+      const T ad = fabs(det);
       if constexpr (FORM == FFC_MASS) {
-        gout[0] = T(ad);
+        gout[0] = ad;
       } else {
         // |det| (F'^-1 F'^-T)[a][b] = (adj adj^T)[a][b] / |det|
+        const T r = T(1) / ad;
 #pragma unroll
         for (int a = 0; a < D; ++a)
 #pragma unroll
           for (int b = a; b < D; ++b) {
-            double s = 0.0;
+            T sq = T(0);
 #pragma unroll
-            for (int c = 0; c < D; ++c) s = fma(A[a][c], A[b][c], s);
-            gout[qsym<D>(a, b)] = T(s / ad);
+            for (int c = 0; c < D; ++c) sq = fma(A[a][c], A[b][c], sq);
+            gout[qsym<D>(a, b) * MC] = sq * r;
           }
       }
     }
-    __syncthreads();
-    const T* At = static_cast<const T*>(p.At);
-    for (int item = t; item < p.ne * (QT_CELLS / QT_GROUP); item += QT_THREADS) {
-      const int u = item % p.ne, cg = item / p.ne;
-      if (cg * QT_GROUP >= cells_here) continue;
-      T acc[QT_GROUP];
+    // entry blocks of NB: lane l takes entries nb + 4l .. nb + 4l + 3, warp w cells TM w ..
+    for (int nb = 0; nb < p.ne; nb += NB) {
+      const int nbw = min(NB, p.ne_pad - nb);  // staged width (a multiple of 16 bytes)
+      auto stage = [&](int kc, int buf) {
+        const int rows = min(KC, K - kc * KC);
+        constexpr int V = 16 / int(sizeof(T));  // values of one 16-byte copy
+        const int per_row = nbw / V;
+        T* dst = ab + size_t(buf) * KC * NB;
+        for (int c = t; c < rows * per_row; c += QT_THREADS) {
+          const int r = c / per_row, x = (c - r * per_row) * V;
+          q_cp_async16(dst + r * NB + x, At + size_t(kc * KC + r) * p.ne_pad + nb + x);
+        }
+        q_cp_commit();
+      };
+      T acc[TM][TN];
 #pragma unroll
-      for (int c = 0; c < QT_GROUP; ++c) acc[c] = T(0);
-      const T* a = At + u;
-      const T* g = gt + size_t(cg) * QT_GROUP * K;
-      for (int j = 0; j < K; ++j) {
-        const T av = __ldg(a + size_t(j) * p.ne);
+      for (int i = 0; i < TM; ++i)
 #pragma unroll
-        for (int c = 0; c < QT_GROUP; ++c) acc[c] = fma(av, g[c * K + j], acc[c]);
+        for (int j = 0; j < TN; ++j) acc[i][j] = T(0);
+      __syncthreads();  // G~ written; the A~0 buffers free
+      stage(0, 0);
+      for (int kc = 0; kc < n_kc; ++kc) {
+        if (kc + 1 < n_kc) {
+          stage(kc + 1, (kc + 1) & 1);
+          q_cp_wait1();
+        } else {
+          q_cp_wait0();
+        }
+        __syncthreads();
+        const T* a = ab + size_t(kc & 1) * KC * NB + TN * lane;
+        const T* g = gt + size_t(kc) * KC * MC + TM * w;
+        const int rows = min(KC, K - kc * KC);
+        for (int r = 0; r < rows; ++r) {
+          T av[TN], gv[TM];
+          if constexpr (sizeof(T) == 4) {
+            const float4 x = *reinterpret_cast<const float4*>(a + r * NB);
+            av[0] = x.x, av[1] = x.y, av[2] = x.z, av[3] = x.w;
+            const float4 y = *reinterpret_cast<const float4*>(g + r * MC);
+            gv[0] = y.x, gv[1] = y.y, gv[2] = y.z, gv[3] = y.w;
+          } else {
+            const double2 x0 = *reinterpret_cast<const double2*>(a + r * NB);
+            av[0] = x0.x, av[1] = x0.y;
+            const double2 y = *reinterpret_cast<const double2*>(g + r * MC);
+            gv[0] = y.x, gv[1] = y.y;
+          }
+#pragma unroll
+          for (int i = 0; i < TM; ++i)
+#pragma unroll
+            for (int j = 0; j < TN; ++j) acc[i][j] = fma(gv[i], av[j], acc[i][j]);
+        }
+        __syncthreads();  // this buffer is staged again two chunks later
       }
-      int i1, i2;
-      if constexpr (SYMM) {
-        const unsigned ep = p.epair[u];
-        i1 = int(ep >> 8);
-        i2 = int(ep & 255u);
-      } else {
-        i1 = u / p.n;
-        i2 = u - i1 * p.n;
-      }
+      // results: cells c0 + TM w + i, entries nb + TN lane + j
 #pragma unroll
-      for (int c = 0; c < QT_GROUP; ++c) {
-        const int e = cg * QT_GROUP + c;
+      for (int i = 0; i < TM; ++i) {
+        const int e = TM * w + i;
         if (e >= cells_here) break;
         const long long cell = c0 + e;
-        if constexpr (ASM) {
-          double* csr = static_cast<double*>(p.out);
-          const long long s1 = p.slot[cell * p.nn + i1 * p.n + i2];
-          if (s1 >= 0 && s1 < p.nnz) atomicAdd(csr + s1, double(acc[c]));
-          else bad_node = true;
-          if (SYMM && i1 != i2) {
-            const long long s2 = p.slot[cell * p.nn + i2 * p.n + i1];
-            if (s2 >= 0 && s2 < p.nnz) atomicAdd(csr + s2, double(acc[c]));
-            else bad_node = true;
-          }
-        } else {
+        const int u0 = nb + TN * lane;
+        if constexpr (!ASM && !SYMM) {
           T* o = static_cast<T*>(p.out) + cell * p.nn;
-          o[i1 * p.n + i2] = acc[c];
-          if (SYMM && i1 != i2) o[i2 * p.n + i1] = acc[c];
+          if (u0 + TN <= p.ne && (p.nn % 4) == 0) {
+            *reinterpret_cast<float4*>(o + u0) = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+            continue;
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < TN; ++j) {
+          const int u = u0 + j;
+          if (u >= p.ne) break;
+          int i1, i2;
+          if constexpr (SYMM) {
+            const unsigned ep = p.epair[u];
+            i1 = int(ep >> 8);
+            i2 = int(ep & 255u);
+          } else {
+            i1 = u / p.n;
+            i2 = u - i1 * p.n;
+          }
+          if constexpr (ASM) {
+            double* csr = static_cast<double*>(p.out);
+            const long long s1 = p.slot[cell * p.nn + i1 * p.n + i2];
+            if (s1 >= 0 && s1 < p.nnz) atomicAdd(csr + s1, double(acc[i][j]));
+            else bad_node = true;
+            if (SYMM && i1 != i2) {
+              const long long s2 = p.slot[cell * p.nn + i2 * p.n + i1];
+              if (s2 >= 0 && s2 < p.nnz) atomicAdd(csr + s2, double(acc[i][j]));
+              else bad_node = true;
+            }
+          } else {
+            T* o = static_cast<T*>(p.out) + cell * p.nn;
+            o[i1 * p.n + i2] = acc[i][j];
+            if (SYMM && i1 != i2) o[i2 * p.n + i1] = acc[i][j];
+          }
         }
       }
     }
@@ -311,8 +415,7 @@ __global__ void __launch_bounds__(QT_THREADS) quad_kernel(QParams p) {
 
 template <int D, int FORM, typename T, bool ASM, bool SYMM>
 int launch_quad(const QParams& prm, cudaStream_t s) {
-  const size_t smem = size_t(prm.nq) * prm.ngeo * D * sizeof(double) + size_t(QT_CELLS) * prm.ngeo * D * sizeof(double) +
-                      size_t(QT_CELLS) * prm.K * sizeof(T);
+  const size_t smem = quad_smem_bytes<D, T>(prm.nq, prm.ngeo, prm.K);
   int dev = 0, optin = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
@@ -325,7 +428,7 @@ int launch_quad(const QParams& prm, cudaStream_t s) {
   int sms = 0, per_sm = 1;
   if (launch_config(reinterpret_cast<const void*>(kern), QT_THREADS, smem, -1, &sms, &per_sm) != FFC_OK)
     return FFC_ECUDA;
-  const long long tiles = (prm.n_elem + QT_CELLS - 1) / QT_CELLS;
+  const long long tiles = (prm.n_elem + QTile<T>::MC - 1) / QTile<T>::MC;
   long long blocks = std::min<long long>(tiles, (long long)sms * std::max(per_sm, 1));
   kern<<<unsigned(std::max<long long>(blocks, 1)), QT_THREADS, smem, s>>>(prm);
   const cudaError_t e = cudaGetLastError();
@@ -350,7 +453,8 @@ int run_quadrature(const ffc_qform* f, int64_t n_elem, const int32_t* cells, con
     return FFC_ECUDA;
   }
   const bool fp64 = precision == FFC_FP64;
-  QParams prm{f->n,          f->n * f->n, fp64 ? f->n * (f->n + 1) / 2 : f->n * f->n,
+  const int ne = fp64 ? f->n * (f->n + 1) / 2 : f->n * f->n;
+  QParams prm{f->n,          f->n * f->n, ne, fp64 ? (ne + 1) / 2 * 2 : (ne + 3) / 4 * 4,
               f->ngeo,       f->nq,       f->K,
               n_elem,        n_nodes,     nnz,
               cells,
