@@ -60,8 +60,33 @@ __device__ __forceinline__ void gather_vertices(const int32_t* __restrict__ cell
       bad_index = true;
       id[j] = 0;
     }
-#pragma unroll
-    for (int r = 0; r < D; ++r) x[j][r] = __ldg(vertices + int64_t(id[j]) * D + r);
+    // 16-byte loads where the vertex's coordinates allow them: in 2D a vertex is one
+    // 16-byte pair when its address is 16-byte aligned; in 3D its 24 bytes are a pair and
+    // a single value, in the order its address's alignment gives
+    const double* v = vertices + int64_t(id[j]) * D;
+    const bool odd = (reinterpret_cast<uintptr_t>(v) >> 3) & 1;
+    if constexpr (D == 2) {
+      if (!odd) {
+        const double2 a = __ldg(reinterpret_cast<const double2*>(v));
+        x[j][0] = a.x;
+        x[j][1] = a.y;
+      } else {
+        x[j][0] = __ldg(v);
+        x[j][1] = __ldg(v + 1);
+      }
+    } else {
+      if (!odd) {
+        const double2 a = __ldg(reinterpret_cast<const double2*>(v));
+        x[j][0] = a.x;
+        x[j][1] = a.y;
+        x[j][2] = __ldg(v + 2);
+      } else {
+        x[j][0] = __ldg(v);
+        const double2 a = __ldg(reinterpret_cast<const double2*>(v + 1));
+        x[j][1] = a.x;
+        x[j][2] = a.y;
+      }
+    }
   }
 }
 
