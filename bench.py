@@ -643,7 +643,8 @@ def measure_detail(F, ctx, args, device, reps=5):
             r = {"elem_per_s": n_elem / t, "ms": t * 1e3, "hbm_frac": byts / t / 1e9 / hbm_peak}
             if prec == "fp64" and pr["form"] == 1:
                 # executed FP64 FMAs: the symmetric form contracts the entries i1 <= i2 only
-                fl = 2.0 * n * (n + 1) / 2 * pr["F"].n_alpha * n_elem / t / 1e12
+                nak = 3 * (3 + 1) // 2  # symmetric G of the tetrahedron: 6 columns
+                fl = 2.0 * n * (n + 1) / 2 * nak * n_elem / t / 1e12
                 r["fp64_tflops"] = fl
                 r["fp64_frac"] = fl / compute_peaks(F)["fp64_fma"]
             if prec == "fp64":
@@ -653,6 +654,20 @@ def measure_detail(F, ctx, args, device, reps=5):
                 r["max_rel_err_vs_fp64"] = float(d.max().item())
                 r["mean_rel_err_vs_fp64"] = float(d.mean().item())
             rec[prec] = r
+            if prec != "fp64" and pr["form"] == 1 and pr["q"] >= 3:
+                # the same element tensors on the tensor cores (tcgen05, split products)
+                for tc in ("tf32x3", "bf16x3"):
+                    F.tabulate(pr["F"], ctx["cells"], ctx["verts"], out=A, precision=tc)
+                    torch.cuda.synchronize()
+                    a.record()
+                    for _ in range(reps):
+                        F.tabulate(pr["F"], ctx["cells"], ctx["verts"], out=A, precision=tc)
+                    b.record()
+                    torch.cuda.synchronize()
+                    ttc = a.elapsed_time(b) / 1e3 / reps
+                    d = (A.double() - ref).reshape(n_elem, -1).norm(dim=1) / ref.reshape(n_elem, -1).norm(dim=1)
+                    rec[tc] = {"ms": ttc * 1e3, "hbm_frac": byts / ttc / 1e9 / hbm_peak,
+                               "max_rel_err_vs_fp64": float(d.max().item())}
             del A
         ref = None
         torch.cuda.empty_cache()

@@ -83,14 +83,16 @@ struct TcParams {
   unsigned* status;
 };
 
-constexpr int KCH = 32;  // K per staged A0 chunk
-
 template <int D, int FORM, int Q, int MODE>
 struct TcCfg {
   using S = Split<MODE>;
   static constexpr int N = nlocal(FORM, D, Q);
   static constexpr int NN = N * N;
   static constexpr int NA = nalpha(FORM, D, Q);
+  // K per staged A0 chunk: 16 (a multiple of both MMA K steps, 8 for TF32 and 16 for
+  // BF16) for forms with |alpha| <= 16 (mass 1, Poisson 4 or 9), whose K then pads to 16
+  // instead of 32; 32 for the vector forms
+  static constexpr int KCH = NA <= 16 ? 16 : 32;
   static constexpr int KPAD = (NA + KCH - 1) / KCH * KCH;  // a whole number of chunks
   static constexpr int KC = KPAD / S::EPC;                 // core-matrix columns of B
   static constexpr int NCH = KPAD / KCH;                   // A0 chunks per M-tile
@@ -305,7 +307,7 @@ __global__ void __launch_bounds__(WS_THREADS, 1) tc_ws_kernel(TcParams p) {
       constexpr uint32_t IDESC = S::idesc(M_TILE, N_CELLS);
       constexpr uint32_t SBO_A = C::KCC * 128;  // chunk: row groups of KCC core matrices
       constexpr uint32_t SBO_B = C::KC * 128;   // B: row groups of all KC core matrices
-      constexpr int KS_PER_CH = KCH / S::KSTEP;
+      constexpr int KS_PER_CH = C::KCH / S::KSTEP;
       uint32_t ph_full = 0, ph_acc_empty = 0, ph_b = 0;
       bool ok = true;
       long long g = 0, gm = 0;  // chunks and M-tiles consumed
@@ -555,14 +557,14 @@ int upload_parts(ffc_form* f, DeviceTensors* t) {
   const int fam = S::BF16 ? 1 : 0;
   std::lock_guard<std::mutex> g(f->lock);
   if (t->tc_part[fam][S::PARTS - 1] && t->tc_kpad[fam] == C::KPAD) return FFC_OK;
-  const size_t per = size_t(C::MT) * M_TILE * C::KPAD;  // elements per part: [MT][NCH][128 x KCH] chunks
+  const size_t per = size_t(C::MT) * M_TILE * C::KPAD;  // elements per part: [MT][NCH][128 x C::KCH] chunks
   const int nparts = S::BF16 ? 3 : 2;                    // a family uploads all its parts once
   std::vector<std::vector<typename S::Store>> parts(nparts, std::vector<typename S::Store>(per, 0));
   for (int i = 0; i < C::NN; ++i)
     for (int k = 0; k < C::NA; ++k) {
       double r = f->A0[size_t(i) * C::NA + k];
-      const size_t o = (size_t(i / M_TILE) * C::NCH + k / KCH) * (M_TILE * KCH) +
-                       core_offset(i % M_TILE, k % KCH, C::KCC, S::EPC);
+      const size_t o = (size_t(i / M_TILE) * C::NCH + k / C::KCH) * (M_TILE * C::KCH) +
+                       core_offset(i % M_TILE, k % C::KCH, C::KCC, S::EPC);
       for (int q = 0; q < nparts; ++q) {
         if constexpr (S::BF16) {
           const uint16_t b = host_bf16_bits(r);
