@@ -385,12 +385,18 @@ void ffc_qform_destroy(ffc_qform* f);
  * ffc_tabulate_quadrature -- A_K = A~0 : G~_K for a batch of cells:
  *   cells   device int32 [n_elem][n_geometry], geometry node ids in [0, n_nodes)
  *   nodes   device double [n_nodes][d], node coordinates
- *   A_K     device [n_elem][n][n], double (FFC_FP64) or float (FFC_FP32), 16-byte aligned
+ *   A_K     device [n_elem][n][n], double (FFC_FP64) or float (the others), 16-byte aligned
  * FFC_FP64: G~_K and the contraction in FP64. FFC_FP32: F', its determinant and inverse
  * in FP64, G~_K rounded to FP32, the contraction in FP32. A node id out of range sets
  * FFC_FLAG_BOUNDS (its cell's tensor is then computed from node 0); a point where
  * |det F'| <= 1e-14 h^d (h the largest node distance from node 0) sets
- * FFC_FLAG_DEGENERATE. FFC_EINVAL for other precisions or bad pointers.
+ * FFC_FLAG_DEGENERATE.
+ * FFC_TF32 / FFC_TF32X3 / FFC_BF16X3 (element tensors of at most 128 entries: P1-P2 on
+ * tets, P1-P3 on triangles, else FFC_EUNSUPPORTED): the contraction on the tensor cores
+ * (tcgen05) in 128-cell tiles, A~0 split into TF32 or BF16 parts on the host, G~_K per
+ * point in FP32 split the same way on the device, A_K written as float. The split
+ * precisions keep FP32 accuracy; FFC_TF32 alone has TF32's 11-bit precision.
+ * FFC_EINVAL for other precisions or bad pointers.
  *
  * ffc_assemble_quadrature -- Algorithm 2 fused, as ffc_assemble:
  *   csr_val[slot[e][i1][i2]] += A_K[e][i1][i2]   (FP64 atomic adds)

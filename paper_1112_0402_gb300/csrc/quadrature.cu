@@ -34,6 +34,7 @@
 #include <vector>
 
 #include "ffc_internal.h"
+#include "tc_common.cuh"
 
 struct ffc_qform {
   int kind = 0, d = 0, q = 0, g = 0, p = 0;
@@ -50,6 +51,8 @@ struct ffc_qform {
     float* at_f32 = nullptr;   // [K][ne32], all entries, padded to a multiple of 4
     double* dgeo = nullptr;
     uint16_t* epair = nullptr;  // [n(n+1)/2]: i1 << 8 | i2
+    void* tc_part[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};  // TF32 / BF16 parts
+    float* dgeo32 = nullptr;  // geometry basis gradients in FP32 (the tensor-core producers)
   };
   std::mutex lock;
   std::map<int, Dev> dev;
@@ -442,6 +445,432 @@ int launch_quad_prec(const QParams& prm, int precision, bool assemble, cudaStrea
   return assemble ? launch_quad<D, FORM, float, true, false>(prm, s) : launch_quad<D, FORM, float, false, false>(prm, s);
 }
 
+// ------------------------------------------------------------------ tensor cores
+// The same contraction on tcgen05 for forms whose element tensor fits one M-tile (at most
+// 128 entries: P1 and P2), D[i][e] = sum_j A~0[i][j] G~[e][j] with M = entries, N = 128
+// cells, K = points x geometry entries, in K chunks of 48 columns (8 points of the 3D
+// Poisson form): both operands are streamed per chunk. A~0 is split on the host into
+// TF32 or BF16 parts and laid out per chunk in the K-major core-matrix layout, one 1-D
+// bulk copy per part; G~ is produced per chunk by four warps (one cell per thread: F'
+// at the chunk's points in FP32 from FP64 node differences, its determinant and adjugate,
+// split into the same parts) into a second ring. One thread issues the split products
+// (the correction products into their own TMEM accumulator), four warps drain TMEM to
+// A_K. Warps: 0-3 producers, 4-7 drainers, 8 MMA, 9 TMA; 2 A stages, 2 B stages, two TMEM
+// accumulators (cell tiles alternate). Every mbarrier wait is bounded.
+namespace tq {
+using namespace ffc::tc;
+
+constexpr int QKCH = 48;  // K columns per chunk (a multiple of both MMA K steps)
+constexpr int TQ_THREADS = 320;
+
+template <int D, int FORM, int G, int MODE>
+struct TqCfg {
+  using S = Split<MODE>;
+  static constexpr int NG = FORM == FFC_MASS ? 1 : D * (D + 1) / 2;
+  static constexpr int PPC = QKCH / NG;                // points per chunk
+  static constexpr int NGEO = G == 1 ? D + 1 : (D + 1) * (D + 2) / 2;
+  static constexpr int KCC = QKCH / S::EPC;            // core-matrix columns per chunk
+  static constexpr uint32_t CH_BYTES = M_TILE * QKCH * S::ESIZE;  // one part of one chunk (A or B)
+  static constexpr uint32_t STAGE_BYTES = S::PARTS * CH_BYTES;
+  static constexpr int ACC_COLS = S::NPROD > 1 ? 2 * N_CELLS : N_CELLS;
+  static constexpr uint32_t TMEM_COLS = 2 * ACC_COLS;
+  static_assert(QKCH % NG == 0 && QKCH % S::KSTEP == 0, "chunk width");
+};
+
+struct TqParams {
+  const int32_t* cells;
+  const double* nodes;
+  long long n_nodes, n_elem;
+  const float* dgeo;        // [nq][NGEO][D]
+  const void* a_part[3];    // [NCH][128 x QKCH] per part
+  float* out;               // A_K [n_elem][nn]
+  int nn, nq, nch;
+  unsigned* status;
+};
+
+template <int D, int FORM, int G, int MODE>
+__global__ void __launch_bounds__(TQ_THREADS, 1) tq_kernel(TqParams p) {
+  using C = TqCfg<D, FORM, G, MODE>;
+  using S = Split<MODE>;
+  constexpr int NG = C::NG, NGEO = C::NGEO;
+  extern __shared__ __align__(1024) unsigned char smem[];
+  unsigned char* As = smem;                                  // 2 x STAGE_BYTES
+  unsigned char* Bs = smem + 2 * C::STAGE_BYTES;             // 2 x STAGE_BYTES
+  float* dg = reinterpret_cast<float*>(smem + 4 * C::STAGE_BYTES);  // [nq][NGEO][D]
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + 4 * C::STAGE_BYTES +
+                                               (size_t(p.nq) * NGEO * D * 4 + 15) / 16 * 16);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 12);
+  __shared__ int abort_flag;
+  constexpr int A_FULL = 0, A_EMPTY = 2, B_FULL = 4, B_EMPTY = 6, ACC_FULL = 8, ACC_EMPTY = 10;
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  auto bar = [&](int k) { return smem_u32(&bars[k]); };
+  for (int i = t; i < p.nq * NGEO * D; i += TQ_THREADS) dg[i] = p.dgeo[i];
+  if (t == 0) {
+    for (int k = 0; k < 2; ++k) {
+      mbar_init(bar(A_FULL + k), 1);
+      mbar_init(bar(A_EMPTY + k), 1);
+      mbar_init(bar(B_FULL + k), 128);
+      mbar_init(bar(B_EMPTY + k), 1);
+      mbar_init(bar(ACC_FULL + k), 1);
+      mbar_init(bar(ACC_EMPTY + k), 128);
+    }
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(C::TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const long long n_tiles = (p.n_elem + N_CELLS - 1) / N_CELLS;
+  const long long my_tiles = blockIdx.x < n_tiles ? (n_tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  const long long total = my_tiles * p.nch;  // chunks this CTA consumes
+  if (warp == 9) {
+    // ---------------------------------------------------------------- TMA: A~0 chunks
+    if (lane == 0) {
+      bool ok = true;
+      for (long long g = 0; g < total && ok; ++g) {
+        const int s = int(g & 1);
+        if (g >= 2) ok = mbar_wait_or_abort(bar(A_EMPTY + s), uint32_t((g - 2) >> 1) & 1u, &abort_flag);
+        if (!ok) break;
+        const long long c = g % p.nch;
+        mbar_expect_tx(bar(A_FULL + s), C::STAGE_BYTES);
+#pragma unroll
+        for (int q = 0; q < S::PARTS; ++q)
+          bulk_g2s(smem_u32(As + s * C::STAGE_BYTES + q * C::CH_BYTES),
+                   static_cast<const unsigned char*>(p.a_part[q]) + size_t(c) * C::CH_BYTES, C::CH_BYTES,
+                   bar(A_FULL + s));
+      }
+      if (!ok) {
+        atomicOr(p.status, FFC_FLAG_TIMEOUT);
+        abort_flag = 1;
+      }
+    }
+  } else if (warp == 8) {
+    // ---------------------------------------------------------------- MMA issue
+    if (lane == 0) {
+      constexpr uint32_t IDESC = S::idesc(M_TILE, N_CELLS);
+      constexpr uint32_t SBO = C::KCC * 128;
+      constexpr int KS = QKCH / S::KSTEP;
+      bool ok = true;
+      long long g = 0;
+      for (long long ct = 0; ct < my_tiles && ok; ++ct) {
+        const int acc = int(ct & 1);
+        if (ct >= 2) ok = mbar_wait_or_abort(bar(ACC_EMPTY + acc), uint32_t((ct - 2) >> 1) & 1u, &abort_flag);
+        if (!ok) break;
+        const uint32_t d_main = tmem + uint32_t(acc * C::ACC_COLS);
+        const uint32_t d_corr = d_main + uint32_t(N_CELLS);
+        for (int c = 0; c < p.nch && ok; ++c, ++g) {
+          const int s = int(g & 1);
+          const uint32_t ph = uint32_t(g >> 1) & 1u;
+          ok = mbar_wait_or_abort(bar(A_FULL + s), ph, &abort_flag) && mbar_wait_or_abort(bar(B_FULL + s), ph, &abort_flag);
+          if (!ok) break;
+          fence_after();
+#pragma unroll
+          for (int ks = 0; ks < KS; ++ks) {
+#pragma unroll
+            for (int k = 0; k < S::NPROD; ++k) {
+              const uint64_t da = smem_desc(smem_u32(As + s * C::STAGE_BYTES + S::pa(k) * C::CH_BYTES) + ks * 256, 128, SBO);
+              const uint64_t db = smem_desc(smem_u32(Bs + s * C::STAGE_BYTES + S::pb(k) * C::CH_BYTES) + ks * 256, 128, SBO);
+              const bool first = c == 0 && ks == 0;
+              if (k == S::NPROD - 1) mma<S::BF16>(d_main, da, db, IDESC, first ? 0u : 1u);
+              else mma<S::BF16>(d_corr, da, db, IDESC, (first && k == 0) ? 0u : 1u);
+            }
+          }
+          mma_commit(bar(A_EMPTY + s));
+          mma_commit(bar(B_EMPTY + s));
+        }
+        if (ok) mma_commit(bar(ACC_FULL + acc));
+      }
+      if (!ok) {
+        atomicOr(p.status, FFC_FLAG_TIMEOUT);
+        abort_flag = 1;
+      }
+      if (g > 0) mbar_wait(bar(A_EMPTY + int((g - 1) & 1)), uint32_t((g - 1) >> 1) & 1u);  // last chain done
+    }
+  } else if (warp < 4) {
+    // ---------------------------------------------------------------- producers: G~ chunks
+    bool ok = true;
+    long long g = 0;
+    for (long long ct = 0; ct < my_tiles && ok; ++ct) {
+      const long long e = (blockIdx.x + ct * gridDim.x) * N_CELLS + t;
+      // node coordinates relative to node 0 (FP64 differences, rounded to FP32) and h^D
+      float xr[NGEO][D];
+      double hd = 0.0;
+      const bool live = e < p.n_elem;
+      {
+        long long id0 = live ? p.cells[e * NGEO] : 0;
+        if (id0 < 0 || id0 >= p.n_nodes) {
+          atomicOr(p.status, FFC_FLAG_BOUNDS);
+          id0 = 0;
+        }
+        double h2 = 0.0;
+#pragma unroll
+        for (int nd = 0; nd < NGEO; ++nd) {
+          long long id = live ? p.cells[e * NGEO + nd] : id0;
+          if (id < 0 || id >= p.n_nodes) {
+            atomicOr(p.status, FFC_FLAG_BOUNDS);
+            id = id0;
+          }
+          double sq = 0.0;
+#pragma unroll
+          for (int a = 0; a < D; ++a) {
+            const double dx = p.nodes[id * D + a] - p.nodes[id0 * D + a];
+            xr[nd][a] = float(dx);
+            sq += dx * dx;
+          }
+          if (nd >= 1 && nd <= D) h2 = fmax(h2, sq);
+        }
+        hd = D == 2 ? h2 : h2 * sqrt(h2);
+      }
+      bool degenerate = false;
+      for (int c = 0; c < p.nch && ok; ++c, ++g) {
+        const int s = int(g & 1);
+        if (g >= 2) ok = mbar_wait_or_abort(bar(B_EMPTY + s), uint32_t((g - 2) >> 1) & 1u, &abort_flag);
+        if (!ok) break;
+        float col[QKCH];
+#pragma unroll
+        for (int pp = 0; pp < C::PPC; ++pp) {
+          const int k = c * C::PPC + pp;
+          if (!live || k >= p.nq) {
+#pragma unroll
+            for (int gg = 0; gg < NG; ++gg) col[pp * NG + gg] = 0.f;
+            continue;
+          }
+          const float* dk = dg + size_t(k) * NGEO * D;
+          float J[D][D];
+#pragma unroll
+          for (int a = 0; a < D; ++a)
+#pragma unroll
+            for (int b = 0; b < D; ++b) J[a][b] = 0.f;
+#pragma unroll
+          for (int nd = 1; nd < NGEO; ++nd)
+#pragma unroll
+            for (int a = 0; a < D; ++a)
+#pragma unroll
+              for (int b = 0; b < D; ++b) J[a][b] = fmaf(xr[nd][a], dk[nd * D + b], J[a][b]);
+          float A[D][D];
+          const float det = det_adj<D, float>(J, A);
+          if (!(fabs(double(det)) > 1e-14 * hd)) degenerate = true;
+          const float ad = fabsf(det);
+          if constexpr (FORM == FFC_MASS) {
+            col[pp] = ad;
+          } else {
+            const float r = 1.f / ad;
+#pragma unroll
+            for (int a = 0; a < D; ++a)
+#pragma unroll
+              for (int b = a; b < D; ++b) {
+                float sq = 0.f;
+#pragma unroll
+                for (int cc = 0; cc < D; ++cc) sq = fmaf(A[a][cc], A[b][cc], sq);
+                col[pp * NG + qsym<D>(a, b)] = sq * r;
+              }
+          }
+        }
+        // split into the parts and write this cell's row of the chunk, 16 bytes at a time
+        unsigned char* bs = Bs + s * C::STAGE_BYTES;
+#pragma unroll
+        for (int kc = 0; kc < C::KCC; ++kc) {
+          uint32_t w[S::PARTS][4];
+#pragma unroll
+          for (int j = 0; j < S::EPC; ++j) {
+            typename S::Store parts[3];
+            split_f32<MODE>(col[kc * S::EPC + j], parts);
+#pragma unroll
+            for (int qq = 0; qq < S::PARTS; ++qq) {
+              if constexpr (S::BF16) {
+                if (j & 1) w[qq][j >> 1] |= uint32_t(parts[qq]) << 16;
+                else w[qq][j >> 1] = uint32_t(parts[qq]);
+              } else {
+                w[qq][j] = uint32_t(parts[qq]);
+              }
+            }
+          }
+          const uint32_t o = core_offset(t, kc * S::EPC, C::KCC, S::EPC) * S::ESIZE;
+#pragma unroll
+          for (int qq = 0; qq < S::PARTS; ++qq)
+            *reinterpret_cast<uint4*>(bs + qq * C::CH_BYTES + o) = make_uint4(w[qq][0], w[qq][1], w[qq][2], w[qq][3]);
+        }
+        fence_proxy_async();
+        mbar_arrive(bar(B_FULL + s));
+      }
+      if (degenerate) atomicOr(p.status, FFC_FLAG_DEGENERATE);
+    }
+    if (!ok) {
+      atomicOr(p.status, FFC_FLAG_TIMEOUT);
+      abort_flag = 1;
+    }
+  } else {
+    // ---------------------------------------------------------------- drainers: TMEM -> A_K
+    bool ok = true;
+    const int q4 = warp & 3;
+    const int i = q4 * 32 + lane;  // element-tensor entry (TMEM lane)
+    for (long long ct = 0; ct < my_tiles && ok; ++ct) {
+      const int acc = int(ct & 1);
+      ok = mbar_wait_or_abort(bar(ACC_FULL + acc), uint32_t(ct >> 1) & 1u, &abort_flag);
+      if (__any_sync(0xffffffffu, !ok)) {
+        ok = false;
+        break;
+      }
+      fence_after();
+      const long long e0 = (blockIdx.x + ct * gridDim.x) * N_CELLS;
+      const uint32_t taddr = tmem + (uint32_t(q4 * 32) << 16) + uint32_t(acc * C::ACC_COLS);
+#pragma unroll 1
+      for (int c = 0; c < N_CELLS / 32; ++c) {
+        uint32_t rv[32];
+        float v[32];
+        tmem_ld16_issue(taddr + c * 32, rv);
+        tmem_ld16_issue(taddr + c * 32 + 16, rv + 16);
+        if constexpr (S::NPROD > 1) {
+          uint32_t rw[32];
+          tmem_ld16_issue(taddr + N_CELLS + c * 32, rw);
+          tmem_ld16_issue(taddr + N_CELLS + c * 32 + 16, rw + 16);
+          tmem_wait_ld();
+#pragma unroll
+          for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(rv[j]) + __uint_as_float(rw[j]);
+        } else {
+          tmem_wait_ld();
+#pragma unroll
+          for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(rv[j]);
+        }
+        if (i < p.nn) {
+          const long long ec = e0 + c * 32;
+          float* dst = p.out + ec * p.nn + i;
+#pragma unroll
+          for (int j = 0; j < 32; ++j)
+            if (ec + j < p.n_elem) __stcs(dst + j * p.nn, v[j]);
+        }
+      }
+      fence_before();
+      mbar_arrive(bar(ACC_EMPTY + acc));
+    }
+    if (!ok) {
+      if (lane == 0) atomicOr(p.status, FFC_FLAG_TIMEOUT);
+      abort_flag = 1;
+    }
+  }
+  fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(C::TMEM_COLS));
+  }
+}
+
+template <int MODE>
+int upload_tq(ffc_qform* f, ffc_qform::Dev* dv, int nch) {
+  using S = Split<MODE>;
+  const int fam = S::BF16 ? 1 : 0;
+  std::lock_guard<std::mutex> g(f->lock);
+  if (dv->tc_part[fam][S::PARTS - 1] && dv->dgeo32) return FFC_OK;
+  const int nn = f->n * f->n, K = f->K;
+  const size_t per = size_t(nch) * M_TILE * QKCH;  // elements per part
+  const int nparts = S::BF16 ? 3 : 2;  // a family uploads all its parts once
+  std::vector<std::vector<typename S::Store>> parts(nparts, std::vector<typename S::Store>(per, 0));
+  for (int i = 0; i < nn; ++i)
+    for (int j = 0; j < K; ++j) {
+      double r = f->At[size_t(i) * K + j];
+      const size_t o = size_t(j / QKCH) * (M_TILE * QKCH) + core_offset(i, j % QKCH, QKCH / S::EPC, S::EPC);
+      for (int q = 0; q < nparts; ++q) {
+        if constexpr (S::BF16) {
+          const uint16_t b = host_bf16_bits(r);
+          parts[q][o] = b;
+          r -= host_value(uint32_t(b) << 16);
+        } else {
+          const uint32_t b = host_tf32_bits(r);
+          parts[q][o] = b;
+          r -= host_value(b);
+        }
+      }
+    }
+  cudaError_t e = cudaSuccess;
+  for (int q = 0; q < nparts && e == cudaSuccess; ++q) {
+    cudaFree(dv->tc_part[fam][q]);
+    dv->tc_part[fam][q] = nullptr;
+    if ((e = cudaMalloc(&dv->tc_part[fam][q], per * sizeof(typename S::Store))) == cudaSuccess)
+      e = cudaMemcpy(dv->tc_part[fam][q], parts[q].data(), per * sizeof(typename S::Store), cudaMemcpyHostToDevice);
+  }
+  if (e == cudaSuccess && !dv->dgeo32) {
+    std::vector<float> d32(f->dgeo.begin(), f->dgeo.end());
+    if ((e = cudaMalloc(&dv->dgeo32, d32.size() * sizeof(float))) == cudaSuccess)
+      e = cudaMemcpy(dv->dgeo32, d32.data(), d32.size() * sizeof(float), cudaMemcpyHostToDevice);
+  }
+  return e == cudaSuccess ? FFC_OK : cuda_fail(e, "ffc_tabulate_quadrature: tensor-core operands");
+}
+
+template <int D, int FORM, int G, int MODE>
+int launch_tq(ffc_qform* f, ffc_qform::Dev* dv, long long n_elem, const int32_t* cells, const double* nodes,
+              long long n_nodes, float* out, unsigned* status, cudaStream_t s) {
+  using C = TqCfg<D, FORM, G, MODE>;
+  using S = Split<MODE>;
+  const int nch = (f->K + QKCH - 1) / QKCH;
+  int rc = upload_tq<MODE>(f, dv, nch);
+  if (rc != FFC_OK) return rc;
+  TqParams p{};
+  p.cells = cells;
+  p.nodes = nodes;
+  p.n_nodes = n_nodes;
+  p.n_elem = n_elem;
+  p.dgeo = dv->dgeo32;
+  for (int q = 0; q < 3; ++q) p.a_part[q] = dv->tc_part[S::BF16 ? 1 : 0][q];
+  p.out = out;
+  p.nn = f->n * f->n;
+  p.nq = f->nq;
+  p.nch = nch;
+  p.status = status;
+  const size_t smem = 4 * size_t(C::STAGE_BYTES) + (size_t(f->nq) * C::NGEO * D * 4 + 15) / 16 * 16 + 12 * 8 + 16;
+  int dev = 0, optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (smem > size_t(optin)) {
+    set_error("ffc_tabulate_quadrature: the rule's geometry tables do not fit next to the operand stages");
+    return FFC_EINVAL;
+  }
+  auto kern = tq_kernel<D, FORM, G, MODE>;
+  int sms = 0;
+  if (launch_config(reinterpret_cast<const void*>(kern), TQ_THREADS, smem, -1, &sms, nullptr) != FFC_OK)
+    return FFC_ECUDA;
+  const long long n_tiles = (n_elem + N_CELLS - 1) / N_CELLS;
+  const long long grid = std::min<long long>(sms, n_tiles);
+  kern<<<unsigned(std::max<long long>(grid, 1)), TQ_THREADS, smem, s>>>(p);
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? FFC_OK : cuda_fail(e, "tq_kernel launch");
+}
+
+template <int D, int FORM, int G>
+int launch_tq_mode(ffc_qform* f, ffc_qform::Dev* dv, int precision, long long n_elem, const int32_t* cells,
+                   const double* nodes, long long n_nodes, float* out, unsigned* status, cudaStream_t s) {
+  switch (precision) {
+    case FFC_TF32: return launch_tq<D, FORM, G, MODE_TF32>(f, dv, n_elem, cells, nodes, n_nodes, out, status, s);
+    case FFC_TF32X3: return launch_tq<D, FORM, G, MODE_TF32X3>(f, dv, n_elem, cells, nodes, n_nodes, out, status, s);
+    default: return launch_tq<D, FORM, G, MODE_BF16X3>(f, dv, n_elem, cells, nodes, n_nodes, out, status, s);
+  }
+}
+
+int run_tq(ffc_qform* f, ffc_qform::Dev* dv, int precision, long long n_elem, const int32_t* cells,
+           const double* nodes, long long n_nodes, float* out, unsigned* status, cudaStream_t s) {
+  const bool mass = f->kind == FFC_MASS;
+  if (f->d == 2) {
+    if (f->g == 1)
+      return mass ? launch_tq_mode<2, FFC_MASS, 1>(f, dv, precision, n_elem, cells, nodes, n_nodes, out, status, s)
+                  : launch_tq_mode<2, FFC_POISSON, 1>(f, dv, precision, n_elem, cells, nodes, n_nodes, out, status, s);
+    return mass ? launch_tq_mode<2, FFC_MASS, 2>(f, dv, precision, n_elem, cells, nodes, n_nodes, out, status, s)
+                : launch_tq_mode<2, FFC_POISSON, 2>(f, dv, precision, n_elem, cells, nodes, n_nodes, out, status, s);
+  }
+  if (f->g == 1)
+    return mass ? launch_tq_mode<3, FFC_MASS, 1>(f, dv, precision, n_elem, cells, nodes, n_nodes, out, status, s)
+                : launch_tq_mode<3, FFC_POISSON, 1>(f, dv, precision, n_elem, cells, nodes, n_nodes, out, status, s);
+  return mass ? launch_tq_mode<3, FFC_MASS, 2>(f, dv, precision, n_elem, cells, nodes, n_nodes, out, status, s)
+              : launch_tq_mode<3, FFC_POISSON, 2>(f, dv, precision, n_elem, cells, nodes, n_nodes, out, status, s);
+}
+
+}  // namespace tq
+
 int run_quadrature(const ffc_qform* f, int64_t n_elem, const int32_t* cells, const double* nodes, int64_t n_nodes,
                    void* out, const int32_t* slot, int64_t nnz, int precision, void* stream, const char* who) {
   ffc_qform::Dev* dv = nullptr;
@@ -471,10 +900,17 @@ int run_quadrature(const ffc_qform* f, int64_t n_elem, const int32_t* cells, con
 }
 
 int check_args(const ffc_qform* f, int64_t n_elem, const int32_t* cells, const double* nodes, int64_t n_nodes,
-               int precision, const char* who) {
-  if (!f || n_elem < 0 || n_nodes < 0 || (precision != FFC_FP64 && precision != FFC_FP32)) {
-    set_error(std::string(who) + ": invalid argument (precision must be FFC_FP64 or FFC_FP32)");
+               int precision, const char* who, bool tensor_cores = false) {
+  const bool tc = precision == FFC_TF32 || precision == FFC_TF32X3 || precision == FFC_BF16X3;
+  if (!f || n_elem < 0 || n_nodes < 0 || (precision != FFC_FP64 && precision != FFC_FP32 && !(tensor_cores && tc))) {
+    set_error(std::string(who) + (tensor_cores ? ": invalid argument (precision FFC_FP64, FFC_FP32, FFC_TF32, "
+                                                 "FFC_TF32X3 or FFC_BF16X3)"
+                                               : ": invalid argument (precision must be FFC_FP64 or FFC_FP32)"));
     return FFC_EINVAL;
+  }
+  if (tc && f->n * f->n > tc::M_TILE) {
+    set_error(std::string(who) + ": the tensor-core precisions take element tensors of at most 128 entries");
+    return FFC_EUNSUPPORTED;
   }
   if (n_elem > 0 && (!cells || !nodes || n_nodes == 0 || (reinterpret_cast<uintptr_t>(nodes) & 7))) {
     set_error(std::string(who) + ": null or misaligned cells / nodes");
@@ -543,6 +979,9 @@ extern "C" void ffc_qform_destroy(ffc_qform* f) {
     cudaFree(kv.second.at_f32);
     cudaFree(kv.second.dgeo);
     cudaFree(kv.second.epair);
+    cudaFree(kv.second.dgeo32);
+    for (auto& fam : kv.second.tc_part)
+      for (void* q : fam) cudaFree(q);
     cudaSetDevice(prev);
   }
   delete f;
@@ -550,11 +989,22 @@ extern "C" void ffc_qform_destroy(ffc_qform* f) {
 
 extern "C" int ffc_tabulate_quadrature(const ffc_qform* f, int64_t n_elem, const int32_t* cells, const double* nodes,
                                        int64_t n_nodes, void* A_K, int precision, void* stream) {
-  int rc = check_args(f, n_elem, cells, nodes, n_nodes, precision, "ffc_tabulate_quadrature");
+  int rc = check_args(f, n_elem, cells, nodes, n_nodes, precision, "ffc_tabulate_quadrature", true);
   if (rc != FFC_OK || n_elem == 0) return rc;
   if (!A_K || (reinterpret_cast<uintptr_t>(A_K) & 15)) {
     set_error("ffc_tabulate_quadrature: A_K null or not 16-byte aligned");
     return FFC_EINVAL;
+  }
+  if (precision != FFC_FP64 && precision != FFC_FP32) {
+    ffc_qform::Dev* dv = nullptr;
+    if ((rc = ensure_qdev(const_cast<ffc_qform*>(f), &dv)) != FFC_OK) return rc;
+    unsigned* st = status_word();
+    if (!st) {
+      set_error("ffc_tabulate_quadrature: status word allocation failed");
+      return FFC_ECUDA;
+    }
+    return tq::run_tq(const_cast<ffc_qform*>(f), dv, precision, n_elem, cells, nodes, n_nodes, static_cast<float*>(A_K),
+                      st, static_cast<cudaStream_t>(stream));
   }
   return run_quadrature(f, n_elem, cells, nodes, n_nodes, A_K, nullptr, 0, precision, stream,
                         "ffc_tabulate_quadrature");

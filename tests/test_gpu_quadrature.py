@@ -156,3 +156,42 @@ def test_quadrature_flags_and_limits(F):
     out = F.tabulate_quadrature(qf, empty, _dev(cm.nodes), precision="fp64")
     assert out.shape == (0, 10, 10)
     assert F.status_poll() == 0
+
+
+@pytest.mark.parametrize("d,n", [(2, 5), (3, 2)])
+@pytest.mark.parametrize("form,q", [(0, 1), (1, 1), (0, 2), (1, 2)])
+@pytest.mark.parametrize("prec,tol", [("bf16x3", 1e-6), ("tf32x3", 3e-6), ("tf32", 5e-3)])
+def test_tensor_core_quadrature_matches_the_oracle(F, d, n, form, q, prec, tol):
+    """The tcgen05 contraction (element tensors of at most 128 entries) on curved cells:
+    BF16x3 within the 1e-6 target, 3xTF32 within 3e-6 (two TF32 parts), single TF32
+    within its 11-bit precision."""
+    cm = curved_mesh(d, n, eps=0.12)
+    qf = F.QForm(form, _cell(F, d), q, 2)
+    ref = OC.element_tensors_curved(form, gather_nodes(cm), q, 2, qf.quad_degree)
+    got = F.tabulate_quadrature(qf, _dev(cm.cells), _dev(cm.nodes), precision=prec).double().cpu().numpy()
+    assert F.status_poll() == 0
+    assert _rel(got, ref) <= tol
+
+
+@pytest.mark.parametrize("count", [1, 127, 129, 300])
+def test_tensor_core_quadrature_ragged_tiles(F, count):
+    """Cell counts around the 128-cell tile: every cell written, nothing beyond."""
+    import torch
+
+    cm = curved_mesh(3, 4, eps=0.1)
+    qf = F.QForm(1, F.TETRAHEDRON, 2, 2)
+    cells = _dev(cm.cells[:count])
+    out = torch.full((count + 1, 10, 10), 7.0, dtype=torch.float32, device="cuda")
+    F.tabulate_quadrature(qf, cells, _dev(cm.nodes), precision="bf16x3", out=out[:count])
+    assert F.status_poll() == 0
+    ref = OC.element_tensors_curved(1, gather_nodes(cm)[:count], 2, 2, qf.quad_degree)
+    assert _rel(out[:count].double().cpu().numpy(), ref) <= 1e-6
+    assert bool((out[count] == 7.0).all())
+
+
+def test_tensor_core_quadrature_limits(F):
+    cm = curved_mesh(3, 1, eps=0.1)
+    big = F.QForm(1, F.TETRAHEDRON, 3, 2)  # 400 entries: more than one 128-entry tile
+    with pytest.raises(F.FFCError) as e:
+        F.tabulate_quadrature(big, _dev(cm.cells), _dev(cm.nodes), precision="bf16x3")
+    assert e.value.code == -5

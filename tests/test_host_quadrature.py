@@ -105,3 +105,19 @@ def test_qform_validates_arguments():
     assert L.ffc_tabulate_quadrature(qf.handle, 4, None, None, 10, None, 7, None) == -1
     assert L.ffc_assemble_quadrature(qf.handle, 4, None, None, 10, None, None, 5, 0, None) == -1
     assert L.ffc_tabulate_quadrature(qf.handle, 0, None, None, 0, None, 0, None) == 0
+
+
+def test_tensor_core_precisions_are_checked_before_device_work():
+    """ffc_tabulate_quadrature takes the tensor-core precisions for element tensors of at
+    most 128 entries (refused with FFC_EUNSUPPORTED above), ffc_assemble_quadrature does
+    not take them at all."""
+    F = _F()
+    from paper_1112_0402_gb300 import _capi
+
+    L = _capi.lib()
+    p3 = F.QForm(F.POISSON, F.TETRAHEDRON, 3, 2)  # 20 x 20 = 400 entries
+    p2 = F.QForm(F.POISSON, F.TETRAHEDRON, 2, 2)
+    for prec in (F.TF32, F.TF32X3, F.BF16X3):
+        assert L.ffc_tabulate_quadrature(p3.handle, 4, None, None, 10, None, prec, None) == -5
+        assert L.ffc_tabulate_quadrature(p2.handle, 4, None, None, 10, None, prec, None) == -1  # null cells
+        assert L.ffc_assemble_quadrature(p2.handle, 4, None, None, 10, None, None, 5, prec, None) == -1
