@@ -1102,20 +1102,39 @@ def measure_other(F, args, device, workload):
         detail["tabulate_fp64_ms"] = _timed(lambda: F.tabulate_quadrature(qf, cells, nodes, "fp64", out=A64),
                                             args.steps, args.warmup) * 1e3
         A32 = torch.empty((cm.n_elem, n, n), dtype=torch.float32, device=device)
+        pk = compute_peaks(F)
+
+        def max_rel(A):
+            d = (A.double() - A64).reshape(cm.n_elem, -1).norm(dim=1) / A64.reshape(cm.n_elem, -1).norm(dim=1)
+            return float(d.max())
+
+        # the SIMT FP32 contraction and the tensor-core ones; the headline is 3xTF32 (FP32
+        # accuracy; the worst cell's relative error against the FP64 result is recorded)
+        t32 = _timed(lambda: F.tabulate_quadrature(qf, cells, nodes, "fp32", out=A32), args.steps, args.warmup)
+        assert F.status_poll() == 0
+        flops32 = 2.0 * n * n * qf.k_contract * cm.n_elem  # executed by the SIMT kernel (all n^2 entries)
+        detail["simt_fp32"] = {"ms": t32 * 1e3, "max_rel_err_vs_fp64": max_rel(A32),
+                               "tflops": flops32 / t32 / 1e12, "fp32_fma_frac": flops32 / t32 / 1e12 / pk["fp32_fma"]}
+        for prec in ("tf32", "bf16x3"):
+            tp = _timed(lambda: F.tabulate_quadrature(qf, cells, nodes, prec, out=A32), args.steps, args.warmup)
+            assert F.status_poll() == 0
+            detail[prec] = {"ms": tp * 1e3, "max_rel_err_vs_fp64": max_rel(A32)}
         clocks.start()
-        t = _timed(lambda: F.tabulate_quadrature(qf, cells, nodes, "fp32", out=A32), args.steps, args.warmup)
+        t = _timed(lambda: F.tabulate_quadrature(qf, cells, nodes, "tf32x3", out=A32), args.steps, args.warmup)
         clk = clocks.stop()
         assert F.status_poll() == 0
-        d = (A32.double() - A64).reshape(cm.n_elem, -1).norm(dim=1) / A64.reshape(cm.n_elem, -1).norm(dim=1)
-        detail["fp32_max_rel_err_vs_fp64"] = float(d.max())
+        detail["tf32x3_max_rel_err_vs_fp64"] = max_rel(A32)
         del A64, A32
-        # executed FLOPs of the FP32 contraction (all n^2 entries) and of the FP64 one
-        # (entries i1 <= i2)
-        flops32 = 2.0 * n * n * qf.k_contract * cm.n_elem
-        flops64 = 2.0 * n * (n + 1) / 2 * qf.k_contract * cm.n_elem
-        pk = compute_peaks(F)
+        # algorithmic FLOPs of the contraction (one product, n^2 entries) and those the
+        # tensor cores execute (128-entry M tiles, K padded to 48-column chunks, 3 products)
+        flops_alg = 2.0 * n * n * qf.k_contract * cm.n_elem
+        n_tiles = -(-cm.n_elem // 128)
+        flops_exec = 3 * 2.0 * 128 * 128 * (-(-qf.k_contract // 48) * 48) * n_tiles
+        flops64 = 2.0 * n * (n + 1) / 2 * qf.k_contract * cm.n_elem  # FP64 kernel: entries i1 <= i2
         detail["fp64_tflops"] = flops64 / (detail["tabulate_fp64_ms"] / 1e3) / 1e12
         detail["fp64_frac"] = detail["fp64_tflops"] / pk["fp64_fma"]
+        detail["tf32x3_executed_tflops"] = flops_exec / t / 1e12
+        detail["tf32x3_executed_frac"] = flops_exec / t / 1e12 / pk["tf32_mma"]
         byts = cm.n_elem * (4 * qf.n_geometry + 4 * n * n) + cm.nodes.size * 8
         # T_Q / T_T on affine cells: the headline mesh, mass and Poisson P1-P3
         m = W.tet_scalar_mesh(40)
@@ -1144,13 +1163,13 @@ def measure_other(F, args, device, workload):
             pool.close()
             pool.join()
         out.update({"metric": "element tensors/s (P2 Poisson on 40^3x6 curved tets, quadrature as contraction)",
-                    "value": cm.n_elem / t, "ms_per_step": t * 1e3, "dtype": "f32",
+                    "value": cm.n_elem / t, "ms_per_step": t * 1e3, "dtype": "tf32x3",
                     "config": {"workload": "quad_curved_p2_40", "cells": cm.n_elem, "geometry_degree": 2,
                                "l2": "output 154 MB per step > L2"},
-                    "roofline": {"bound": "alu", "achieved": flops32 / t / 1e12, "peak": pk["fp32_fma"],
-                                 "unit": "TFLOP/s", "frac": flops32 / t / 1e12 / pk["fp32_fma"],
-                                 "peak_kind": "measured (ffc_diag_peak FP32 FMA, this run)", "traffic": None,
-                                 "hbm_gbs": byts / t / 1e9, "kernel": "quad_kernel<3, POISSON, float>"},
+                    "roofline": {"bound": "tensor", "achieved": flops_alg / t / 1e12, "peak": pk["tf32_mma"],
+                                 "unit": "TFLOP/s", "frac": flops_alg / t / 1e12 / pk["tf32_mma"],
+                                 "peak_kind": "measured (ffc_diag_peak TF32 tcgen05 MMA, this run)", "traffic": None,
+                                 "hbm_gbs": byts / t / 1e9, "kernel": "tq_kernel<3, POISSON, 2, TF32X3>"},
                     "clocks": clk, "gpu_launches": args.steps,
                     "cpu_baseline": {"value": cpu_rate, "unit": "elem/s", "cores": cores, "kind": "oracle",
                                      "sample": f"{S} curved cells, point-by-point quadrature"},

@@ -52,7 +52,7 @@ struct ffc_qform {
     double* dgeo = nullptr;
     uint16_t* epair = nullptr;  // [n(n+1)/2]: i1 << 8 | i2
     void* tc_part[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};  // TF32 / BF16 parts
-    float* dgeo32 = nullptr;  // geometry basis gradients in FP32 (the tensor-core producers)
+    float* tq_table = nullptr;  // the tensor-core producers' geometry table (FP32)
   };
   std::mutex lock;
   std::map<int, Dev> dev;
@@ -460,59 +460,106 @@ int launch_quad_prec(const QParams& prm, int precision, bool assemble, cudaStrea
 namespace tq {
 using namespace ffc::tc;
 
+// Warp roles: 0-7 produce the G~ chunks (two lanes per cell, each half of a chunk's
+// columns), 8-11 drain TMEM into A_K, 12 issues the MMAs, 13 streams the A~0 chunks,
+// 14-15 gather the cells' nodes and form the per-cell Jacobian coefficients one tile ahead.
 constexpr int QKCH = 48;  // K columns per chunk (a multiple of both MMA K steps)
-constexpr int TQ_THREADS = 320;
+constexpr int TQ_PRODUCER_WARPS = 8;
+constexpr int TQ_DRAIN_WARP0 = 8, TQ_MMA_WARP = 12, TQ_TMA_WARP = 13, TQ_GEO_WARP0 = 14;
+constexpr int TQ_THREADS = 512;
+constexpr int TQ_GEO_THREADS = TQ_THREADS - 32 * TQ_GEO_WARP0;
+
+// symmetric index of (b, c) in either order
+template <int D>
+__host__ __device__ constexpr int qsym_any(int b, int c) {
+  return b <= c ? (b == c ? b : (D == 2 ? 2 : (b == 0 ? (c == 1 ? 3 : 4) : 5)))
+                : (D == 2 ? 2 : (c == 0 ? (b == 1 ? 3 : 4) : 5));
+}
 
 template <int D, int FORM, int G, int MODE>
 struct TqCfg {
   using S = Split<MODE>;
   static constexpr int NG = FORM == FFC_MASS ? 1 : D * (D + 1) / 2;
   static constexpr int PPC = QKCH / NG;                // points per chunk
+  static constexpr int PPH = PPC / 2;                  // points per producer lane and chunk
   static constexpr int NGEO = G == 1 ? D + 1 : (D + 1) * (D + 2) / 2;
+  // the map's Jacobian is affine in X for geometry degree 2:
+  //   F'(X)[a][b] = J0[a][b] + sum_c H[a][(b,c)] X_c
+  // J0 = sum_n x_n (dPsi_n/dX_b)(0), H[a][(b,c)] = sum_n x_n[a] d2Psi_n/dX_b dX_c
+  static constexpr int NH = G == 2 ? D * (D + 1) / 2 : 0;
+  static constexpr int NJ = D * D + D * NH;            // per-cell coefficients
   static constexpr int KCC = QKCH / S::EPC;            // core-matrix columns per chunk
   static constexpr uint32_t CH_BYTES = M_TILE * QKCH * S::ESIZE;  // one part of one chunk (A or B)
   static constexpr uint32_t STAGE_BYTES = S::PARTS * CH_BYTES;
   static constexpr int ACC_COLS = S::NPROD > 1 ? 2 * N_CELLS : N_CELLS;
   static constexpr uint32_t TMEM_COLS = 2 * ACC_COLS;
   static_assert(QKCH % NG == 0 && QKCH % S::KSTEP == 0, "chunk width");
+  static_assert(PPC % 2 == 0 && (QKCH / 2) % S::EPC == 0, "a chunk splits into two lanes' halves");
+  // shared memory: A stages, B stages, the geometry table, the per-cell slot, barriers
+  static constexpr size_t table_floats(int nq) { return size_t(NGEO) * D + size_t(NGEO) * NH + size_t(nq) * D; }
+  static constexpr size_t off_table() { return 4 * size_t(STAGE_BYTES); }
+  static constexpr size_t off_cell(int nq) { return off_table() + (table_floats(nq) * 4 + 15) / 16 * 16; }
+  static constexpr size_t off_gbar(int nq) { return off_cell(nq) + size_t(NJ + 1) * N_CELLS * 4; }
+  static constexpr size_t off_bars(int nq) { return off_gbar(nq) + size_t(2) * NG * N_CELLS * 4; }
+  static constexpr size_t smem_bytes(int nq) { return off_bars(nq) + NBARS * 8 + 16; }
+  static constexpr int NBARS = 20;
 };
 
 struct TqParams {
   const int32_t* cells;
   const double* nodes;
   long long n_nodes, n_elem;
-  const float* dgeo;        // [nq][NGEO][D]
+  const float* table;       // [NGEO][D] dPsi(0), [NGEO][NH] second derivatives, [nq][D] points
+  const float* a0sum;       // [nn][NG]: A~0 summed over the points (the centroid term)
   const void* a_part[3];    // [NCH][128 x QKCH] per part
   float* out;               // A_K [n_elem][nn]
   int nn, nq, nch;
   unsigned* status;
 };
 
+// every lane of the warp waits; the warp goes on only when all of them saw the phase
+__device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t phase, volatile int* abort_flag) {
+  const bool ok = mbar_wait_or_abort(bar, phase, abort_flag);
+  return __all_sync(0xffffffffu, ok);
+}
+
 template <int D, int FORM, int G, int MODE>
 __global__ void __launch_bounds__(TQ_THREADS, 1) tq_kernel(TqParams p) {
   using C = TqCfg<D, FORM, G, MODE>;
   using S = Split<MODE>;
-  constexpr int NG = C::NG, NGEO = C::NGEO;
+  constexpr int NG = C::NG, NGEO = C::NGEO, NH = C::NH, NJ = C::NJ;
   extern __shared__ __align__(1024) unsigned char smem[];
-  unsigned char* As = smem;                                  // 2 x STAGE_BYTES
-  unsigned char* Bs = smem + 2 * C::STAGE_BYTES;             // 2 x STAGE_BYTES
-  float* dg = reinterpret_cast<float*>(smem + 4 * C::STAGE_BYTES);  // [nq][NGEO][D]
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + 4 * C::STAGE_BYTES +
-                                               (size_t(p.nq) * NGEO * D * 4 + 15) / 16 * 16);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 12);
+  unsigned char* As = smem;                          // 2 x STAGE_BYTES
+  unsigned char* Bs = smem + 2 * C::STAGE_BYTES;     // 2 x STAGE_BYTES
+  float* tab = reinterpret_cast<float*>(smem + C::off_table());
+  const float* g0 = tab;                             // [NGEO][D]
+  const float* hs = tab + NGEO * D;                  // [NGEO][NH]
+  const float* xq = hs + NGEO * NH;                  // [nq][D]
+  float* cellj = reinterpret_cast<float*>(smem + C::off_cell(p.nq));  // [NJ][128], then thr [128]
+  float* thr_s = cellj + NJ * N_CELLS;
+  float* gbar = reinterpret_cast<float*>(smem + C::off_gbar(p.nq));  // [2][NG][128]: G~ at the centroid
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + C::off_bars(p.nq));
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + C::NBARS);
   __shared__ int abort_flag;
-  constexpr int A_FULL = 0, A_EMPTY = 2, B_FULL = 4, B_EMPTY = 6, ACC_FULL = 8, ACC_EMPTY = 10;
+  constexpr int A_FULL = 0, A_EMPTY = 2, B_FULL = 4, B_EMPTY = 6, ACC_FULL = 8, ACC_EMPTY = 10, GEO_FULL = 12,
+                GEO_EMPTY = 13, GBAR_FULL = 14, GBAR_EMPTY = 16;
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
   auto bar = [&](int k) { return smem_u32(&bars[k]); };
-  for (int i = t; i < p.nq * NGEO * D; i += TQ_THREADS) dg[i] = p.dgeo[i];
+  for (int i = t; i < int(C::table_floats(p.nq)); i += TQ_THREADS) tab[i] = p.table[i];
   if (t == 0) {
     for (int k = 0; k < 2; ++k) {
       mbar_init(bar(A_FULL + k), 1);
       mbar_init(bar(A_EMPTY + k), 1);
-      mbar_init(bar(B_FULL + k), 128);
+      mbar_init(bar(B_FULL + k), TQ_PRODUCER_WARPS);
       mbar_init(bar(B_EMPTY + k), 1);
       mbar_init(bar(ACC_FULL + k), 1);
-      mbar_init(bar(ACC_EMPTY + k), 128);
+      mbar_init(bar(ACC_EMPTY + k), 4);
+    }
+    mbar_init(bar(GEO_FULL), TQ_GEO_THREADS / 32);
+    mbar_init(bar(GEO_EMPTY), TQ_PRODUCER_WARPS);
+    for (int k = 0; k < 2; ++k) {
+      mbar_init(bar(GBAR_FULL + k), TQ_PRODUCER_WARPS);
+      mbar_init(bar(GBAR_EMPTY + k), 4);
     }
     abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -529,7 +576,7 @@ __global__ void __launch_bounds__(TQ_THREADS, 1) tq_kernel(TqParams p) {
   const long long n_tiles = (p.n_elem + N_CELLS - 1) / N_CELLS;
   const long long my_tiles = blockIdx.x < n_tiles ? (n_tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
   const long long total = my_tiles * p.nch;  // chunks this CTA consumes
-  if (warp == 9) {
+  if (warp == TQ_TMA_WARP) {
     // ---------------------------------------------------------------- TMA: A~0 chunks
     if (lane == 0) {
       bool ok = true;
@@ -550,7 +597,7 @@ __global__ void __launch_bounds__(TQ_THREADS, 1) tq_kernel(TqParams p) {
         abort_flag = 1;
       }
     }
-  } else if (warp == 8) {
+  } else if (warp == TQ_MMA_WARP) {
     // ---------------------------------------------------------------- MMA issue
     if (lane == 0) {
       constexpr uint32_t IDESC = S::idesc(M_TILE, N_CELLS);
@@ -592,90 +639,203 @@ __global__ void __launch_bounds__(TQ_THREADS, 1) tq_kernel(TqParams p) {
       }
       if (g > 0) mbar_wait(bar(A_EMPTY + int((g - 1) & 1)), uint32_t((g - 1) >> 1) & 1u);  // last chain done
     }
-  } else if (warp < 4) {
-    // ---------------------------------------------------------------- producers: G~ chunks
+  } else if (warp >= TQ_GEO_WARP0) {
+    // ---------------------------------------------------------------- per-cell geometry, one tile ahead
+    const int gt = t - 32 * TQ_GEO_WARP0;
     bool ok = true;
-    long long g = 0;
     for (long long ct = 0; ct < my_tiles && ok; ++ct) {
-      const long long e = (blockIdx.x + ct * gridDim.x) * N_CELLS + t;
-      // node coordinates relative to node 0 (FP64 differences, rounded to FP32) and h^D
-      float xr[NGEO][D];
-      double hd = 0.0;
-      const bool live = e < p.n_elem;
-      {
+#pragma unroll 1
+      for (int half = 0; half < N_CELLS / TQ_GEO_THREADS; ++half) {
+        const int c = gt + half * TQ_GEO_THREADS;
+        const long long e = (blockIdx.x + ct * gridDim.x) * N_CELLS + c;
+        const bool live = e < p.n_elem;
+        // node coordinates relative to node 0: FP64 differences rounded to FP32
+        float xr[NGEO][D];
+        float h2 = 0.f;
         long long id0 = live ? p.cells[e * NGEO] : 0;
         if (id0 < 0 || id0 >= p.n_nodes) {
           atomicOr(p.status, FFC_FLAG_BOUNDS);
           id0 = 0;
         }
-        double h2 = 0.0;
+        double x0[D];
 #pragma unroll
-        for (int nd = 0; nd < NGEO; ++nd) {
+        for (int a = 0; a < D; ++a) x0[a] = p.nodes[id0 * D + a];
+#pragma unroll
+        for (int nd = 1; nd < NGEO; ++nd) {
           long long id = live ? p.cells[e * NGEO + nd] : id0;
           if (id < 0 || id >= p.n_nodes) {
             atomicOr(p.status, FFC_FLAG_BOUNDS);
             id = id0;
           }
-          double sq = 0.0;
+          float sq = 0.f;
 #pragma unroll
           for (int a = 0; a < D; ++a) {
-            const double dx = p.nodes[id * D + a] - p.nodes[id0 * D + a];
-            xr[nd][a] = float(dx);
-            sq += dx * dx;
+            xr[nd][a] = float(p.nodes[id * D + a] - x0[a]);
+            sq = fmaf(xr[nd][a], xr[nd][a], sq);
           }
-          if (nd >= 1 && nd <= D) h2 = fmax(h2, sq);
+          if (nd <= D) h2 = fmaxf(h2, sq);
         }
-        hd = D == 2 ? h2 : h2 * sqrt(h2);
-      }
-      bool degenerate = false;
-      for (int c = 0; c < p.nch && ok; ++c, ++g) {
-        const int s = int(g & 1);
-        if (g >= 2) ok = mbar_wait_or_abort(bar(B_EMPTY + s), uint32_t((g - 2) >> 1) & 1u, &abort_flag);
-        if (!ok) break;
-        float col[QKCH];
+        float cj[NJ];
 #pragma unroll
-        for (int pp = 0; pp < C::PPC; ++pp) {
-          const int k = c * C::PPC + pp;
+        for (int a = 0; a < D; ++a) {
+#pragma unroll
+          for (int b = 0; b < D; ++b) {
+            float s = 0.f;
+#pragma unroll
+            for (int nd = 1; nd < NGEO; ++nd) s = fmaf(xr[nd][a], g0[nd * D + b], s);
+            cj[a * D + b] = s;
+          }
+#pragma unroll
+          for (int h = 0; h < NH; ++h) {
+            float s = 0.f;
+#pragma unroll
+            for (int nd = 1; nd < NGEO; ++nd) s = fmaf(xr[nd][a], hs[nd * NH + h], s);
+            cj[D * D + a * NH + h] = s;
+          }
+        }
+        const float thr = 1e-14f * (D == 2 ? h2 : h2 * sqrtf(h2));
+        if (half == 0 && ct >= 1) ok = warp_wait(bar(GEO_EMPTY), uint32_t(ct - 1) & 1u, &abort_flag);
+        if (!ok) break;
+#pragma unroll
+        for (int j = 0; j < NJ; ++j) cellj[j * N_CELLS + c] = cj[j];
+        thr_s[c] = thr;
+      }
+      if (!ok) break;
+      __syncwarp();
+      if (lane == 0) mbar_arrive(bar(GEO_FULL));
+    }
+    if (!ok) {
+      if (lane == 0) atomicOr(p.status, FFC_FLAG_TIMEOUT);
+      abort_flag = 1;
+    }
+  } else if (warp < TQ_PRODUCER_WARPS) {
+    // ---------------------------------------------------------------- producers: G~ chunks
+    // lanes 0-7 and 8-15 take cells 0-7 of the warp's 16 (first and second half of the
+    // columns), lanes 16-31 cells 8-15: each 8-lane phase of a 16-byte store writes eight
+    // different rows of a core matrix, one bank group each
+    const int c = warp * 16 + (lane & 7) + ((lane >> 4) << 3), hlf = (lane >> 3) & 1;
+    bool ok = true;
+    long long g = 0;
+    for (long long ct = 0; ct < my_tiles && ok; ++ct) {
+      ok = warp_wait(bar(GEO_FULL), uint32_t(ct) & 1u, &abort_flag);
+      if (!ok) break;
+      float cj[NJ];
+#pragma unroll
+      for (int j = 0; j < NJ; ++j) cj[j] = cellj[j * N_CELLS + c];
+      const float thr = thr_s[c];
+      __syncwarp();
+      if (lane == 0) mbar_arrive(bar(GEO_EMPTY));
+      const long long e = (blockIdx.x + ct * gridDim.x) * N_CELLS + c;
+      const bool live = e < p.n_elem;
+      bool degenerate = false;
+      // G~ at one point from the Jacobian there
+      auto point_geometry = [&](const float (&J)[D][D], float* out) {
+        float A[D][D];
+        const float det = det_adj<D, float>(J, A);
+        if (!(fabsf(det) > thr)) degenerate = true;
+        const float ad = fabsf(det);
+        if constexpr (FORM == FFC_MASS) {
+          out[0] = ad;
+        } else {
+          const float r = __frcp_rn(ad);
+#pragma unroll
+          for (int a = 0; a < D; ++a)
+#pragma unroll
+            for (int b = a; b < D; ++b) {
+              float sq = 0.f;
+#pragma unroll
+              for (int cc = 0; cc < D; ++cc) sq = fmaf(A[a][cc], A[b][cc], sq);
+              out[qsym<D>(a, b)] = sq * r;
+            }
+        }
+      };
+      // G~ at the reference centroid: the drainers add (sum_k A~0(k)) : G~c in FP32 and
+      // the tensor cores accumulate only the deviations G~(X_k) - G~c (exactly zero on
+      // affine cells), so their FP32 accumulation error scales with the deviations
+      float gc[NG];
+      {
+        float J[D][D];
+        constexpr float xc = 1.f / (D + 1);
+#pragma unroll
+        for (int a = 0; a < D; ++a)
+#pragma unroll
+          for (int b = 0; b < D; ++b) {
+            float v = cj[a * D + b];
+#pragma unroll
+            for (int cc = 0; cc < D; ++cc)
+              if constexpr (NH > 0) v = fmaf(cj[D * D + a * NH + qsym_any<D>(b, cc)], xc, v);
+            J[a][b] = v;
+          }
+        float A[D][D];
+        const float det = det_adj<D, float>(J, A);
+        const float ad = fabsf(det);
+        if constexpr (FORM == FFC_MASS) {
+          gc[0] = ad;
+        } else {
+          const float r = __frcp_rn(ad);
+#pragma unroll
+          for (int a = 0; a < D; ++a)
+#pragma unroll
+            for (int b = a; b < D; ++b) {
+              float sq = 0.f;
+#pragma unroll
+              for (int cc = 0; cc < D; ++cc) sq = fmaf(A[a][cc], A[b][cc], sq);
+              gc[qsym<D>(a, b)] = sq * r;
+            }
+        }
+        if (G == 1 && !(ad > thr)) degenerate = true;
+        if (!live) {
+#pragma unroll
+          for (int gg = 0; gg < NG; ++gg) gc[gg] = 0.f;
+        }
+      }
+      if (ct >= 2) ok = warp_wait(bar(GBAR_EMPTY + int(ct & 1)), uint32_t((ct - 2) >> 1) & 1u, &abort_flag);
+      if (!ok) break;
+      if (hlf == 0) {
+#pragma unroll
+        for (int gg = 0; gg < NG; ++gg) gbar[(int(ct & 1) * NG + gg) * N_CELLS + c] = gc[gg];
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(bar(GBAR_FULL + int(ct & 1)));
+      for (int ch = 0; ch < p.nch && ok; ++ch, ++g) {
+        const int s = int(g & 1);
+        if (g >= 2) ok = warp_wait(bar(B_EMPTY + s), uint32_t((g - 2) >> 1) & 1u, &abort_flag);
+        if (!ok) break;
+        float col[QKCH / 2];
+#pragma unroll
+        for (int pp = 0; pp < C::PPH; ++pp) {
+          const int k = ch * C::PPC + hlf * C::PPH + pp;
           if (!live || k >= p.nq) {
 #pragma unroll
             for (int gg = 0; gg < NG; ++gg) col[pp * NG + gg] = 0.f;
             continue;
           }
-          const float* dk = dg + size_t(k) * NGEO * D;
-          float J[D][D];
+          if constexpr (G == 1) {
 #pragma unroll
-          for (int a = 0; a < D; ++a)
-#pragma unroll
-            for (int b = 0; b < D; ++b) J[a][b] = 0.f;
-#pragma unroll
-          for (int nd = 1; nd < NGEO; ++nd)
-#pragma unroll
-            for (int a = 0; a < D; ++a)
-#pragma unroll
-              for (int b = 0; b < D; ++b) J[a][b] = fmaf(xr[nd][a], dk[nd * D + b], J[a][b]);
-          float A[D][D];
-          const float det = det_adj<D, float>(J, A);
-          if (!(fabs(double(det)) > 1e-14 * hd)) degenerate = true;
-          const float ad = fabsf(det);
-          if constexpr (FORM == FFC_MASS) {
-            col[pp] = ad;
+            for (int gg = 0; gg < NG; ++gg) col[pp * NG + gg] = 0.f;
           } else {
-            const float r = 1.f / ad;
+            float X[D];
+#pragma unroll
+            for (int a = 0; a < D; ++a) X[a] = xq[k * D + a];
+            float J[D][D];
 #pragma unroll
             for (int a = 0; a < D; ++a)
 #pragma unroll
-              for (int b = a; b < D; ++b) {
-                float sq = 0.f;
+              for (int b = 0; b < D; ++b) {
+                float v = cj[a * D + b];
 #pragma unroll
-                for (int cc = 0; cc < D; ++cc) sq = fmaf(A[a][cc], A[b][cc], sq);
-                col[pp * NG + qsym<D>(a, b)] = sq * r;
+                for (int cc = 0; cc < D; ++cc) v = fmaf(cj[D * D + a * NH + qsym_any<D>(b, cc)], X[cc], v);
+                J[a][b] = v;
               }
+            point_geometry(J, col + pp * NG);
+#pragma unroll
+            for (int gg = 0; gg < NG; ++gg) col[pp * NG + gg] -= gc[gg];
           }
         }
-        // split into the parts and write this cell's row of the chunk, 16 bytes at a time
+        // split into the parts and write this lane's half of the cell's chunk row, 16 bytes at a time
         unsigned char* bs = Bs + s * C::STAGE_BYTES;
 #pragma unroll
-        for (int kc = 0; kc < C::KCC; ++kc) {
+        for (int kc = 0; kc < C::KCC / 2; ++kc) {
           uint32_t w[S::PARTS][4];
 #pragma unroll
           for (int j = 0; j < S::EPC; ++j) {
@@ -691,63 +851,75 @@ __global__ void __launch_bounds__(TQ_THREADS, 1) tq_kernel(TqParams p) {
               }
             }
           }
-          const uint32_t o = core_offset(t, kc * S::EPC, C::KCC, S::EPC) * S::ESIZE;
+          const uint32_t o = core_offset(c, (hlf * (C::KCC / 2) + kc) * S::EPC, C::KCC, S::EPC) * S::ESIZE;
 #pragma unroll
           for (int qq = 0; qq < S::PARTS; ++qq)
             *reinterpret_cast<uint4*>(bs + qq * C::CH_BYTES + o) = make_uint4(w[qq][0], w[qq][1], w[qq][2], w[qq][3]);
         }
         fence_proxy_async();
-        mbar_arrive(bar(B_FULL + s));
+        __syncwarp();
+        if (lane == 0) mbar_arrive(bar(B_FULL + s));
       }
-      if (degenerate) atomicOr(p.status, FFC_FLAG_DEGENERATE);
+      if (live && degenerate) atomicOr(p.status, FFC_FLAG_DEGENERATE);
     }
     if (!ok) {
-      atomicOr(p.status, FFC_FLAG_TIMEOUT);
+      if (lane == 0) atomicOr(p.status, FFC_FLAG_TIMEOUT);
       abort_flag = 1;
     }
   } else {
     // ---------------------------------------------------------------- drainers: TMEM -> A_K
     bool ok = true;
-    const int q4 = warp & 3;
+    const int q4 = warp - TQ_DRAIN_WARP0;  // TMEM lanes 32 q4 .. 32 q4 + 31 (warp % 4)
     const int i = q4 * 32 + lane;  // element-tensor entry (TMEM lane)
+    float a0s[NG];
+#pragma unroll
+    for (int gg = 0; gg < NG; ++gg) a0s[gg] = i < p.nn ? p.a0sum[i * NG + gg] : 0.f;
     for (long long ct = 0; ct < my_tiles && ok; ++ct) {
       const int acc = int(ct & 1);
-      ok = mbar_wait_or_abort(bar(ACC_FULL + acc), uint32_t(ct >> 1) & 1u, &abort_flag);
-      if (__any_sync(0xffffffffu, !ok)) {
-        ok = false;
-        break;
-      }
+      ok = warp_wait(bar(ACC_FULL + acc), uint32_t(ct >> 1) & 1u, &abort_flag) &&
+           warp_wait(bar(GBAR_FULL + acc), uint32_t(ct >> 1) & 1u, &abort_flag);
+      if (!ok) break;
       fence_after();
+      const float* gb = gbar + acc * NG * N_CELLS;
       const long long e0 = (blockIdx.x + ct * gridDim.x) * N_CELLS;
       const uint32_t taddr = tmem + (uint32_t(q4 * 32) << 16) + uint32_t(acc * C::ACC_COLS);
 #pragma unroll 1
-      for (int c = 0; c < N_CELLS / 32; ++c) {
-        uint32_t rv[32];
-        float v[32];
-        tmem_ld16_issue(taddr + c * 32, rv);
-        tmem_ld16_issue(taddr + c * 32 + 16, rv + 16);
+      for (int c = 0; c < N_CELLS / 16; ++c) {
+        uint32_t rv[16];
+        float v[16];
+        tmem_ld16_issue(taddr + c * 16, rv);
         if constexpr (S::NPROD > 1) {
-          uint32_t rw[32];
-          tmem_ld16_issue(taddr + N_CELLS + c * 32, rw);
-          tmem_ld16_issue(taddr + N_CELLS + c * 32 + 16, rw + 16);
+          uint32_t rw[16];
+          tmem_ld16_issue(taddr + N_CELLS + c * 16, rw);
           tmem_wait_ld();
 #pragma unroll
-          for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(rv[j]) + __uint_as_float(rw[j]);
+          for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(rv[j]) + __uint_as_float(rw[j]);
         } else {
           tmem_wait_ld();
 #pragma unroll
-          for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(rv[j]);
+          for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(rv[j]);
+        }
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          float m = 0.f;
+#pragma unroll
+          for (int gg = 0; gg < NG; ++gg) m = fmaf(a0s[gg], gb[gg * N_CELLS + c * 16 + j], m);
+          v[j] += m;
         }
         if (i < p.nn) {
-          const long long ec = e0 + c * 32;
+          const long long ec = e0 + c * 16;
           float* dst = p.out + ec * p.nn + i;
 #pragma unroll
-          for (int j = 0; j < 32; ++j)
+          for (int j = 0; j < 16; ++j)
             if (ec + j < p.n_elem) __stcs(dst + j * p.nn, v[j]);
         }
       }
       fence_before();
-      mbar_arrive(bar(ACC_EMPTY + acc));
+      __syncwarp();
+      if (lane == 0) {
+        mbar_arrive(bar(ACC_EMPTY + acc));
+        mbar_arrive(bar(GBAR_EMPTY + acc));
+      }
     }
     if (!ok) {
       if (lane == 0) atomicOr(p.status, FFC_FLAG_TIMEOUT);
@@ -762,12 +934,40 @@ __global__ void __launch_bounds__(TQ_THREADS, 1) tq_kernel(TqParams p) {
   }
 }
 
+// The geometry table of the producers: gradients of the geometry basis at X = 0
+// [NGEO][D], its second derivatives [NGEO][D(D+1)/2] (geometry degree 2; differences of
+// the gradients at X = e_c and X = 0, exact for a quadratic basis), the rule's points [nq][D].
+std::vector<float> tq_table(const ffc_qform* f) {
+  const int d = f->d, ng = f->ngeo, nh = f->g == 2 ? d * (d + 1) / 2 : 0;
+  std::vector<double> X(size_t(d + 1) * d, 0.0), psi, dpsi;
+  for (int c = 0; c < d; ++c) X[size_t(c + 1) * d + c] = 1.0;
+  reference_basis(d, f->g, X, psi, dpsi);  // [d+1][ng][d]
+  std::vector<float> t;
+  for (int nd = 0; nd < ng; ++nd)
+    for (int b = 0; b < d; ++b) t.push_back(float(dpsi[size_t(nd) * d + b]));
+  std::vector<double> h(size_t(ng) * std::max(nh, 1), 0.0);
+  for (int nd = 0; nd < ng && nh; ++nd)
+    for (int b = 0; b < d; ++b)
+      for (int c = b; c < d; ++c)
+        h[size_t(nd) * nh + sym_pair(d, b, c)] = dpsi[(size_t(c + 1) * ng + nd) * d + b] - dpsi[size_t(nd) * d + b];
+  for (int i = 0; i < ng * nh; ++i) t.push_back(float(h[i]));
+  for (double x : f->X) t.push_back(float(x));
+  // A~0 summed over the points, [n*n][n_g] (FP64 sums rounded once)
+  for (int i = 0; i < f->n * f->n; ++i)
+    for (int gg = 0; gg < f->ng; ++gg) {
+      double sum = 0.0;
+      for (int k = 0; k < f->nq; ++k) sum += f->At[size_t(i) * f->K + size_t(k) * f->ng + gg];
+      t.push_back(float(sum));
+    }
+  return t;
+}
+
 template <int MODE>
 int upload_tq(ffc_qform* f, ffc_qform::Dev* dv, int nch) {
   using S = Split<MODE>;
   const int fam = S::BF16 ? 1 : 0;
   std::lock_guard<std::mutex> g(f->lock);
-  if (dv->tc_part[fam][S::PARTS - 1] && dv->dgeo32) return FFC_OK;
+  if (dv->tc_part[fam][S::PARTS - 1] && dv->tq_table) return FFC_OK;
   const int nn = f->n * f->n, K = f->K;
   const size_t per = size_t(nch) * M_TILE * QKCH;  // elements per part
   const int nparts = S::BF16 ? 3 : 2;  // a family uploads all its parts once
@@ -795,10 +995,10 @@ int upload_tq(ffc_qform* f, ffc_qform::Dev* dv, int nch) {
     if ((e = cudaMalloc(&dv->tc_part[fam][q], per * sizeof(typename S::Store))) == cudaSuccess)
       e = cudaMemcpy(dv->tc_part[fam][q], parts[q].data(), per * sizeof(typename S::Store), cudaMemcpyHostToDevice);
   }
-  if (e == cudaSuccess && !dv->dgeo32) {
-    std::vector<float> d32(f->dgeo.begin(), f->dgeo.end());
-    if ((e = cudaMalloc(&dv->dgeo32, d32.size() * sizeof(float))) == cudaSuccess)
-      e = cudaMemcpy(dv->dgeo32, d32.data(), d32.size() * sizeof(float), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && !dv->tq_table) {
+    const std::vector<float> t = tq_table(f);
+    if ((e = cudaMalloc(&dv->tq_table, t.size() * sizeof(float))) == cudaSuccess)
+      e = cudaMemcpy(dv->tq_table, t.data(), t.size() * sizeof(float), cudaMemcpyHostToDevice);
   }
   return e == cudaSuccess ? FFC_OK : cuda_fail(e, "ffc_tabulate_quadrature: tensor-core operands");
 }
@@ -809,6 +1009,14 @@ int launch_tq(ffc_qform* f, ffc_qform::Dev* dv, long long n_elem, const int32_t*
   using C = TqCfg<D, FORM, G, MODE>;
   using S = Split<MODE>;
   const int nch = (f->K + QKCH - 1) / QKCH;
+  const size_t smem = C::smem_bytes(f->nq);
+  int dev = 0, optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (smem > size_t(optin)) {
+    set_error("ffc_tabulate_quadrature: the rule's points do not fit next to the operand stages");
+    return FFC_EINVAL;
+  }
   int rc = upload_tq<MODE>(f, dv, nch);
   if (rc != FFC_OK) return rc;
   TqParams p{};
@@ -816,21 +1024,14 @@ int launch_tq(ffc_qform* f, ffc_qform::Dev* dv, long long n_elem, const int32_t*
   p.nodes = nodes;
   p.n_nodes = n_nodes;
   p.n_elem = n_elem;
-  p.dgeo = dv->dgeo32;
+  p.table = dv->tq_table;
+  p.a0sum = dv->tq_table + C::table_floats(f->nq);
   for (int q = 0; q < 3; ++q) p.a_part[q] = dv->tc_part[S::BF16 ? 1 : 0][q];
   p.out = out;
   p.nn = f->n * f->n;
   p.nq = f->nq;
   p.nch = nch;
   p.status = status;
-  const size_t smem = 4 * size_t(C::STAGE_BYTES) + (size_t(f->nq) * C::NGEO * D * 4 + 15) / 16 * 16 + 12 * 8 + 16;
-  int dev = 0, optin = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  if (smem > size_t(optin)) {
-    set_error("ffc_tabulate_quadrature: the rule's geometry tables do not fit next to the operand stages");
-    return FFC_EINVAL;
-  }
   auto kern = tq_kernel<D, FORM, G, MODE>;
   int sms = 0;
   if (launch_config(reinterpret_cast<const void*>(kern), TQ_THREADS, smem, -1, &sms, nullptr) != FFC_OK)
@@ -979,7 +1180,7 @@ extern "C" void ffc_qform_destroy(ffc_qform* f) {
     cudaFree(kv.second.at_f32);
     cudaFree(kv.second.dgeo);
     cudaFree(kv.second.epair);
-    cudaFree(kv.second.dgeo32);
+    cudaFree(kv.second.tq_table);
     for (auto& fam : kv.second.tc_part)
       for (void* q : fam) cudaFree(q);
     cudaSetDevice(prev);

@@ -115,9 +115,13 @@ def test_curved_assembly_matches_algorithm2(F, d, n, form, q):
 
 
 def test_full_size_curved_sample(F):
-    """40^3 x 6 = 384,000 curved tets (the bench configuration), P2 Poisson and mass,
-    FP64 and FP32, 300 seeded cells against the oracle, plus the Poisson rows' zero sums
-    over all cells."""
+    """40^3 x 6 = 384,000 curved tets (the bench configuration), P2 Poisson and mass:
+    FP64, FP32 and the tensor-core precisions on 300 seeded cells against the oracle; the
+    Poisson rows' zero sums over all cells; and every cell of the FP32-accurate paths
+    (FP32, 3xTF32, BF16x3) within 1e-6 of the FP64 path (itself within 1e-12 of the
+    oracle on the sample)."""
+    import torch
+
     cm = curved_mesh(3, 40, eps=0.08)
     rng = np.random.default_rng(20261203)
     sel = np.sort(rng.choice(cm.n_elem, 300, replace=False))
@@ -125,7 +129,9 @@ def test_full_size_curved_sample(F):
     for form in (0, 1):
         qf = F.QForm(form, F.TETRAHEDRON, 2, 2)
         ref = OC.element_tensors_curved(form, gather_nodes(cm)[sel], 2, 2, qf.quad_degree)
-        for prec, tol in (("fp64", FP64_TOL), ("fp32", FP32_TOL)):
+        A64 = None
+        for prec, tol in (("fp64", FP64_TOL), ("fp32", FP32_TOL), ("tf32x3", FP32_TOL), ("bf16x3", FP32_TOL),
+                          ("tf32", 5e-5)):
             A = F.tabulate_quadrature(qf, cells, nodes, precision=prec)
             assert F.status_poll() == 0
             got = A[_dev(sel).long()].double().cpu().numpy()
@@ -133,7 +139,15 @@ def test_full_size_curved_sample(F):
             if form == 1:
                 rs = A.double().sum(dim=2).abs().max().item()
                 assert rs <= (1e-12 if prec == "fp64" else 1e-5) * A.double().abs().max().item()
+            if prec == "fp64":
+                A64 = A
+                continue
+            if prec != "tf32":
+                d = (A.double() - A64).reshape(cm.n_elem, -1).norm(dim=1) / A64.reshape(cm.n_elem, -1).norm(dim=1)
+                assert d.max().item() <= FP32_TOL, (prec, d.max().item())
             del A
+        del A64
+        torch.cuda.empty_cache()
 
 
 def test_quadrature_flags_and_limits(F):
@@ -160,11 +174,12 @@ def test_quadrature_flags_and_limits(F):
 
 @pytest.mark.parametrize("d,n", [(2, 5), (3, 2)])
 @pytest.mark.parametrize("form,q", [(0, 1), (1, 1), (0, 2), (1, 2)])
-@pytest.mark.parametrize("prec,tol", [("bf16x3", 1e-6), ("tf32x3", 3e-6), ("tf32", 5e-3)])
+@pytest.mark.parametrize("prec,tol", [("bf16x3", 1e-6), ("tf32x3", 1e-6), ("tf32", 1e-4)])
 def test_tensor_core_quadrature_matches_the_oracle(F, d, n, form, q, prec, tol):
     """The tcgen05 contraction (element tensors of at most 128 entries) on curved cells:
-    BF16x3 within the 1e-6 target, 3xTF32 within 3e-6 (two TF32 parts), single TF32
-    within its 11-bit precision."""
+    the split precisions within the FP32 target 1e-6; single TF32 (11-bit operands) is
+    applied only to the deviations of G~ from its centroid value, so its error is
+    TF32's precision times their relative size."""
     cm = curved_mesh(d, n, eps=0.12)
     qf = F.QForm(form, _cell(F, d), q, 2)
     ref = OC.element_tensors_curved(form, gather_nodes(cm), q, 2, qf.quad_degree)
