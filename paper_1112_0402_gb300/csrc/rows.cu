@@ -596,7 +596,13 @@ struct RowsCfg {
   static constexpr int NA = FORM == ROWS_PAIR ? 1 + NP : (FORM == FFC_POISSON ? NP : 1);  // A0 values per entry
   static constexpr int NG = FORM == FFC_MASS ? 1 : 8;  // G_K values read per pair (vector loads)
   static constexpr int TB = ROWS_TB;    // items of one task of the columns beyond the first 32
-  static constexpr int WB = ROWS_WB;    // digit indices of one write-out task
+  // Order of an iteration's tasks after the staging ones: for n >= 32 (lane per column)
+  // the work units first and the write-out blocks, shorter (128 indices), last, so that
+  // the iteration ends on short tasks (P4 tets: mass + Poisson 4.28 -> 4.04 ms at 48^3);
+  // otherwise units and write-out blocks alternate while both last (P3: 1.64 ms, 1.69
+  // units first)
+  static constexpr bool UNITS_FIRST = MAIN;
+  static constexpr int WB = MAIN ? 128 : ROWS_WB;  // digit indices of one write-out task
 };
 
 // A0 entry (i1, i2) of the kernel's form(s), in the order the contraction uses, from the
@@ -680,6 +686,8 @@ __device__ __forceinline__ int rows_pos(int q) { return q & (ROWS_VMAX - 1); }
 #define ROWS_UNROLL 2
 #endif
 constexpr int kRowsUnroll = ROWS_UNROLL;  // pairs of a work unit in flight per loop step
+
+
 
 // One work unit (class i1, pairs [k0, k1)) of a chunk, by one warp: for n >= 32 lane l takes
 // column l of every pair (the A0 column in registers), for n < 32 the unit's (pair, column)
@@ -1038,10 +1046,12 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 1024 : 512, 1) rows_assemble(
         continue;
       }
       k -= NSPECIAL;
-      // items and write-out blocks alternate while both last
       bool item;
       int j;
-      if (k < nMix) {
+      if constexpr (K::UNITS_FIRST) {
+        item = k < nI;
+        j = item ? k : k - nI;
+      } else if (k < nMix) {  // items and write-out blocks alternate while both last
         item = (k & 1) == 0;
         j = k >> 1;
       } else {
