@@ -1101,6 +1101,17 @@ def measure_other(F, args, device, workload):
         A64 = torch.empty((cm.n_elem, n, n), dtype=torch.float64, device=device)
         detail["tabulate_fp64_ms"] = _timed(lambda: F.tabulate_quadrature(qf, cells, nodes, "fp64", out=A64),
                                             args.steps, args.warmup) * 1e3
+        # FP64 by exact digit products on the tensor cores (Ozaki-style splitting)
+        B64 = torch.empty_like(A64)
+        t_oz = _timed(lambda: F.tabulate_quadrature(qf, cells, nodes, "fp64_ozaki", out=B64), args.steps, args.warmup)
+        assert F.status_poll() == 0
+        d_oz = (B64 - A64).reshape(cm.n_elem, -1).norm(dim=1) / A64.reshape(cm.n_elem, -1).norm(dim=1)
+        oz_pieces = -(-qf.k_contract // 48) * 3
+        detail["fp64_ozaki"] = {"ms": t_oz * 1e3, "max_rel_diff_vs_fp64": float(d_oz.max()),
+                                "speedup_vs_fp64": detail["tabulate_fp64_ms"] / (t_oz * 1e3),
+                                "bf16_digit_products_tflops": 36 * 2.0 * 128 * 64 * 16 * oz_pieces
+                                * (-(-cm.n_elem // 64)) / t_oz / 1e12}
+        del B64
         A32 = torch.empty((cm.n_elem, n, n), dtype=torch.float32, device=device)
         pk = compute_peaks(F)
 

@@ -82,7 +82,8 @@ typedef enum {
   FFC_FP32 = 1,   /* FP32 G and A0, FP32 accumulation on CUDA cores, A_K stored as float */
   FFC_TF32 = 2,   /* tcgen05 kind::tf32, one product, FP32 accumulation in TMEM, float out */
   FFC_TF32X3 = 3, /* tcgen05 kind::tf32 with hi/lo splits of G and A0 (three products), float out */
-  FFC_BF16X3 = 4  /* tcgen05 kind::f16 (BF16) with three-part splits of G and A0 (six products), float out */
+  FFC_BF16X3 = 4, /* tcgen05 kind::f16 (BF16) with three-part splits of G and A0 (six products), float out */
+  FFC_FP64_OZAKI = 5 /* FP64 by exact products of 7-bit digits on tcgen05, double out (ffc_tabulate_quadrature) */
 } ffc_precision;
 
 /* How the CUDA-core precisions (FFC_FP64, FFC_FP32) evaluate the vector forms.
@@ -385,7 +386,8 @@ void ffc_qform_destroy(ffc_qform* f);
  * ffc_tabulate_quadrature -- A_K = A~0 : G~_K for a batch of cells:
  *   cells   device int32 [n_elem][n_geometry], geometry node ids in [0, n_nodes)
  *   nodes   device double [n_nodes][d], node coordinates
- *   A_K     device [n_elem][n][n], double (FFC_FP64) or float (the others), 16-byte aligned
+ *   A_K     device [n_elem][n][n], double (FFC_FP64, FFC_FP64_OZAKI) or float (the others),
+ *           16-byte aligned
  * FFC_FP64: G~_K and the contraction in FP64. FFC_FP32: F', its determinant and inverse
  * in FP64, G~_K rounded to FP32, the contraction in FP32. A node id out of range sets
  * FFC_FLAG_BOUNDS (its cell's tensor is then computed from node 0); a point where
@@ -396,6 +398,16 @@ void ffc_qform_destroy(ffc_qform* f);
  * (tcgen05) in 128-cell tiles, A~0 split into TF32 or BF16 parts on the host, G~_K per
  * point in FP32 split the same way on the device, A_K written as float. The split
  * precisions keep FP32 accuracy; FFC_TF32 alone has TF32's 11-bit precision.
+ * FFC_FP64_OZAKI (the same element tensors of at most 128 entries, and K = points x n_g
+ * at most 400, else FFC_EUNSUPPORTED): A_K as double, FP64-accurate, with the contraction
+ * on the tensor cores by exact products of small-integer digits (the splitting of Ozaki,
+ * Ogita, Oishi and Rump, Numer. Algorithms 59, 2012): each row of A~0 and each cell's
+ * column of G~ (computed in FP64) scaled by a power of two and written as eight balanced
+ * 7-bit digits, exact in BF16; the digit products summed per digit order in FP32 TMEM
+ * accumulators, exact integers for K <= 400; recombined in 64-bit integers and rounded
+ * once to FP64. Truncation below 2^-56 of the row and column scales. A value beyond a
+ * column's scale (a cell whose FP32 and FP64 geometry disagree, a NaN) is clamped and
+ * sets FFC_FLAG_DEGENERATE.
  * FFC_EINVAL for other precisions or bad pointers.
  *
  * ffc_assemble_quadrature -- Algorithm 2 fused, as ffc_assemble:

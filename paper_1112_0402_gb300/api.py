@@ -25,8 +25,9 @@ from ._capi import lib
 
 MASS, POISSON, NS_CONVECTION, ELASTICITY, SOURCE = 0, 1, 2, 3, 4
 TRIANGLE, TETRAHEDRON = 2, 3
-FP64, FP32, TF32, TF32X3, BF16X3 = 0, 1, 2, 3, 4
-PRECISIONS = {"fp64": FP64, "fp32": FP32, "tf32": TF32, "tf32x3": TF32X3, "bf16x3": BF16X3}
+FP64, FP32, TF32, TF32X3, BF16X3, FP64_OZAKI = 0, 1, 2, 3, 4, 5
+PRECISIONS = {"fp64": FP64, "fp32": FP32, "tf32": TF32, "tf32x3": TF32X3, "bf16x3": BF16X3,
+              "fp64_ozaki": FP64_OZAKI}
 FLAG_DEGENERATE, FLAG_BOUNDS, FLAG_TIMEOUT = 1, 2, 4
 ALG_AUTO, ALG_DENSE, ALG_BLOCK = 0, 1, 2
 
@@ -348,7 +349,7 @@ def tabulate_quadrature(form: QForm, cells, nodes, precision="fp64", out=None, s
     n_elem = cells.shape[0]
     c = _dev_ptr(cells, torch.int32, "cells", (n_elem, form.n_geometry))
     v = _dev_ptr(nodes, torch.float64, "nodes", (nodes.shape[0], form.dim))
-    dt = torch.float64 if p == FP64 else torch.float32
+    dt = torch.float64 if p in (FP64, FP64_OZAKI) else torch.float32
     if out is None:
         out = torch.empty((n_elem, form.n_local, form.n_local), dtype=dt, device=cells.device)
     o = _dev_ptr(out, dt, "out", (n_elem, form.n_local, form.n_local))

@@ -34,29 +34,9 @@
 #include <vector>
 
 #include "ffc_internal.h"
+#include "quadrature.h"
 #include "tc_common.cuh"
 
-struct ffc_qform {
-  int kind = 0, d = 0, q = 0, g = 0, p = 0;
-  int n = 0;     // local dofs
-  int ngeo = 0;  // geometry nodes per cell
-  int nq = 0;    // quadrature points
-  int ng = 0;    // geometry entries per point
-  int K = 0;     // contraction length nq * ng
-  std::vector<double> X, W;  // rule: points [nq][d], weights [nq]
-  std::vector<double> At;    // A~0 [n*n][K], j = k * ng + g
-  std::vector<double> dgeo;  // geometry basis gradients [nq][ngeo][d]
-  struct Dev {
-    double* at_f64 = nullptr;  // [K][ne64], entries i1 <= i2, padded to an even count
-    float* at_f32 = nullptr;   // [K][ne32], all entries, padded to a multiple of 4
-    double* dgeo = nullptr;
-    uint16_t* epair = nullptr;  // [n(n+1)/2]: i1 << 8 | i2
-    void* tc_part[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};  // TF32 / BF16 parts
-    float* tq_table = nullptr;  // the tensor-core producers' geometry table (FP32)
-  };
-  std::mutex lock;
-  std::map<int, Dev> dev;
-};
 
 namespace ffc {
 namespace {
@@ -1103,15 +1083,21 @@ int run_quadrature(const ffc_qform* f, int64_t n_elem, const int32_t* cells, con
 int check_args(const ffc_qform* f, int64_t n_elem, const int32_t* cells, const double* nodes, int64_t n_nodes,
                int precision, const char* who, bool tensor_cores = false) {
   const bool tc = precision == FFC_TF32 || precision == FFC_TF32X3 || precision == FFC_BF16X3;
-  if (!f || n_elem < 0 || n_nodes < 0 || (precision != FFC_FP64 && precision != FFC_FP32 && !(tensor_cores && tc))) {
+  const bool oz = precision == FFC_FP64_OZAKI;
+  if (!f || n_elem < 0 || n_nodes < 0 ||
+      (precision != FFC_FP64 && precision != FFC_FP32 && !(tensor_cores && (tc || oz)))) {
     set_error(std::string(who) + (tensor_cores ? ": invalid argument (precision FFC_FP64, FFC_FP32, FFC_TF32, "
-                                                 "FFC_TF32X3 or FFC_BF16X3)"
+                                                 "FFC_TF32X3, FFC_BF16X3 or FFC_FP64_OZAKI)"
                                                : ": invalid argument (precision must be FFC_FP64 or FFC_FP32)"));
     return FFC_EINVAL;
   }
   if (tc && f->n * f->n > tc::M_TILE) {
     set_error(std::string(who) + ": the tensor-core precisions take element tensors of at most 128 entries");
     return FFC_EUNSUPPORTED;
+  }
+  if (oz) {
+    const int rc = ozaki_supported(f);
+    if (rc != FFC_OK) return rc;
   }
   if (n_elem > 0 && (!cells || !nodes || n_nodes == 0 || (reinterpret_cast<uintptr_t>(nodes) & 7))) {
     set_error(std::string(who) + ": null or misaligned cells / nodes");
@@ -1181,6 +1167,8 @@ extern "C" void ffc_qform_destroy(ffc_qform* f) {
     cudaFree(kv.second.dgeo);
     cudaFree(kv.second.epair);
     cudaFree(kv.second.tq_table);
+    cudaFree(kv.second.oz_a);
+    cudaFree(kv.second.oz_table);
     for (auto& fam : kv.second.tc_part)
       for (void* q : fam) cudaFree(q);
     cudaSetDevice(prev);
@@ -1204,6 +1192,9 @@ extern "C" int ffc_tabulate_quadrature(const ffc_qform* f, int64_t n_elem, const
       set_error("ffc_tabulate_quadrature: status word allocation failed");
       return FFC_ECUDA;
     }
+    if (precision == FFC_FP64_OZAKI)
+      return run_ozaki(const_cast<ffc_qform*>(f), dv, n_elem, cells, nodes, n_nodes, static_cast<double*>(A_K), st,
+                       static_cast<cudaStream_t>(stream));
     return tq::run_tq(const_cast<ffc_qform*>(f), dv, precision, n_elem, cells, nodes, n_nodes, static_cast<float*>(A_K),
                       st, static_cast<cudaStream_t>(stream));
   }

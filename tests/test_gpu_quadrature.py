@@ -116,10 +116,10 @@ def test_curved_assembly_matches_algorithm2(F, d, n, form, q):
 
 def test_full_size_curved_sample(F):
     """40^3 x 6 = 384,000 curved tets (the bench configuration), P2 Poisson and mass:
-    FP64, FP32 and the tensor-core precisions on 300 seeded cells against the oracle; the
-    Poisson rows' zero sums over all cells; and every cell of the FP32-accurate paths
-    (FP32, 3xTF32, BF16x3) within 1e-6 of the FP64 path (itself within 1e-12 of the
-    oracle on the sample)."""
+    FP64 (CUDA cores and digit-split tensor cores), FP32 and the tensor-core precisions on
+    300 seeded cells against the oracle; the Poisson rows' zero sums over all cells; every
+    cell of the FP32-accurate paths (FP32, 3xTF32, BF16x3) within 1e-6 of the FP64 path
+    (itself within 1e-12 of the oracle on the sample), of the digit-split FP64 within 1e-13."""
     import torch
 
     cm = curved_mesh(3, 40, eps=0.08)
@@ -130,8 +130,8 @@ def test_full_size_curved_sample(F):
         qf = F.QForm(form, F.TETRAHEDRON, 2, 2)
         ref = OC.element_tensors_curved(form, gather_nodes(cm)[sel], 2, 2, qf.quad_degree)
         A64 = None
-        for prec, tol in (("fp64", FP64_TOL), ("fp32", FP32_TOL), ("tf32x3", FP32_TOL), ("bf16x3", FP32_TOL),
-                          ("tf32", 5e-5)):
+        for prec, tol in (("fp64", FP64_TOL), ("fp64_ozaki", FP64_TOL), ("fp32", FP32_TOL), ("tf32x3", FP32_TOL),
+                          ("bf16x3", FP32_TOL), ("tf32", 5e-5)):
             A = F.tabulate_quadrature(qf, cells, nodes, precision=prec)
             assert F.status_poll() == 0
             got = A[_dev(sel).long()].double().cpu().numpy()
@@ -144,7 +144,7 @@ def test_full_size_curved_sample(F):
                 continue
             if prec != "tf32":
                 d = (A.double() - A64).reshape(cm.n_elem, -1).norm(dim=1) / A64.reshape(cm.n_elem, -1).norm(dim=1)
-                assert d.max().item() <= FP32_TOL, (prec, d.max().item())
+                assert d.max().item() <= (1e-13 if prec == "fp64_ozaki" else FP32_TOL), (prec, d.max().item())
             del A
         del A64
         torch.cuda.empty_cache()
@@ -210,3 +210,74 @@ def test_tensor_core_quadrature_limits(F):
     with pytest.raises(F.FFCError) as e:
         F.tabulate_quadrature(big, _dev(cm.cells), _dev(cm.nodes), precision="bf16x3")
     assert e.value.code == -5
+
+
+@pytest.mark.parametrize("d,n", [(2, 5), (3, 2)])
+@pytest.mark.parametrize("form,q", [(0, 1), (1, 1), (0, 2), (1, 2)])
+def test_digit_split_fp64_matches_the_oracle(F, d, n, form, q):
+    """FFC_FP64_OZAKI (FP64 from exact BF16 digit products on the tensor cores) on curved
+    cells: within the FP64 tolerance of the oracle, and of the CUDA-core FP64 kernel."""
+    cm = curved_mesh(d, n, eps=0.12)
+    qf = F.QForm(form, _cell(F, d), q, 2)
+    ref = OC.element_tensors_curved(form, gather_nodes(cm), q, 2, qf.quad_degree)
+    cells, nodes = _dev(cm.cells), _dev(cm.nodes)
+    got = F.tabulate_quadrature(qf, cells, nodes, precision="fp64_ozaki")
+    assert F.status_poll() == 0
+    assert got.dtype.is_floating_point and got.element_size() == 8
+    got = got.cpu().numpy()
+    assert _rel(got, ref) <= FP64_TOL
+    simt = F.tabulate_quadrature(qf, cells, nodes, precision="fp64").cpu().numpy()
+    assert _rel(got, simt) <= 1e-13
+
+
+@pytest.mark.parametrize("d", [2, 3])
+@pytest.mark.parametrize("form", [0, 1])
+def test_digit_split_fp64_on_affine_cells(F, d, form):
+    """Geometry degree 1: equal to the tensor representation's FP64 element tensors."""
+    import torch
+
+    m = M.unit_square_triangles(4, 0.25, 5) if d == 2 else M.unit_cube_tets(2, 0.25, 5)
+    V = M.gather_cell_vertices(m)
+    tensor = F.tabulate(F.Form(form, _cell(F, d), 2), _dev(m.cells, torch.int32), _dev(m.vertices, torch.float64),
+                        precision="fp64").cpu().numpy()
+    nodes = OC.affine_nodes(V, 1)
+    E, ng = nodes.shape[:2]
+    cells = np.arange(E * ng, dtype=np.int32).reshape(E, ng)
+    qf = F.QForm(form, _cell(F, d), 2, 1, 4)
+    got = F.tabulate_quadrature(qf, _dev(cells), _dev(nodes.reshape(-1, d)), precision="fp64_ozaki").cpu().numpy()
+    assert F.status_poll() == 0
+    assert _rel(got, tensor) <= FP64_TOL
+
+
+@pytest.mark.parametrize("count", [1, 63, 65, 200])
+def test_digit_split_fp64_ragged_tiles(F, count):
+    """Cell counts around the 64-cell tile: every cell written, nothing beyond."""
+    import torch
+
+    cm = curved_mesh(3, 4, eps=0.1)
+    qf = F.QForm(1, F.TETRAHEDRON, 2, 2)
+    out = torch.full((count + 1, 10, 10), 7.0, dtype=torch.float64, device="cuda")
+    F.tabulate_quadrature(qf, _dev(cm.cells[:count]), _dev(cm.nodes), precision="fp64_ozaki", out=out[:count])
+    assert F.status_poll() == 0
+    ref = OC.element_tensors_curved(1, gather_nodes(cm)[:count], 2, 2, qf.quad_degree)
+    assert _rel(out[:count].cpu().numpy(), ref) <= FP64_TOL
+    assert bool((out[count] == 7.0).all())
+
+
+def test_digit_split_fp64_limits_and_flags(F):
+    cm = curved_mesh(3, 1, eps=0.1)
+    cells, nodes = _dev(cm.cells), _dev(cm.nodes)
+    for qf in (F.QForm(1, F.TETRAHEDRON, 3, 2),      # 400 entries: more than one 128-entry tile
+               F.QForm(1, F.TETRAHEDRON, 2, 2, 9)):  # 125 points x 6 = 750 > 400 terms
+        with pytest.raises(F.FFCError) as e:
+            F.tabulate_quadrature(qf, cells, nodes, precision="fp64_ozaki")
+        assert e.value.code == -5
+    qf = F.QForm(1, F.TETRAHEDRON, 2, 2)
+    flat = cm.cells.copy()
+    flat[1, :] = flat[1, 0]
+    F.tabulate_quadrature(qf, _dev(flat), nodes, precision="fp64_ozaki")
+    assert F.status_poll() & F.FLAG_DEGENERATE
+    bad = cm.cells.copy()
+    bad[0, 4] = cm.nodes.shape[0] + 7
+    F.tabulate_quadrature(qf, _dev(bad), nodes, precision="fp64_ozaki")
+    assert F.status_poll() & F.FLAG_BOUNDS

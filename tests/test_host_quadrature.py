@@ -121,3 +121,23 @@ def test_tensor_core_precisions_are_checked_before_device_work():
         assert L.ffc_tabulate_quadrature(p3.handle, 4, None, None, 10, None, prec, None) == -5
         assert L.ffc_tabulate_quadrature(p2.handle, 4, None, None, 10, None, prec, None) == -1  # null cells
         assert L.ffc_assemble_quadrature(p2.handle, 4, None, None, 10, None, None, 5, prec, None) == -1
+
+
+def test_digit_split_fp64_is_checked_before_device_work():
+    """FFC_FP64_OZAKI: ffc_tabulate_quadrature only, element tensors of at most 128 entries
+    and contractions of at most 400 terms (FFC_EUNSUPPORTED beyond)."""
+    F = _F()
+    from paper_1112_0402_gb300 import _capi
+
+    L = _capi.lib()
+    assert F.FP64_OZAKI == 5 and F.PRECISIONS["fp64_ozaki"] == 5
+    p2 = F.QForm(F.POISSON, F.TETRAHEDRON, 2, 2)   # 100 entries, 64 x 6 = 384 terms
+    assert L.ffc_tabulate_quadrature(p2.handle, 4, None, None, 10, None, F.FP64_OZAKI, None) == -1  # null cells
+    assert L.ffc_tabulate_quadrature(F.QForm(F.POISSON, F.TETRAHEDRON, 3, 2).handle, 4, None, None, 10, None,
+                                     F.FP64_OZAKI, None) == -5
+    assert L.ffc_tabulate_quadrature(F.QForm(F.POISSON, F.TETRAHEDRON, 2, 2, 9).handle, 4, None, None, 10, None,
+                                     F.FP64_OZAKI, None) == -5
+    assert L.ffc_assemble_quadrature(p2.handle, 4, None, None, 10, None, None, 5, F.FP64_OZAKI, None) == -1
+    # the tensor representation's entry points refuse it
+    f = F.Form(F.POISSON, F.TETRAHEDRON, 2)
+    assert L.ffc_tabulate(f.handle, 4, None, None, 10, None, None, F.FP64_OZAKI, None) == -1
