@@ -492,7 +492,10 @@ struct TqParams {
   const float* table;       // [NGEO][D] dPsi(0), [NGEO][NH] second derivatives, [nq][D] points
   const float* a0sum;       // [nn][NG]: A~0 summed over the points (the centroid term)
   const void* a_part[3];    // [NCH][128 x QKCH] per part
-  float* out;               // A_K [n_elem][nn]
+  float* out;               // A_K [n_elem][nn], or (slot set) CSR values csr_val[slot] += A_K
+  const int32_t* slot;
+  double* csr_val;
+  long long nnz;
   int nn, nq, nch;
   unsigned* status;
 };
@@ -888,10 +891,20 @@ __global__ void __launch_bounds__(TQ_THREADS, 1) tq_kernel(TqParams p) {
         }
         if (i < p.nn) {
           const long long ec = e0 + c * 16;
-          float* dst = p.out + ec * p.nn + i;
+          if (p.slot) {  // Algorithm 2: FP64 atomic adds into the CSR values
 #pragma unroll
-          for (int j = 0; j < 16; ++j)
-            if (ec + j < p.n_elem) __stcs(dst + j * p.nn, v[j]);
+            for (int j = 0; j < 16; ++j)
+              if (ec + j < p.n_elem) {
+                const int sl = __ldg(p.slot + (ec + j) * p.nn + i);
+                if (sl >= 0 && sl < p.nnz) atomicAdd(p.csr_val + sl, double(v[j]));
+                else atomicOr(p.status, FFC_FLAG_BOUNDS);
+              }
+          } else {
+            float* dst = p.out + ec * p.nn + i;
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+              if (ec + j < p.n_elem) __stcs(dst + j * p.nn, v[j]);
+          }
         }
       }
       fence_before();
@@ -985,7 +998,7 @@ int upload_tq(ffc_qform* f, ffc_qform::Dev* dv, int nch) {
 
 template <int D, int FORM, int G, int MODE>
 int launch_tq(ffc_qform* f, ffc_qform::Dev* dv, long long n_elem, const int32_t* cells, const double* nodes,
-              long long n_nodes, float* out, unsigned* status, cudaStream_t s) {
+              long long n_nodes, const QOut& o, unsigned* status, cudaStream_t s) {
   using C = TqCfg<D, FORM, G, MODE>;
   using S = Split<MODE>;
   const int nch = (f->K + QKCH - 1) / QKCH;
@@ -1007,7 +1020,10 @@ int launch_tq(ffc_qform* f, ffc_qform::Dev* dv, long long n_elem, const int32_t*
   p.table = dv->tq_table;
   p.a0sum = dv->tq_table + C::table_floats(f->nq);
   for (int q = 0; q < 3; ++q) p.a_part[q] = dv->tc_part[S::BF16 ? 1 : 0][q];
-  p.out = out;
+  p.out = static_cast<float*>(o.out);
+  p.slot = o.slot;
+  p.csr_val = o.csr_val;
+  p.nnz = o.nnz;
   p.nn = f->n * f->n;
   p.nq = f->nq;
   p.nch = nch;
@@ -1025,7 +1041,7 @@ int launch_tq(ffc_qform* f, ffc_qform::Dev* dv, long long n_elem, const int32_t*
 
 template <int D, int FORM, int G>
 int launch_tq_mode(ffc_qform* f, ffc_qform::Dev* dv, int precision, long long n_elem, const int32_t* cells,
-                   const double* nodes, long long n_nodes, float* out, unsigned* status, cudaStream_t s) {
+                   const double* nodes, long long n_nodes, const QOut& out, unsigned* status, cudaStream_t s) {
   switch (precision) {
     case FFC_TF32: return launch_tq<D, FORM, G, MODE_TF32>(f, dv, n_elem, cells, nodes, n_nodes, out, status, s);
     case FFC_TF32X3: return launch_tq<D, FORM, G, MODE_TF32X3>(f, dv, n_elem, cells, nodes, n_nodes, out, status, s);
@@ -1034,7 +1050,7 @@ int launch_tq_mode(ffc_qform* f, ffc_qform::Dev* dv, int precision, long long n_
 }
 
 int run_tq(ffc_qform* f, ffc_qform::Dev* dv, int precision, long long n_elem, const int32_t* cells,
-           const double* nodes, long long n_nodes, float* out, unsigned* status, cudaStream_t s) {
+           const double* nodes, long long n_nodes, const QOut& out, unsigned* status, cudaStream_t s) {
   const bool mass = f->kind == FFC_MASS;
   if (f->d == 2) {
     if (f->g == 1)
@@ -1192,11 +1208,13 @@ extern "C" int ffc_tabulate_quadrature(const ffc_qform* f, int64_t n_elem, const
       set_error("ffc_tabulate_quadrature: status word allocation failed");
       return FFC_ECUDA;
     }
+    QOut o;
+    o.out = A_K;
     if (precision == FFC_FP64_OZAKI)
-      return run_ozaki(const_cast<ffc_qform*>(f), dv, n_elem, cells, nodes, n_nodes, static_cast<double*>(A_K), st,
+      return run_ozaki(const_cast<ffc_qform*>(f), dv, n_elem, cells, nodes, n_nodes, o, st,
                        static_cast<cudaStream_t>(stream));
-    return tq::run_tq(const_cast<ffc_qform*>(f), dv, precision, n_elem, cells, nodes, n_nodes, static_cast<float*>(A_K),
-                      st, static_cast<cudaStream_t>(stream));
+    return tq::run_tq(const_cast<ffc_qform*>(f), dv, precision, n_elem, cells, nodes, n_nodes, o, st,
+                      static_cast<cudaStream_t>(stream));
   }
   return run_quadrature(f, n_elem, cells, nodes, n_nodes, A_K, nullptr, 0, precision, stream,
                         "ffc_tabulate_quadrature");
@@ -1205,11 +1223,29 @@ extern "C" int ffc_tabulate_quadrature(const ffc_qform* f, int64_t n_elem, const
 extern "C" int ffc_assemble_quadrature(const ffc_qform* f, int64_t n_elem, const int32_t* cells, const double* nodes,
                                        int64_t n_nodes, const int32_t* slot, double* csr_val, int64_t nnz,
                                        int precision, void* stream) {
-  int rc = check_args(f, n_elem, cells, nodes, n_nodes, precision, "ffc_assemble_quadrature");
+  int rc = check_args(f, n_elem, cells, nodes, n_nodes, precision, "ffc_assemble_quadrature", true);
   if (rc != FFC_OK || n_elem == 0) return rc;
   if (!slot || !csr_val || nnz <= 0) {
     set_error("ffc_assemble_quadrature: slot / csr_val");
     return FFC_EINVAL;
+  }
+  if (precision != FFC_FP64 && precision != FFC_FP32) {  // the tensor-core kernels, atomics in their drain
+    ffc_qform::Dev* dv = nullptr;
+    if ((rc = ensure_qdev(const_cast<ffc_qform*>(f), &dv)) != FFC_OK) return rc;
+    unsigned* st = status_word();
+    if (!st) {
+      set_error("ffc_assemble_quadrature: status word allocation failed");
+      return FFC_ECUDA;
+    }
+    QOut o;
+    o.slot = slot;
+    o.csr_val = csr_val;
+    o.nnz = nnz;
+    if (precision == FFC_FP64_OZAKI)
+      return run_ozaki(const_cast<ffc_qform*>(f), dv, n_elem, cells, nodes, n_nodes, o, st,
+                       static_cast<cudaStream_t>(stream));
+    return tq::run_tq(const_cast<ffc_qform*>(f), dv, precision, n_elem, cells, nodes, n_nodes, o, st,
+                      static_cast<cudaStream_t>(stream));
   }
   return run_quadrature(f, n_elem, cells, nodes, n_nodes, csr_val, slot, nnz, precision, stream,
                         "ffc_assemble_quadrature");

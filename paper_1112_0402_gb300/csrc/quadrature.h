@@ -35,10 +35,19 @@ struct ffc_qform {
 };
 
 namespace ffc {
-// The digit-split FP64 contraction of quadrature.cu's ffc_tabulate_quadrature (precision
-// FFC_FP64_OZAKI): A_K as doubles for n_elem cells; dv is the form's device state.
+// Where a tensor-core quadrature kernel puts A_K: stored into `out` ([n_elem][n*n], float or
+// double by precision), or, when `slot` is set, added into csr_val[slot[e][i]] with FP64
+// atomics (Algorithm 2; a slot outside [0, nnz) sets FFC_FLAG_BOUNDS and is skipped).
+struct QOut {
+  void* out = nullptr;
+  const int32_t* slot = nullptr;
+  double* csr_val = nullptr;
+  long long nnz = 0;
+};
+// The digit-split FP64 contraction (precision FFC_FP64_OZAKI) for n_elem cells; dv is the
+// form's device state.
 int run_ozaki(ffc_qform* f, ffc_qform::Dev* dv, long long n_elem, const int32_t* cells, const double* nodes,
-              long long n_nodes, double* out, unsigned* status, cudaStream_t s);
+              long long n_nodes, const QOut& o, unsigned* status, cudaStream_t s);
 // FFC_EUNSUPPORTED (with the reason set) when the form is outside the kernel's range.
 int ozaki_supported(const ffc_qform* f);
 }  // namespace ffc

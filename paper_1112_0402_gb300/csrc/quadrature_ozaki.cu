@@ -106,7 +106,10 @@ struct OzParams {
   long long n_nodes, n_elem;
   const double* table;   // see OzCfg::table_doubles, then e_i [128]
   const void* a_digits;  // [pieces][8 planes][128 x 16] BF16, core-matrix layout
-  double* out;           // A_K [n_elem][nn]
+  double* out;           // A_K [n_elem][nn], or (slot set) CSR values csr_val[slot] += A_K
+  const int32_t* slot;
+  double* csr_val;
+  long long nnz;
   int nn, nq, nch;
   unsigned* status;
 };
@@ -547,7 +550,15 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_kernel(OzParams p) {
           const long long L = P[4] * 2097152ll + P[5] * 16384ll + P[6] * 128ll + P[7];
           const double v = oz_scale(fma(double(H), 268435456.0, double(L)), ei + tau[cb * 8 + j] - 63);
           const long long e = e0 + cb * 8 + j;
-          if (i < p.nn && e < p.n_elem) __stcs(p.out + e * p.nn + i, v);
+          if (i < p.nn && e < p.n_elem) {
+            if (p.slot) {  // Algorithm 2: FP64 atomic add into the CSR values
+              const int sl = __ldg(p.slot + e * p.nn + i);
+              if (sl >= 0 && sl < p.nnz) atomicAdd(p.csr_val + sl, v);
+              else atomicOr(p.status, FFC_FLAG_BOUNDS);
+            } else {
+              __stcs(p.out + e * p.nn + i, v);
+            }
+          }
         }
       }
       fence_before();
@@ -638,7 +649,7 @@ int upload_oz(ffc_qform* f, ffc_qform::Dev* dv, int nch) {
 
 template <int D, int FORM, int G>
 int launch_oz(ffc_qform* f, ffc_qform::Dev* dv, long long n_elem, const int32_t* cells, const double* nodes,
-              long long n_nodes, double* out, unsigned* status, cudaStream_t s) {
+              long long n_nodes, const QOut& o, unsigned* status, cudaStream_t s) {
   using C = OzCfg<D, FORM, G>;
   const int nch = (f->K + OZ_KB - 1) / OZ_KB;
   const size_t smem = C::smem_bytes(f->nq);
@@ -658,7 +669,10 @@ int launch_oz(ffc_qform* f, ffc_qform::Dev* dv, long long n_elem, const int32_t*
   p.n_elem = n_elem;
   p.table = dv->oz_table;
   p.a_digits = dv->oz_a;
-  p.out = out;
+  p.out = static_cast<double*>(o.out);
+  p.slot = o.slot;
+  p.csr_val = o.csr_val;
+  p.nnz = o.nnz;
   p.nn = f->n * f->n;
   p.nq = f->nq;
   p.nch = nch;
@@ -691,7 +705,7 @@ int ozaki_supported(const ffc_qform* f) {
 }
 
 int run_ozaki(ffc_qform* f, ffc_qform::Dev* dv, long long n_elem, const int32_t* cells, const double* nodes,
-              long long n_nodes, double* out, unsigned* status, cudaStream_t s) {
+              long long n_nodes, const QOut& out, unsigned* status, cudaStream_t s) {
   const bool mass = f->kind == FFC_MASS;
   if (f->d == 2) {
     if (f->g == 1)

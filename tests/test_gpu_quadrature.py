@@ -96,7 +96,7 @@ def test_curved_cells_match_the_oracle(F, d, n, form, q):
 
 
 @pytest.mark.parametrize("d,n", [(2, 4), (3, 2)])
-@pytest.mark.parametrize("form,q", [(1, 2), (0, 2), (1, 3)])
+@pytest.mark.parametrize("form,q", [(1, 2), (0, 2), (1, 3), (1, 1)])
 def test_curved_assembly_matches_algorithm2(F, d, n, form, q):
     import torch
 
@@ -107,11 +107,14 @@ def test_curved_assembly_matches_algorithm2(F, d, n, form, q):
     ref_ptr, ref_col, ref_val = OA.assemble_csr(ref_K, dofmap, n_dof)
     row_ptr, col, slot = F.csr_pattern(dofmap, n_dof)
     assert np.array_equal(row_ptr, ref_ptr) and np.array_equal(col, ref_col)
-    for prec, tol in (("fp64", FP64_TOL), ("fp32", FP32_TOL)):
+    precs = [("fp64", FP64_TOL), ("fp32", FP32_TOL)]
+    if qf.n_local ** 2 <= 128:  # the tensor-core kernels, atomics in their drain
+        precs += [("fp64_ozaki", FP64_TOL), ("tf32x3", FP32_TOL), ("bf16x3", FP32_TOL)]
+    for prec, tol in precs:
         val = torch.zeros(col.size, dtype=torch.float64, device="cuda")
         F.assemble_quadrature(qf, _dev(cm.cells), _dev(cm.nodes), _dev(slot, torch.int32), val, precision=prec)
         assert F.status_poll() == 0
-        assert np.abs(val.cpu().numpy() - ref_val).max() <= tol * np.abs(ref_val).max()
+        assert np.abs(val.cpu().numpy() - ref_val).max() <= tol * np.abs(ref_val).max(), prec
 
 
 def test_full_size_curved_sample(F):
@@ -213,8 +216,10 @@ def test_tensor_core_quadrature_limits(F):
 
 
 @pytest.mark.parametrize("d,n", [(2, 5), (3, 2)])
-@pytest.mark.parametrize("form,q", [(0, 1), (1, 1), (0, 2), (1, 2)])
+@pytest.mark.parametrize("form,q", [(0, 1), (1, 1), (0, 2), (1, 2), (1, 3)])
 def test_digit_split_fp64_matches_the_oracle(F, d, n, form, q):
+    if d == 3 and q == 3:
+        pytest.skip("P3 tets: 400 entries, more than one 128-entry tile")
     """FFC_FP64_OZAKI (FP64 from exact BF16 digit products on the tensor cores) on curved
     cells: within the FP64 tolerance of the oracle, and of the CUDA-core FP64 kernel."""
     cm = curved_mesh(d, n, eps=0.12)
