@@ -1160,6 +1160,10 @@ def measure_other(F, args, device, workload):
                 tq = _timed(lambda: F.tabulate_quadrature(qa, ca, va, precision="fp32", out=A), args.steps, 1)
                 ratio[f"{FORM_NAME[form]}_p{q}"] = {"tensor_ms": tt * 1e3, "quadrature_ms": tq * 1e3,
                                                     "TQ_over_TT": tq / tt}
+                if f.n_local ** 2 <= 128:  # the quadrature contraction on the tensor cores (3xTF32)
+                    tc = _timed(lambda: F.tabulate_quadrature(qa, ca, va, precision="tf32x3", out=A), args.steps, 1)
+                    ratio[f"{FORM_NAME[form]}_p{q}"].update({"quadrature_tf32x3_ms": tc * 1e3,
+                                                             "TQ_tf32x3_over_TT": tc / tt})
                 del A
         detail["affine_fp32_T_Q_over_T_T"] = ratio
         cpu_rate, S = None, 0
