@@ -371,10 +371,19 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_kernel(OzParams p) {
       }
       const double thr = 1e-14 * (D == 2 ? h2 : h2 * sqrt(h2));
       // the column's scale: an FP32 estimate of its largest |G~| over the points, with a
-      // 2^-10 margin, rounded up to a power of two
+      // 2^-10 margin, rounded up to a power of two. The estimate runs on the coefficients
+      // times 2^-eh (2^eh about the cell's size h), which keeps it inside FP32's range for
+      // any cell size; G~ of the map scaled by l is l^D G~ (mass) or l^(D-2) G~ (Poisson),
+      // so the exponent found is shifted back by eh times that power.
+      int eh = 0;
+      if (h2 > 0.0 && h2 < DBL_MAX) {
+        frexp(h2, &eh);
+        eh /= 2;
+      }
+      const double down = __longlong_as_double(static_cast<long long>(1023 - eh) << 52);
       float c32[NJ];
 #pragma unroll
-      for (int j = 0; j < NJ; ++j) c32[j] = float(cj[j]);
+      for (int j = 0; j < NJ; ++j) c32[j] = float(cj[j] * down);
       float mx = 0.f;
       const int npts = G == 1 ? 1 : p.nq;
       for (int k = 0; k < npts; ++k) {
@@ -394,7 +403,10 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_kernel(OzParams p) {
         for (int gg = 0; gg < NG; ++gg) mx = fmaxf(mx, fabsf(v[gg]));
       }
       int ec = 0;
-      if (mx > 0.f && mx <= FLT_MAX) frexpf(mx * (1.f + 0.0009765625f), &ec);
+      if (mx > 0.f && mx <= FLT_MAX) {
+        frexp(double(mx) * (1.0 + 0.0009765625), &ec);
+        ec += eh * (FORM == FFC_MASS ? D : D - 2);
+      }
       if (ct >= 1) ok = warp_wait(bar(GEO_EMPTY), uint32_t(ct - 1) & 1u, &abort_flag);
       if (!ok) break;
 #pragma unroll

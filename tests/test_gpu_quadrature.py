@@ -286,3 +286,18 @@ def test_digit_split_fp64_limits_and_flags(F):
     bad[0, 4] = cm.nodes.shape[0] + 7
     F.tabulate_quadrature(qf, _dev(bad), nodes, precision="fp64_ozaki")
     assert F.status_poll() & F.FLAG_BOUNDS
+
+
+@pytest.mark.parametrize("scale_exp", [-40, 40])
+def test_digit_split_fp64_on_tiny_and_huge_cells(F, scale_exp):
+    """Cells scaled by 2^-40 and 2^40 (mass |det| by 2^-120 / 2^120, beyond FP32's range for
+    the column-scale estimate): the digit-split FP64 result is the unscaled one times the
+    exact power of two, to FP64 accuracy."""
+    cm = curved_mesh(3, 2, eps=0.12)
+    cells = _dev(cm.cells)
+    for form, power in ((0, 3), (1, 1)):
+        qf = F.QForm(form, F.TETRAHEDRON, 2, 2)
+        base = F.tabulate_quadrature(qf, cells, _dev(cm.nodes), precision="fp64_ozaki").cpu().numpy()
+        got = F.tabulate_quadrature(qf, cells, _dev(cm.nodes * 2.0 ** scale_exp), precision="fp64_ozaki")
+        assert F.status_poll() == 0
+        assert _rel(got.cpu().numpy() * 2.0 ** (-power * scale_exp), base) <= 1e-14
