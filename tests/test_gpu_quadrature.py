@@ -176,9 +176,11 @@ def test_quadrature_flags_and_limits(F):
 
 
 @pytest.mark.parametrize("d,n", [(2, 5), (3, 2)])
-@pytest.mark.parametrize("form,q", [(0, 1), (1, 1), (0, 2), (1, 2)])
+@pytest.mark.parametrize("form,q", [(0, 1), (1, 1), (0, 2), (1, 2), (1, 3)])
 @pytest.mark.parametrize("prec,tol", [("bf16x3", 1e-6), ("tf32x3", 1e-6), ("tf32", 1e-4)])
 def test_tensor_core_quadrature_matches_the_oracle(F, d, n, form, q, prec, tol):
+    if d == 3 and q == 3:
+        pytest.skip("P3 tets: 400 entries, more than one 128-entry tile")
     """The tcgen05 contraction (element tensors of at most 128 entries) on curved cells:
     the split precisions within the FP32 target 1e-6; single TF32 (11-bit operands) is
     applied only to the deviations of G~ from its centroid value, so its error is
@@ -301,3 +303,28 @@ def test_digit_split_fp64_on_tiny_and_huge_cells(F, scale_exp):
         got = F.tabulate_quadrature(qf, cells, _dev(cm.nodes * 2.0 ** scale_exp), precision="fp64_ozaki")
         assert F.status_poll() == 0
         assert _rel(got.cpu().numpy() * 2.0 ** (-power * scale_exp), base) <= 1e-14
+
+
+@pytest.mark.parametrize("prec", ["tf32x3", "fp64_ozaki"])
+def test_tensor_core_assembly_skips_a_bad_slot(F, prec):
+    """A slot outside [0, nnz) is skipped and reported; every other value is added."""
+    import torch
+
+    cm = curved_mesh(3, 2, eps=0.1)
+    qf = F.QForm(1, F.TETRAHEDRON, 2, 2)
+    dofmap, n_dof = D.scalar_dofmap(cm.mesh, 2)
+    _, col, slot = F.csr_pattern(dofmap, n_dof)
+    ref = torch.zeros(col.size, dtype=torch.float64, device="cuda")
+    F.assemble_quadrature(qf, _dev(cm.cells), _dev(cm.nodes), _dev(slot, torch.int32), ref, precision=prec)
+    assert F.status_poll() == 0
+    bad = slot.copy()
+    s0 = int(bad.reshape(-1)[5])
+    bad.reshape(-1)[5] = col.size + 3
+    val = torch.zeros(col.size, dtype=torch.float64, device="cuda")
+    F.assemble_quadrature(qf, _dev(cm.cells), _dev(cm.nodes), _dev(bad, torch.int32), val, precision=prec)
+    assert F.status_poll() & F.FLAG_BOUNDS
+    A = F.tabulate_quadrature(qf, _dev(cm.cells), _dev(cm.nodes), precision=prec).double().reshape(-1)
+    diff = (ref - val).cpu().numpy()
+    assert abs(diff[s0] - A[5].item()) <= 1e-9 * abs(A[5].item()) + 1e-15
+    diff[s0] = 0.0
+    assert np.abs(diff).max() <= 1e-9 * ref.abs().max().item()
