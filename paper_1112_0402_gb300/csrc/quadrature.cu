@@ -137,33 +137,7 @@ struct QParams {
   unsigned* status;
 };
 
-template <int D, typename T>
-__device__ __forceinline__ T det_adj(const T (&J)[D][D], T (&A)[D][D]) {
-  if constexpr (D == 2) {
-    A[0][0] = J[1][1];
-    A[0][1] = -J[0][1];
-    A[1][0] = -J[1][0];
-    A[1][1] = J[0][0];
-    return J[0][0] * J[1][1] - J[0][1] * J[1][0];
-  } else {
-    A[0][0] = J[1][1] * J[2][2] - J[1][2] * J[2][1];
-    A[0][1] = J[0][2] * J[2][1] - J[0][1] * J[2][2];
-    A[0][2] = J[0][1] * J[1][2] - J[0][2] * J[1][1];
-    A[1][0] = J[1][2] * J[2][0] - J[1][0] * J[2][2];
-    A[1][1] = J[0][0] * J[2][2] - J[0][2] * J[2][0];
-    A[1][2] = J[0][2] * J[1][0] - J[0][0] * J[1][2];
-    A[2][0] = J[1][0] * J[2][1] - J[1][1] * J[2][0];
-    A[2][1] = J[0][1] * J[2][0] - J[0][0] * J[2][1];
-    A[2][2] = J[0][0] * J[1][1] - J[0][1] * J[1][0];
-    return J[0][0] * A[0][0] + J[0][1] * A[1][0] + J[0][2] * A[2][0];
-  }
-}
-
-// column of the pair (a <= b): diagonal pairs first, then (0,1) [, (0,2), (1,2)]
-template <int D>
-__device__ __forceinline__ int qsym(int a, int b) {
-  return a == b ? a : (D == 2 ? 2 : (a == 0 ? (b == 1 ? 3 : 4) : 5));
-}
+using quad::det_adj;
 
 __device__ __forceinline__ void q_cp_async16(void* smem_dst, const void* gsrc) {
   const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(smem_dst));
@@ -290,7 +264,7 @@ __global__ void __launch_bounds__(QT_THREADS) quad_kernel(QParams p) {
             T sq = T(0);
 #pragma unroll
             for (int c = 0; c < D; ++c) sq = fma(A[a][c], A[b][c], sq);
-            gout[qsym<D>(a, b) * MC] = sq * r;
+            gout[quad::qpair<D>(a, b) * MC] = sq * r;
           }
       }
     }
@@ -448,13 +422,6 @@ constexpr int TQ_PRODUCER_WARPS = 8;
 constexpr int TQ_DRAIN_WARP0 = 8, TQ_MMA_WARP = 12, TQ_TMA_WARP = 13, TQ_GEO_WARP0 = 14;
 constexpr int TQ_THREADS = 512;
 constexpr int TQ_GEO_THREADS = TQ_THREADS - 32 * TQ_GEO_WARP0;
-
-// symmetric index of (b, c) in either order
-template <int D>
-__host__ __device__ constexpr int qsym_any(int b, int c) {
-  return b <= c ? (b == c ? b : (D == 2 ? 2 : (b == 0 ? (c == 1 ? 3 : 4) : 5)))
-                : (D == 2 ? 2 : (c == 0 ? (b == 1 ? 3 : 4) : 5));
-}
 
 template <int D, int FORM, int G, int MODE>
 struct TqCfg {
@@ -728,7 +695,7 @@ __global__ void __launch_bounds__(TQ_THREADS, 1) tq_kernel(TqParams p) {
               float sq = 0.f;
 #pragma unroll
               for (int cc = 0; cc < D; ++cc) sq = fmaf(A[a][cc], A[b][cc], sq);
-              out[qsym<D>(a, b)] = sq * r;
+              out[quad::qpair<D>(a, b)] = sq * r;
             }
         }
       };
@@ -746,7 +713,7 @@ __global__ void __launch_bounds__(TQ_THREADS, 1) tq_kernel(TqParams p) {
             float v = cj[a * D + b];
 #pragma unroll
             for (int cc = 0; cc < D; ++cc)
-              if constexpr (NH > 0) v = fmaf(cj[D * D + a * NH + qsym_any<D>(b, cc)], xc, v);
+              if constexpr (NH > 0) v = fmaf(cj[D * D + a * NH + quad::qpair<D>(b, cc)], xc, v);
             J[a][b] = v;
           }
         float A[D][D];
@@ -763,7 +730,7 @@ __global__ void __launch_bounds__(TQ_THREADS, 1) tq_kernel(TqParams p) {
               float sq = 0.f;
 #pragma unroll
               for (int cc = 0; cc < D; ++cc) sq = fmaf(A[a][cc], A[b][cc], sq);
-              gc[qsym<D>(a, b)] = sq * r;
+              gc[quad::qpair<D>(a, b)] = sq * r;
             }
         }
         if (G == 1 && !(ad > thr)) degenerate = true;
@@ -807,7 +774,7 @@ __global__ void __launch_bounds__(TQ_THREADS, 1) tq_kernel(TqParams p) {
               for (int b = 0; b < D; ++b) {
                 float v = cj[a * D + b];
 #pragma unroll
-                for (int cc = 0; cc < D; ++cc) v = fmaf(cj[D * D + a * NH + qsym_any<D>(b, cc)], X[cc], v);
+                for (int cc = 0; cc < D; ++cc) v = fmaf(cj[D * D + a * NH + quad::qpair<D>(b, cc)], X[cc], v);
                 J[a][b] = v;
               }
             point_geometry(J, col + pp * NG);
@@ -927,25 +894,11 @@ __global__ void __launch_bounds__(TQ_THREADS, 1) tq_kernel(TqParams p) {
   }
 }
 
-// The geometry table of the producers: gradients of the geometry basis at X = 0
-// [NGEO][D], its second derivatives [NGEO][D(D+1)/2] (geometry degree 2; differences of
-// the gradients at X = e_c and X = 0, exact for a quadratic basis), the rule's points [nq][D].
+// The producers' table in FP32: the geometry table, then A~0 summed over the points
+// [n*n][n_g] (FP64 sums rounded once), the drainers' centroid term.
 std::vector<float> tq_table(const ffc_qform* f) {
-  const int d = f->d, ng = f->ngeo, nh = f->g == 2 ? d * (d + 1) / 2 : 0;
-  std::vector<double> X(size_t(d + 1) * d, 0.0), psi, dpsi;
-  for (int c = 0; c < d; ++c) X[size_t(c + 1) * d + c] = 1.0;
-  reference_basis(d, f->g, X, psi, dpsi);  // [d+1][ng][d]
-  std::vector<float> t;
-  for (int nd = 0; nd < ng; ++nd)
-    for (int b = 0; b < d; ++b) t.push_back(float(dpsi[size_t(nd) * d + b]));
-  std::vector<double> h(size_t(ng) * std::max(nh, 1), 0.0);
-  for (int nd = 0; nd < ng && nh; ++nd)
-    for (int b = 0; b < d; ++b)
-      for (int c = b; c < d; ++c)
-        h[size_t(nd) * nh + sym_pair(d, b, c)] = dpsi[(size_t(c + 1) * ng + nd) * d + b] - dpsi[size_t(nd) * d + b];
-  for (int i = 0; i < ng * nh; ++i) t.push_back(float(h[i]));
-  for (double x : f->X) t.push_back(float(x));
-  // A~0 summed over the points, [n*n][n_g] (FP64 sums rounded once)
+  const std::vector<double> g = quad::geometry_table(f);
+  std::vector<float> t(g.begin(), g.end());
   for (int i = 0; i < f->n * f->n; ++i)
     for (int gg = 0; gg < f->ng; ++gg) {
       double sum = 0.0;
@@ -1123,6 +1076,28 @@ int check_args(const ffc_qform* f, int64_t n_elem, const int32_t* cells, const d
 }
 
 }  // namespace
+}  // namespace ffc
+
+namespace ffc {
+namespace quad {
+std::vector<double> geometry_table(const ffc_qform* f) {
+  const int d = f->d, ng = f->ngeo, nh = f->g == 2 ? d * (d + 1) / 2 : 0;
+  std::vector<double> X(size_t(d + 1) * d, 0.0), psi, dpsi;
+  for (int c = 0; c < d; ++c) X[size_t(c + 1) * d + c] = 1.0;
+  reference_basis(d, f->g, X, psi, dpsi);  // [d+1][ng][d]
+  std::vector<double> t;
+  for (int nd = 0; nd < ng; ++nd)
+    for (int b = 0; b < d; ++b) t.push_back(dpsi[size_t(nd) * d + b]);
+  std::vector<double> h(size_t(ng) * std::max(nh, 1), 0.0);
+  for (int nd = 0; nd < ng && nh; ++nd)
+    for (int b = 0; b < d; ++b)
+      for (int c = b; c < d; ++c)
+        h[size_t(nd) * nh + sym_pair(d, b, c)] = dpsi[(size_t(c + 1) * ng + nd) * d + b] - dpsi[size_t(nd) * d + b];
+  t.insert(t.end(), h.begin(), h.begin() + size_t(ng) * nh);
+  t.insert(t.end(), f->X.begin(), f->X.end());
+  return t;
+}
+}  // namespace quad
 }  // namespace ffc
 
 using namespace ffc;

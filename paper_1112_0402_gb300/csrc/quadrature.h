@@ -35,6 +35,48 @@ struct ffc_qform {
 };
 
 namespace ffc {
+namespace quad {
+
+// Column of the symmetric pair {a, b} (either order) in the Poisson geometry entries:
+// diagonal pairs first, then (0,1) [, (0,2), (1,2)].
+template <int D>
+__host__ __device__ constexpr int qpair(int a, int b) {
+  return a == b ? a : (D == 2 ? 2 : ((a == 0 || b == 0) ? ((a == 1 || b == 1) ? 3 : 4) : 5));
+}
+
+// Determinant of J and its adjugate A (J A = det I).
+template <int D, typename T>
+__host__ __device__ __forceinline__ T det_adj(const T (&J)[D][D], T (&A)[D][D]) {
+  if constexpr (D == 2) {
+    A[0][0] = J[1][1];
+    A[0][1] = -J[0][1];
+    A[1][0] = -J[1][0];
+    A[1][1] = J[0][0];
+    return J[0][0] * J[1][1] - J[0][1] * J[1][0];
+  } else {
+    A[0][0] = J[1][1] * J[2][2] - J[1][2] * J[2][1];
+    A[0][1] = J[0][2] * J[2][1] - J[0][1] * J[2][2];
+    A[0][2] = J[0][1] * J[1][2] - J[0][2] * J[1][1];
+    A[1][0] = J[1][2] * J[2][0] - J[1][0] * J[2][2];
+    A[1][1] = J[0][0] * J[2][2] - J[0][2] * J[2][0];
+    A[1][2] = J[0][2] * J[1][0] - J[0][0] * J[1][2];
+    A[2][0] = J[1][0] * J[2][1] - J[1][1] * J[2][0];
+    A[2][1] = J[0][1] * J[2][0] - J[0][0] * J[2][1];
+    A[2][2] = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+    return J[0][0] * A[0][0] + J[0][1] * A[1][0] + J[0][2] * A[2][0];
+  }
+}
+
+// The tensor-core producers' geometry table of a form (FP64): gradients of the geometry
+// basis at X = 0 [n_geometry][d], its second derivatives [n_geometry][d(d+1)/2] (geometry
+// degree 2 only; differences of the gradients at X = e_c and X = 0, exact for a quadratic
+// basis), then the rule's points [nq][d]. F'(X) of the cell is then affine in X:
+// F'(X)[a][b] = J0[a][b] + sum_c H[a][{b,c}] X_c with J0 and H these tables contracted with
+// the cell's geometry nodes.
+std::vector<double> geometry_table(const ffc_qform* f);
+
+}  // namespace quad
+
 // Where a tensor-core quadrature kernel puts A_K: stored into `out` ([n_elem][n*n], float or
 // double by precision), or, when `slot` is set, added into csr_val[slot[e][i]] with FP64
 // atomics (Algorithm 2; a slot outside [0, nnz) sets FFC_FLAG_BOUNDS and is skipped).

@@ -72,11 +72,8 @@ constexpr unsigned long long OZ_OFF = 64ull * ((1ull << 42) + (1ull << 35) + (1u
                                                (1ull << 14) + (1ull << 7) + 1ull);
 static_assert(OZ_N == OZ_GEO_THREADS && 2 * OZ_N == 32 * OZ_PROD_WARPS, "one geometry thread, two producers per cell");
 
-template <int D>
-__host__ __device__ constexpr int osym(int b, int c) {  // symmetric pair index of (b, c), either order
-  return b <= c ? (b == c ? b : (D == 2 ? 2 : (b == 0 ? (c == 1 ? 3 : 4) : 5)))
-                : (D == 2 ? 2 : (c == 0 ? (b == 1 ? 3 : 4) : 5));
-}
+using quad::det_adj;
+using quad::qpair;
 
 template <int D, int FORM, int G>
 struct OzCfg {
@@ -119,28 +116,6 @@ __device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t phase, volatile
   return __all_sync(0xffffffffu, ok);
 }
 
-template <int D, typename T>
-__device__ __forceinline__ T det_adj(const T (&J)[D][D], T (&A)[D][D]) {
-  if constexpr (D == 2) {
-    A[0][0] = J[1][1];
-    A[0][1] = -J[0][1];
-    A[1][0] = -J[1][0];
-    A[1][1] = J[0][0];
-    return J[0][0] * J[1][1] - J[0][1] * J[1][0];
-  } else {
-    A[0][0] = J[1][1] * J[2][2] - J[1][2] * J[2][1];
-    A[0][1] = J[0][2] * J[2][1] - J[0][1] * J[2][2];
-    A[0][2] = J[0][1] * J[1][2] - J[0][2] * J[1][1];
-    A[1][0] = J[1][2] * J[2][0] - J[1][0] * J[2][2];
-    A[1][1] = J[0][0] * J[2][2] - J[0][2] * J[2][0];
-    A[1][2] = J[0][2] * J[1][0] - J[0][0] * J[1][2];
-    A[2][0] = J[1][0] * J[2][1] - J[1][1] * J[2][0];
-    A[2][1] = J[0][1] * J[2][0] - J[0][0] * J[2][1];
-    A[2][2] = J[0][0] * J[1][1] - J[0][1] * J[1][0];
-    return J[0][0] * A[0][0] + J[0][1] * A[1][0] + J[0][2] * A[2][0];
-  }
-}
-
 // G~ entries of one point from its Jacobian: mass |det|, Poisson adj adj^T / |det| in the
 // pair order (diagonal first, then (0,1) [, (0,2), (1,2)])
 template <int D, int FORM, typename T>
@@ -163,7 +138,7 @@ __device__ __forceinline__ T point_values(const T (&J)[D][D], T* v) {
         T sq = T(0);
 #pragma unroll
         for (int cc = 0; cc < D; ++cc) sq = fma(A[a][cc], A[b][cc], sq);
-        v[osym<D>(a, b)] = sq * r;
+        v[qpair<D>(a, b)] = sq * r;
       }
   }
   return ad;
@@ -395,7 +370,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_kernel(OzParams p) {
             float x = c32[a * D + b];
 #pragma unroll
             for (int cc = 0; cc < D; ++cc)
-              if constexpr (NH > 0) x = fmaf(c32[D * D + a * NH + osym<D>(b, cc)], xq32[k * D + cc], x);
+              if constexpr (NH > 0) x = fmaf(c32[D * D + a * NH + qpair<D>(b, cc)], xq32[k * D + cc], x);
             J[a][b] = x;
           }
         point_values<D, FORM, float>(J, v);
@@ -476,7 +451,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_kernel(OzParams p) {
                 double x = cellj[(a * D + b) * OZ_N + c];
 #pragma unroll
                 for (int cc = 0; cc < D; ++cc)
-                  x = fma(cellj[(D * D + a * NH + osym<D>(b, cc)) * OZ_N + c], xq[k * D + cc], x);
+                  x = fma(cellj[(D * D + a * NH + qpair<D>(b, cc)) * OZ_N + c], xq[k * D + cc], x);
                 J[a][b] = x;
               }
             const double ad = point_values<D, FORM, double>(J, v);
@@ -626,22 +601,8 @@ int upload_oz(ffc_qform* f, ffc_qform::Dev* dv, int nch) {
       }
     }
   }
-  // table: [ngeo][d] gradients at X = 0, [ngeo][nh] second derivatives (differences of the
-  // gradients at X = e_c and 0, exact for a quadratic basis), [nq][d] points, e_i [128]
-  const int ngeo = f->ngeo, nh = f->g == 2 ? d * (d + 1) / 2 : 0;
-  std::vector<double> X(size_t(d + 1) * d, 0.0), psi, dpsi;
-  for (int c = 0; c < d; ++c) X[size_t(c + 1) * d + c] = 1.0;
-  reference_basis(d, f->g, X, psi, dpsi);  // [d+1][ngeo][d]
-  std::vector<double> tab;
-  for (int nd = 0; nd < ngeo; ++nd)
-    for (int b = 0; b < d; ++b) tab.push_back(dpsi[size_t(nd) * d + b]);
-  std::vector<double> h(size_t(ngeo) * std::max(nh, 1), 0.0);
-  for (int nd = 0; nd < ngeo && nh; ++nd)
-    for (int b = 0; b < d; ++b)
-      for (int c = b; c < d; ++c)
-        h[size_t(nd) * nh + sym_pair(d, b, c)] = dpsi[(size_t(c + 1) * ngeo + nd) * d + b] - dpsi[size_t(nd) * d + b];
-  for (int i = 0; i < ngeo * nh; ++i) tab.push_back(h[i]);
-  tab.insert(tab.end(), f->X.begin(), f->X.end());
+  // the geometry table, then e_i [128]
+  std::vector<double> tab = quad::geometry_table(f);
   tab.insert(tab.end(), erow.begin(), erow.end());
   cudaError_t e = cudaSuccess;
   void* a = nullptr;
