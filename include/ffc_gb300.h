@@ -393,12 +393,14 @@ void ffc_qform_destroy(ffc_qform* f);
  * FFC_FLAG_BOUNDS (its cell's tensor is then computed from node 0); a point where
  * |det F'| <= 1e-14 h^d (h the largest node distance from node 0) sets
  * FFC_FLAG_DEGENERATE.
- * FFC_TF32 / FFC_TF32X3 / FFC_BF16X3 (element tensors of at most 128 entries: P1-P2 on
- * tets, P1-P3 on triangles, else FFC_EUNSUPPORTED): the contraction on the tensor cores
- * (tcgen05) in 128-cell tiles, A~0 split into TF32 or BF16 parts on the host, G~_K per
- * point in FP32 split the same way on the device, A_K written as float. The split
- * precisions keep FP32 accuracy; FFC_TF32 alone has TF32's 11-bit precision.
- * FFC_FP64_OZAKI (the same element tensors of at most 128 entries, and K = points x n_g
+ * FFC_TF32 / FFC_TF32X3 / FFC_BF16X3 (element tensors of at most 512 entries, up to four
+ * 128-entry M tiles: P1-P3 on tets, P1-P4 on triangles, else FFC_EUNSUPPORTED): the
+ * contraction on the tensor cores (tcgen05) in 128-cell tiles, A~0 split into TF32 or
+ * BF16 parts on the host, G~_K per point in FP32 split the same way on the device, the
+ * tensor cores accumulating G~_K(X_k) - G~_K(centroid) and the centroid term added in
+ * FP32, A_K written as float. The split precisions keep FP32 accuracy; FFC_TF32 alone has
+ * TF32's 11-bit precision (times the deviations' relative size).
+ * FFC_FP64_OZAKI (element tensors of at most 128 entries, and K = points x n_g
  * at most 400, else FFC_EUNSUPPORTED): A_K as double, FP64-accurate, with the contraction
  * on the tensor cores by exact products of small-integer digits (the splitting of Ozaki,
  * Ogita, Oishi and Rump, Numer. Algorithms 59, 2012): each row of A~0 and each cell's

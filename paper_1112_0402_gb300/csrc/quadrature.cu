@@ -458,12 +458,13 @@ struct TqParams {
   long long n_nodes, n_elem;
   const float* table;       // [NGEO][D] dPsi(0), [NGEO][NH] second derivatives, [nq][D] points
   const float* a0sum;       // [nn][NG]: A~0 summed over the points (the centroid term)
-  const void* a_part[3];    // [NCH][128 x QKCH] per part
+  const void* a_part[3];    // [NCH][MT][128 x QKCH] per part: chunk c of M tile m at block c * MT + m
   float* out;               // A_K [n_elem][nn], or (slot set) CSR values csr_val[slot] += A_K
   const int32_t* slot;
   double* csr_val;
   long long nnz;
   int nn, nq, nch;
+  int mt;                   // 128-entry M tiles (1..4)
   unsigned* status;
 };
 
@@ -514,9 +515,14 @@ __global__ void __launch_bounds__(TQ_THREADS, 1) tq_kernel(TqParams p) {
     abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
+  // one M tile: two accumulator buffers (main and correction products apart, the drain of a
+  // tile overlapping the next tile's MMAs); two to four M tiles: one 128-column accumulator
+  // per M tile holding all the products, single-buffered
+  const uint32_t tmem_cols = p.mt > 1 ? 512u : C::TMEM_COLS;
+  const int nbuf = p.mt > 1 ? 1 : 2;
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                 "r"(C::TMEM_COLS));
+                 "r"(tmem_cols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   fence_before();
@@ -525,7 +531,8 @@ __global__ void __launch_bounds__(TQ_THREADS, 1) tq_kernel(TqParams p) {
   const uint32_t tmem = *tmem_slot;
   const long long n_tiles = (p.n_elem + N_CELLS - 1) / N_CELLS;
   const long long my_tiles = blockIdx.x < n_tiles ? (n_tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
-  const long long total = my_tiles * p.nch;  // chunks this CTA consumes
+  const int nblk = p.nch * p.mt;                   // A~0 blocks per cell tile
+  const long long total = my_tiles * nblk;         // A~0 blocks this CTA consumes
   if (warp == TQ_TMA_WARP) {
     // ---------------------------------------------------------------- TMA: A~0 chunks
     if (lane == 0) {
@@ -534,7 +541,7 @@ __global__ void __launch_bounds__(TQ_THREADS, 1) tq_kernel(TqParams p) {
         const int s = int(g & 1);
         if (g >= 2) ok = mbar_wait_or_abort(bar(A_EMPTY + s), uint32_t((g - 2) >> 1) & 1u, &abort_flag);
         if (!ok) break;
-        const long long c = g % p.nch;
+        const long long c = g % nblk;
         mbar_expect_tx(bar(A_FULL + s), C::STAGE_BYTES);
 #pragma unroll
         for (int q = 0; q < S::PARTS; ++q)
@@ -554,32 +561,39 @@ __global__ void __launch_bounds__(TQ_THREADS, 1) tq_kernel(TqParams p) {
       constexpr uint32_t SBO = C::KCC * 128;
       constexpr int KS = QKCH / S::KSTEP;
       bool ok = true;
-      long long g = 0;
+      long long ga = 0, gb = 0;  // A~0 blocks and G~ chunks consumed
       for (long long ct = 0; ct < my_tiles && ok; ++ct) {
-        const int acc = int(ct & 1);
-        if (ct >= 2) ok = mbar_wait_or_abort(bar(ACC_EMPTY + acc), uint32_t((ct - 2) >> 1) & 1u, &abort_flag);
+        const int acc = int(ct % nbuf);
+        const long long use = ct / nbuf;
+        if (ct >= nbuf) ok = mbar_wait_or_abort(bar(ACC_EMPTY + acc), uint32_t(use - 1) & 1u, &abort_flag);
         if (!ok) break;
-        const uint32_t d_main = tmem + uint32_t(acc * C::ACC_COLS);
-        const uint32_t d_corr = d_main + uint32_t(N_CELLS);
-        for (int c = 0; c < p.nch && ok; ++c, ++g) {
-          const int s = int(g & 1);
-          const uint32_t ph = uint32_t(g >> 1) & 1u;
-          ok = mbar_wait_or_abort(bar(A_FULL + s), ph, &abort_flag) && mbar_wait_or_abort(bar(B_FULL + s), ph, &abort_flag);
-          if (!ok) break;
-          fence_after();
+        for (int c = 0; c < p.nch && ok; ++c, ++gb) {
+          const int sb = int(gb & 1);
+          ok = mbar_wait_or_abort(bar(B_FULL + sb), uint32_t(gb >> 1) & 1u, &abort_flag);
+          for (int m = 0; m < p.mt && ok; ++m, ++ga) {
+            const int sa = int(ga & 1);
+            ok = mbar_wait_or_abort(bar(A_FULL + sa), uint32_t(ga >> 1) & 1u, &abort_flag);
+            if (!ok) break;
+            fence_after();
+            const uint32_t d_main = tmem + uint32_t(nbuf > 1 ? acc * C::ACC_COLS : m * N_CELLS);
+            const uint32_t d_corr = d_main + uint32_t(N_CELLS);
 #pragma unroll
-          for (int ks = 0; ks < KS; ++ks) {
+            for (int ks = 0; ks < KS; ++ks) {
 #pragma unroll
-            for (int k = 0; k < S::NPROD; ++k) {
-              const uint64_t da = smem_desc(smem_u32(As + s * C::STAGE_BYTES + S::pa(k) * C::CH_BYTES) + ks * 256, 128, SBO);
-              const uint64_t db = smem_desc(smem_u32(Bs + s * C::STAGE_BYTES + S::pb(k) * C::CH_BYTES) + ks * 256, 128, SBO);
-              const bool first = c == 0 && ks == 0;
-              if (k == S::NPROD - 1) mma<S::BF16>(d_main, da, db, IDESC, first ? 0u : 1u);
-              else mma<S::BF16>(d_corr, da, db, IDESC, (first && k == 0) ? 0u : 1u);
+              for (int k = 0; k < S::NPROD; ++k) {
+                const uint64_t da =
+                    smem_desc(smem_u32(As + sa * C::STAGE_BYTES + S::pa(k) * C::CH_BYTES) + ks * 256, 128, SBO);
+                const uint64_t db =
+                    smem_desc(smem_u32(Bs + sb * C::STAGE_BYTES + S::pb(k) * C::CH_BYTES) + ks * 256, 128, SBO);
+                const bool first = c == 0 && ks == 0;
+                if (nbuf == 1) mma<S::BF16>(d_main, da, db, IDESC, (first && k == 0) ? 0u : 1u);
+                else if (k == S::NPROD - 1) mma<S::BF16>(d_main, da, db, IDESC, first ? 0u : 1u);
+                else mma<S::BF16>(d_corr, da, db, IDESC, (first && k == 0) ? 0u : 1u);
+              }
             }
+            mma_commit(bar(A_EMPTY + sa));
           }
-          mma_commit(bar(A_EMPTY + s));
-          mma_commit(bar(B_EMPTY + s));
+          if (ok) mma_commit(bar(B_EMPTY + sb));
         }
         if (ok) mma_commit(bar(ACC_FULL + acc));
       }
@@ -587,7 +601,7 @@ __global__ void __launch_bounds__(TQ_THREADS, 1) tq_kernel(TqParams p) {
         atomicOr(p.status, FFC_FLAG_TIMEOUT);
         abort_flag = 1;
       }
-      if (g > 0) mbar_wait(bar(A_EMPTY + int((g - 1) & 1)), uint32_t((g - 1) >> 1) & 1u);  // last chain done
+      if (ga > 0) mbar_wait(bar(A_EMPTY + int((ga - 1) & 1)), uint32_t((ga - 1) >> 1) & 1u);  // last chain done
     }
   } else if (warp >= TQ_GEO_WARP0) {
     // ---------------------------------------------------------------- per-cell geometry, one tile ahead
@@ -820,25 +834,27 @@ __global__ void __launch_bounds__(TQ_THREADS, 1) tq_kernel(TqParams p) {
     // ---------------------------------------------------------------- drainers: TMEM -> A_K
     bool ok = true;
     const int q4 = warp - TQ_DRAIN_WARP0;  // TMEM lanes 32 q4 .. 32 q4 + 31 (warp % 4)
-    const int i = q4 * 32 + lane;  // element-tensor entry (TMEM lane)
-    float a0s[NG];
-#pragma unroll
-    for (int gg = 0; gg < NG; ++gg) a0s[gg] = i < p.nn ? p.a0sum[i * NG + gg] : 0.f;
     for (long long ct = 0; ct < my_tiles && ok; ++ct) {
-      const int acc = int(ct & 1);
-      ok = warp_wait(bar(ACC_FULL + acc), uint32_t(ct >> 1) & 1u, &abort_flag) &&
-           warp_wait(bar(GBAR_FULL + acc), uint32_t(ct >> 1) & 1u, &abort_flag);
+      const int acc = int(ct % nbuf), gsl = int(ct & 1);
+      ok = warp_wait(bar(ACC_FULL + acc), uint32_t(ct / nbuf) & 1u, &abort_flag) &&
+           warp_wait(bar(GBAR_FULL + gsl), uint32_t(ct >> 1) & 1u, &abort_flag);
       if (!ok) break;
       fence_after();
-      const float* gb = gbar + acc * NG * N_CELLS;
+      const float* gb = gbar + gsl * NG * N_CELLS;
       const long long e0 = (blockIdx.x + ct * gridDim.x) * N_CELLS;
-      const uint32_t taddr = tmem + (uint32_t(q4 * 32) << 16) + uint32_t(acc * C::ACC_COLS);
+#pragma unroll 1
+      for (int m = 0; m < p.mt; ++m) {
+      const int i = m * M_TILE + q4 * 32 + lane;  // element-tensor entry (TMEM lane of M tile m)
+      float a0s[NG];
+#pragma unroll
+      for (int gg = 0; gg < NG; ++gg) a0s[gg] = i < p.nn ? p.a0sum[i * NG + gg] : 0.f;
+      const uint32_t taddr = tmem + (uint32_t(q4 * 32) << 16) + uint32_t(nbuf > 1 ? acc * C::ACC_COLS : m * N_CELLS);
 #pragma unroll 1
       for (int c = 0; c < N_CELLS / 16; ++c) {
         uint32_t rv[16];
         float v[16];
         tmem_ld16_issue(taddr + c * 16, rv);
-        if constexpr (S::NPROD > 1) {
+        if (S::NPROD > 1 && nbuf > 1) {
           uint32_t rw[16];
           tmem_ld16_issue(taddr + N_CELLS + c * 16, rw);
           tmem_wait_ld();
@@ -874,11 +890,12 @@ __global__ void __launch_bounds__(TQ_THREADS, 1) tq_kernel(TqParams p) {
           }
         }
       }
+      }
       fence_before();
       __syncwarp();
       if (lane == 0) {
         mbar_arrive(bar(ACC_EMPTY + acc));
-        mbar_arrive(bar(GBAR_EMPTY + acc));
+        mbar_arrive(bar(GBAR_EMPTY + gsl));
       }
     }
     if (!ok) {
@@ -890,7 +907,7 @@ __global__ void __launch_bounds__(TQ_THREADS, 1) tq_kernel(TqParams p) {
   __syncthreads();
   if (warp == 0) {
     fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(C::TMEM_COLS));
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols));
   }
 }
 
@@ -914,14 +931,15 @@ int upload_tq(ffc_qform* f, ffc_qform::Dev* dv, int nch) {
   const int fam = S::BF16 ? 1 : 0;
   std::lock_guard<std::mutex> g(f->lock);
   if (dv->tc_part[fam][S::PARTS - 1] && dv->tq_table) return FFC_OK;
-  const int nn = f->n * f->n, K = f->K;
-  const size_t per = size_t(nch) * M_TILE * QKCH;  // elements per part
+  const int nn = f->n * f->n, K = f->K, mt = (nn + M_TILE - 1) / M_TILE;
+  const size_t per = size_t(nch) * mt * M_TILE * QKCH;  // elements per part
   const int nparts = S::BF16 ? 3 : 2;  // a family uploads all its parts once
   std::vector<std::vector<typename S::Store>> parts(nparts, std::vector<typename S::Store>(per, 0));
   for (int i = 0; i < nn; ++i)
     for (int j = 0; j < K; ++j) {
       double r = f->At[size_t(i) * K + j];
-      const size_t o = size_t(j / QKCH) * (M_TILE * QKCH) + core_offset(i, j % QKCH, QKCH / S::EPC, S::EPC);
+      const size_t o = (size_t(j / QKCH) * mt + i / M_TILE) * (M_TILE * QKCH) +
+                       core_offset(i % M_TILE, j % QKCH, QKCH / S::EPC, S::EPC);
       for (int q = 0; q < nparts; ++q) {
         if constexpr (S::BF16) {
           const uint16_t b = host_bf16_bits(r);
@@ -980,6 +998,7 @@ int launch_tq(ffc_qform* f, ffc_qform::Dev* dv, long long n_elem, const int32_t*
   p.nn = f->n * f->n;
   p.nq = f->nq;
   p.nch = nch;
+  p.mt = (p.nn + M_TILE - 1) / M_TILE;
   p.status = status;
   auto kern = tq_kernel<D, FORM, G, MODE>;
   int sms = 0;
@@ -1060,8 +1079,8 @@ int check_args(const ffc_qform* f, int64_t n_elem, const int32_t* cells, const d
                                                : ": invalid argument (precision must be FFC_FP64 or FFC_FP32)"));
     return FFC_EINVAL;
   }
-  if (tc && f->n * f->n > tc::M_TILE) {
-    set_error(std::string(who) + ": the tensor-core precisions take element tensors of at most 128 entries");
+  if (tc && f->n * f->n > 4 * tc::M_TILE) {
+    set_error(std::string(who) + ": the tensor-core precisions take element tensors of at most 512 entries");
     return FFC_EUNSUPPORTED;
   }
   if (oz) {

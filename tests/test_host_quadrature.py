@@ -108,17 +108,16 @@ def test_qform_validates_arguments():
 
 
 def test_tensor_core_precisions_are_checked_before_device_work():
-    """ffc_tabulate_quadrature takes the tensor-core precisions for element tensors of at
-    most 128 entries (refused with FFC_EUNSUPPORTED above), ffc_assemble_quadrature does
-    not take them at all."""
+    """The tensor-core precisions take element tensors of at most 512 entries (refused with
+    FFC_EUNSUPPORTED above); bad pointers are refused before any device work."""
     F = _F()
     from paper_1112_0402_gb300 import _capi
 
     L = _capi.lib()
-    p3 = F.QForm(F.POISSON, F.TETRAHEDRON, 3, 2)  # 20 x 20 = 400 entries
+    p4 = F.QForm(F.POISSON, F.TETRAHEDRON, 4, 2)  # 35 x 35 = 1225 entries, more than four M tiles
     p2 = F.QForm(F.POISSON, F.TETRAHEDRON, 2, 2)
     for prec in (F.TF32, F.TF32X3, F.BF16X3):
-        assert L.ffc_tabulate_quadrature(p3.handle, 4, None, None, 10, None, prec, None) == -5
+        assert L.ffc_tabulate_quadrature(p4.handle, 4, None, None, 10, None, prec, None) == -5
         assert L.ffc_tabulate_quadrature(p2.handle, 4, None, None, 10, None, prec, None) == -1  # null cells
         assert L.ffc_assemble_quadrature(p2.handle, 4, None, None, 10, None, None, 5, prec, None) == -1
 
