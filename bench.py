@@ -1136,6 +1136,19 @@ def measure_other(F, args, device, workload):
         assert F.status_poll() == 0
         detail["tf32x3_max_rel_err_vs_fp64"] = max_rel(A32)
         del A64, A32
+        # P3 (400 entries: four 128-entry M tiles on the tensor cores), FP32 on CUDA cores
+        # against the tensor-core splits, worst cell against FP64
+        q3 = F.QForm(F.POISSON, F.TETRAHEDRON, 3, 2)
+        B64 = F.tabulate_quadrature(q3, cells, nodes, "fp64")
+        B32 = torch.empty((cm.n_elem, 20, 20), dtype=torch.float32, device=device)
+        p3 = {}
+        for prec in ("fp32", "tf32x3", "bf16x3"):
+            tp = _timed(lambda: F.tabulate_quadrature(q3, cells, nodes, prec, out=B32), args.steps, 1)
+            assert F.status_poll() == 0
+            d3 = (B32.double() - B64).reshape(cm.n_elem, -1).norm(dim=1) / B64.reshape(cm.n_elem, -1).norm(dim=1)
+            p3[prec] = {"ms": tp * 1e3, "max_rel_err_vs_fp64": float(d3.max())}
+        detail["poisson_p3"] = p3
+        del B64, B32
         # algorithmic FLOPs of the contraction (one product, n^2 entries) and those the
         # tensor cores execute (128-entry M tiles, K padded to 48-column chunks, 3 products)
         flops_alg = 2.0 * n * n * qf.k_contract * cm.n_elem
