@@ -474,7 +474,7 @@ __device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t phase, volatile
   return __all_sync(0xffffffffu, ok);
 }
 
-template <int D, int FORM, int G, int MODE>
+template <int D, int FORM, int G, int MODE, bool MULTI>
 __global__ void __launch_bounds__(TQ_THREADS, 1) tq_kernel(TqParams p) {
   using C = TqCfg<D, FORM, G, MODE>;
   using S = Split<MODE>;
@@ -515,11 +515,12 @@ __global__ void __launch_bounds__(TQ_THREADS, 1) tq_kernel(TqParams p) {
     abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  // one M tile: two accumulator buffers (main and correction products apart, the drain of a
-  // tile overlapping the next tile's MMAs); two to four M tiles: one 128-column accumulator
-  // per M tile holding all the products, single-buffered
-  const uint32_t tmem_cols = p.mt > 1 ? 512u : C::TMEM_COLS;
-  const int nbuf = p.mt > 1 ? 1 : 2;
+  // one M tile (MULTI false): two accumulator buffers (main and correction products apart,
+  // the drain of a tile overlapping the next tile's MMAs); two to four M tiles (MULTI
+  // true): one 128-column accumulator per M tile holding all the products, single-buffered
+  constexpr uint32_t tmem_cols = MULTI ? 512u : C::TMEM_COLS;
+  constexpr int nbuf = MULTI ? 1 : 2;
+  const int mt = MULTI ? p.mt : 1;
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
                  "r"(tmem_cols));
@@ -531,7 +532,7 @@ __global__ void __launch_bounds__(TQ_THREADS, 1) tq_kernel(TqParams p) {
   const uint32_t tmem = *tmem_slot;
   const long long n_tiles = (p.n_elem + N_CELLS - 1) / N_CELLS;
   const long long my_tiles = blockIdx.x < n_tiles ? (n_tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
-  const int nblk = p.nch * p.mt;                   // A~0 blocks per cell tile
+  const int nblk = p.nch * mt;                     // A~0 blocks per cell tile
   const long long total = my_tiles * nblk;         // A~0 blocks this CTA consumes
   if (warp == TQ_TMA_WARP) {
     // ---------------------------------------------------------------- TMA: A~0 chunks
@@ -570,7 +571,7 @@ __global__ void __launch_bounds__(TQ_THREADS, 1) tq_kernel(TqParams p) {
         for (int c = 0; c < p.nch && ok; ++c, ++gb) {
           const int sb = int(gb & 1);
           ok = mbar_wait_or_abort(bar(B_FULL + sb), uint32_t(gb >> 1) & 1u, &abort_flag);
-          for (int m = 0; m < p.mt && ok; ++m, ++ga) {
+          for (int m = 0; m < mt && ok; ++m, ++ga) {
             const int sa = int(ga & 1);
             ok = mbar_wait_or_abort(bar(A_FULL + sa), uint32_t(ga >> 1) & 1u, &abort_flag);
             if (!ok) break;
@@ -586,7 +587,7 @@ __global__ void __launch_bounds__(TQ_THREADS, 1) tq_kernel(TqParams p) {
                 const uint64_t db =
                     smem_desc(smem_u32(Bs + sb * C::STAGE_BYTES + S::pb(k) * C::CH_BYTES) + ks * 256, 128, SBO);
                 const bool first = c == 0 && ks == 0;
-                if (nbuf == 1) mma<S::BF16>(d_main, da, db, IDESC, (first && k == 0) ? 0u : 1u);
+                if constexpr (MULTI) mma<S::BF16>(d_main, da, db, IDESC, (first && k == 0) ? 0u : 1u);
                 else if (k == S::NPROD - 1) mma<S::BF16>(d_main, da, db, IDESC, first ? 0u : 1u);
                 else mma<S::BF16>(d_corr, da, db, IDESC, (first && k == 0) ? 0u : 1u);
               }
@@ -834,6 +835,9 @@ __global__ void __launch_bounds__(TQ_THREADS, 1) tq_kernel(TqParams p) {
     // ---------------------------------------------------------------- drainers: TMEM -> A_K
     bool ok = true;
     const int q4 = warp - TQ_DRAIN_WARP0;  // TMEM lanes 32 q4 .. 32 q4 + 31 (warp % 4)
+    float a0s1[NG];  // one M tile: the entry's centroid-term row, loaded once
+#pragma unroll
+    for (int gg = 0; gg < NG; ++gg) a0s1[gg] = (!MULTI && q4 * 32 + lane < p.nn) ? p.a0sum[(q4 * 32 + lane) * NG + gg] : 0.f;
     for (long long ct = 0; ct < my_tiles && ok; ++ct) {
       const int acc = int(ct % nbuf), gsl = int(ct & 1);
       ok = warp_wait(bar(ACC_FULL + acc), uint32_t(ct / nbuf) & 1u, &abort_flag) &&
@@ -843,18 +847,18 @@ __global__ void __launch_bounds__(TQ_THREADS, 1) tq_kernel(TqParams p) {
       const float* gb = gbar + gsl * NG * N_CELLS;
       const long long e0 = (blockIdx.x + ct * gridDim.x) * N_CELLS;
 #pragma unroll 1
-      for (int m = 0; m < p.mt; ++m) {
+      for (int m = 0; m < mt; ++m) {
       const int i = m * M_TILE + q4 * 32 + lane;  // element-tensor entry (TMEM lane of M tile m)
       float a0s[NG];
 #pragma unroll
-      for (int gg = 0; gg < NG; ++gg) a0s[gg] = i < p.nn ? p.a0sum[i * NG + gg] : 0.f;
+      for (int gg = 0; gg < NG; ++gg) a0s[gg] = MULTI ? (i < p.nn ? p.a0sum[i * NG + gg] : 0.f) : a0s1[gg];
       const uint32_t taddr = tmem + (uint32_t(q4 * 32) << 16) + uint32_t(nbuf > 1 ? acc * C::ACC_COLS : m * N_CELLS);
 #pragma unroll 1
       for (int c = 0; c < N_CELLS / 16; ++c) {
         uint32_t rv[16];
         float v[16];
         tmem_ld16_issue(taddr + c * 16, rv);
-        if (S::NPROD > 1 && nbuf > 1) {
+        if constexpr (S::NPROD > 1 && !MULTI) {
           uint32_t rw[16];
           tmem_ld16_issue(taddr + N_CELLS + c * 16, rw);
           tmem_wait_ld();
@@ -1000,7 +1004,7 @@ int launch_tq(ffc_qform* f, ffc_qform::Dev* dv, long long n_elem, const int32_t*
   p.nch = nch;
   p.mt = (p.nn + M_TILE - 1) / M_TILE;
   p.status = status;
-  auto kern = tq_kernel<D, FORM, G, MODE>;
+  auto kern = p.mt > 1 ? tq_kernel<D, FORM, G, MODE, true> : tq_kernel<D, FORM, G, MODE, false>;
   int sms = 0;
   if (launch_config(reinterpret_cast<const void*>(kern), TQ_THREADS, smem, -1, &sms, nullptr) != FFC_OK)
     return FFC_ECUDA;
