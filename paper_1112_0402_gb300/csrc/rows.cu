@@ -591,7 +591,6 @@ struct RowsCfg {
   static constexpr int W = MAIN ? N - 32 : N;        // columns spread over the lanes in order
   static constexpr int I0 = MAIN ? 32 : 0;           // first of those columns
   static constexpr int PER = W > 0 ? W / gcd_c(32, W) : 1;  // steps after which a lane's column repeats
-  static constexpr int UMAX = rows_umax(N);         // pairs of one work unit
   static constexpr int NP = D * (D + 1) / 2;
   static constexpr int NA = FORM == ROWS_PAIR ? 1 + NP : (FORM == FFC_POISSON ? NP : 1);  // A0 values per entry
   static constexpr int NG = FORM == FFC_MASS ? 1 : 8;  // G_K values read per pair (vector loads)
