@@ -283,12 +283,13 @@ void ffc_batch_destroy(ffc_batch* b);
  * produced it) is rounded to a grid with one unit per chunk and form, where 2^(eb-1)
  * bounds every partial sum of the chunk's entries (the largest per-pair bound
  * max|A0[i1][.][.]| * sum|G_K| times the most pairs of one row): u = 2^(eb-62) (63 bits,
- * three 21-bit digits) for FFC_FP64 and u = 2^(eb-41) (42 bits, two digits) for FFC_FP32,
- * whose contributions carry 24 bits. The digits are summed as 32-bit integers in shared
- * memory, so the sums do not depend on their order, and each result is rounded once to
- * FP64. Per entry: |result - exact sum of the contributions| <= m * u / 2 + ulp(result)
- * with m the entry's number of contributions (u / 2 < 2^-40 B for FP32, 2^-61 B for FP64,
- * B the chunk's bound). Results are bitwise reproducible.
+ * three 21-bit digits) for FFC_FP64 and u = 2^(eb-31) (31 bits, one digit) for FFC_FP32.
+ * The digits are summed as 32-bit integers in shared memory, so the sums do not depend on
+ * their order, and each result is rounded once to FP64. Per entry: |result - exact sum
+ * of the contributions| <= m * u / 2 + ulp(result) with m the entry's number of
+ * contributions (u / 2 < 2^-30 B for FP32, 2^-61 B for FP64, B the chunk's bound): for
+ * FP32 well inside 1e-6 of the row's sum of |contributions|. Results are bitwise
+ * reproducible.
  *
  * ffc_row_plan_create -- the row view of a dof map and its CSR pattern, built on the
  * device once per (mesh, space):

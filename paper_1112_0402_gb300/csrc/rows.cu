@@ -27,20 +27,21 @@
 // Fixed-point accumulation. The sums are kept in fixed point with one unit per chunk and
 // form, where 2^(eb-1) bounds every partial sum of every entry of the chunk (the largest
 // |contribution| bound of a pair, a0max[i1] * sum|G_K|, times the largest number of pairs
-// of one row). A contribution x is split into signed digits on the grids 2^(eb-20),
-// 2^(eb-41) (and 2^(eb-62) for FP64 contributions, u = 2^(eb-62); FP32 contributions,
-// 24 bits each, use the first two, u = 2^(eb-41)), each found by adding and subtracting
-// the FP32 constant 1.5 * 2^(grid + 23) (the addition rounds to the grid; the
-// subtraction is exact), and each digit is added with a 32-bit shared-memory atomic into
-// its own array: 32-bit shared atomics run about seven times faster than 64-bit ones on
-// this GPU, and a digit sum of up to 1023 contributions cannot overflow 32 bits. Chunks
-// whose bound lies outside the range of those FP32 constants, and FP64 contributions,
+// of one row). An FP32 contribution x is one 31-bit digit, x 2^(31-eb) rounded to the
+// nearest integer (u = 2^(eb-31)): the scaling is exact and the sums stay within 2^30 u,
+// so one 32-bit shared-memory atomic per contribution adds it, whatever the number of
+// contributions. An FP64 contribution is split into three signed 21-bit digits on the
+// grids 2^(eb-20), 2^(eb-41), 2^(eb-62) (u = 2^(eb-62)), each added with a 32-bit atomic
+// into its own array (a digit sum of up to 1023 contributions cannot overflow 32 bits):
+// 32-bit shared atomics run about seven times faster than 64-bit ones on this GPU.
+// Chunks whose bound lies outside the range of the FP32 scale, and FP64 contributions,
 // take an integer conversion instead (truncation, error < u). The value of an entry is
 // the digit sums' value in units u, rounded once to FP64 in integer arithmetic (the FP64
 // pipe's integer conversion takes half of them where it is exact). Integer addition is
 // exact and associative, so the result does not depend on the order of the additions:
 // per entry |result - exact sum of the contributions| <= m u / 2 + an ulp of the result
-// (m contributions), and the matrix is reproducible bit for bit.
+// (m contributions; u / 2 < 2^-30 B for FP32, 2^-61 B for FP64, B the chunk's bound), and
+// the matrix is reproducible bit for bit.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -404,8 +405,15 @@ __device__ __forceinline__ double fixed_to_double_exact(long long v, int ulog) {
   return __longlong_as_double(static_cast<long long>(bits));
 }
 
+// Digits of the fixed-point sums: one 31-bit digit for FP32 contributions, three 21-bit
+// digits (63 bits) for FP64 ones.
+template <typename T>
+__host__ __device__ constexpr int rows_ndig() { return sizeof(T) == 4 ? 1 : 3; }
+
 // The digits of one contribution for |x| <= 2^(eb-1): NDIG = 3 on the grids 2^(eb-20),
-// 2^(eb-41), 2^(eb-62) (unit u = 2^(eb-62)); NDIG = 2 on the first two (u = 2^(eb-41)).
+// 2^(eb-41), 2^(eb-62) (unit u = 2^(eb-62)); NDIG = 2 on the first two (u = 2^(eb-41));
+// NDIG = 1 one digit on the grid 2^(eb-31) (u = 2^(eb-31): a chunk's sums stay within
+// 2^30 u, so one 32-bit integer holds them whatever the number of contributions).
 // `magic`: the FP32 rounding constants are normal floats (-87 <= eb <= 124); otherwise
 // the integer conversion.
 template <int NDIG>
@@ -414,6 +422,15 @@ struct Digits {
   int b1, b2, b3, ulog;
   bool magic;
   __device__ __forceinline__ void init(int eb) {
+    if constexpr (NDIG == 1) {
+      // the scale 2^(31 - eb) must be a normal float
+      magic = eb >= -96 && eb <= 157;
+      c1 = __int_as_float((31 - (magic ? eb : 0) + 127) << 23);
+      c2 = c3 = 0.f;
+      b1 = b2 = b3 = 0;
+      ulog = eb - 31;
+      return;
+    }
     magic = eb >= -87 && eb <= 124;
     const int e = magic ? eb : 0;
     c1 = one_and_half_pow2(e + 3);
@@ -427,7 +444,12 @@ struct Digits {
   // MAGIC: the FP32 rounding constants (valid when `magic`); otherwise the integer conversion
   template <bool MAGIC>
   __device__ __forceinline__ void split(float x, int (&d)[NDIG]) const {
-    if constexpr (MAGIC) {
+    if constexpr (NDIG == 1) {
+      // x 2^(31 - eb) rounded to the nearest integer (the scaling is exact); |x| <= 2^(eb-1)
+      // keeps it within 2^30
+      if constexpr (MAGIC) d[0] = __float2int_rn(x * c1);
+      else d[0] = int(to_fixed(x, ulog));
+    } else if constexpr (MAGIC) {
       const float t1 = __fadd_rn(x, c1);
       const float r1 = __fsub_rn(x, __fsub_rn(t1, c1));
       const float t2 = __fadd_rn(r1, c2);
@@ -447,7 +469,9 @@ struct Digits {
     split_int(to_fixed(x, ulog), d);
   }
   __device__ __forceinline__ static void split_int(long long f, int (&d)[NDIG]) {
-    if constexpr (NDIG == 3) {
+    if constexpr (NDIG == 1) {
+      d[0] = int(f);
+    } else if constexpr (NDIG == 3) {
       d[2] = int(f & 0x1FFFFFll);
       d[1] = int((f >> 21) & 0x1FFFFFll);
       d[0] = int(f >> 42);
@@ -461,14 +485,21 @@ struct Digits {
   // (fp64_ok), so the other lanes' integer conversions and this one use different pipes
   __device__ __forceinline__ bool fp64_ok() const { return ulog >= -1022 && ulog <= 980; }
   __device__ __forceinline__ double value_fp64(const int (&s)[NDIG]) const {
-    static_assert(NDIG == 2, "FP64-pipe conversion of the 42-bit sums");
-    const long long v = static_cast<long long>(s[0]) * (1ll << 21) + s[1];
-    const long long bits = __double_as_longlong(static_cast<double>(v)) + (static_cast<long long>(ulog) << 52);
-    return __longlong_as_double(v == 0 ? 0ll : bits);
+    static_assert(NDIG <= 2, "FP64-pipe conversion of the 31- or 42-bit sums");
+    if constexpr (NDIG == 1) {
+      const long long bits = __double_as_longlong(static_cast<double>(s[0])) + (static_cast<long long>(ulog) << 52);
+      return __longlong_as_double(s[0] == 0 ? 0ll : bits);
+    } else {
+      const long long v = static_cast<long long>(s[0]) * (1ll << 21) + s[1];
+      const long long bits = __double_as_longlong(static_cast<double>(v)) + (static_cast<long long>(ulog) << 52);
+      return __longlong_as_double(v == 0 ? 0ll : bits);
+    }
   }
   // the entry's value from its digit sums, rounded once to FP64
   __device__ __forceinline__ double value(const int (&s)[NDIG]) const {
-    if constexpr (NDIG == 3) {
+    if constexpr (NDIG == 1) {  // |v| < 2^31: exact in a double
+      return fixed_to_double_exact(static_cast<long long>(s[0]), ulog);
+    } else if constexpr (NDIG == 3) {
       const long long v = static_cast<long long>(s[0]) * (1ll << 42) + static_cast<long long>(s[1]) * (1ll << 21) + s[2];
       return fixed_to_double(v, ulog);
     } else {  // |v| < 2^52: exact in a double
@@ -819,7 +850,7 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 1024 : 512, 1) rows_assemble(
   using C = RowsGeo<D, FORM>;
   using K = RowsCfg<D, FORM, Q>;
   constexpr int N = K::N, NF = C::NF, GS = C::GS, TH = sizeof(T) == 4 ? 1024 : 512;
-  constexpr int NDIG = sizeof(T) == 4 ? 2 : 3;  // digits: 42-bit fixed point for FP32, 63-bit for FP64
+  constexpr int NDIG = rows_ndig<T>();  // digits: 31-bit fixed point for FP32, 63-bit for FP64
   constexpr int ACC = NF * NDIG * ROWS_VSTRIDE;  // ints of one accumulator buffer
   constexpr int NSPECIAL = 3;
   using Slot = RowsSlot<NDIG>;
@@ -958,7 +989,7 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 1024 : 512, 1) rows_assemble(
       const int sh = sl.shift[f];
       double* out = (f == 0 ? p.out_a : p.out_b) + v0 - sh;
       int* a = ab + f * NDIG * ROWS_VSTRIDE;
-      const bool split_pipes = NDIG == 2 && fin && dg.fp64_ok();
+      const bool split_pipes = NDIG <= 2 && fin && dg.fp64_ok();
       const int hi = V + sh, end = min(hi, (b + 1) * K::WB);
       for (int x = b * K::WB + 4 * lane; x < end; x += 128) {
         int4 dd[NDIG];
@@ -973,7 +1004,7 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 1024 : 512, 1) rows_assemble(
           int sd[NDIG];
 #pragma unroll
           for (int d = 0; d < NDIG; ++d) sd[d] = c == 0 ? dd[d].x : c == 1 ? dd[d].y : c == 2 ? dd[d].z : dd[d].w;
-          if constexpr (NDIG == 2) {
+          if constexpr (NDIG <= 2) {
             if (((ROWS_FP64_MASK >> c) & 1) && split_pipes) {
               r[c] = dg.value_fp64(sd);
               continue;
@@ -1082,7 +1113,7 @@ int launch_rows_t(const ffc_row_plan* plan, const void* a0a, const void* a0b, do
   constexpr int N = nscalar(D, Q);
   const int pmax = std::max(plan->max_pairs, 1);
   using K = RowsCfg<D, FORM, Q>;
-  constexpr int NDIG = sizeof(T) == 4 ? 2 : 3;
+  constexpr int NDIG = rows_ndig<T>();
   const int rmax = std::max(plan->max_region, 16);
   const size_t meta_off = (2 * size_t(C::NF) * NDIG * ROWS_VSTRIDE * 4 + 4 * size_t(rmax) +
                            (3 * size_t(pmax) * C::GS + size_t(C::NF) * N) * sizeof(T) +

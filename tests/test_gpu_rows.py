@@ -1,7 +1,7 @@
 """Row-owner assembly (ffc_assemble_rows): parity with the oracle's Algorithm 2 on
 seeded meshes (triangles and tetrahedra, mass and Poisson, P1-P4, FP64 and FP32), the
 accuracy of its fixed-point sums (FP32: the very contributions the fused kernel adds,
-summed in 42-bit fixed point), determinism, overwrite semantics, edge cases and
+summed in 31-bit fixed point), determinism, overwrite semantics, edge cases and
 errors of the plan, and a sampled oracle check at the full 48^3 x 6 workload."""
 import math
 
@@ -89,13 +89,14 @@ def test_rows_match_oracle_algorithm2(F, d, n, form, q, prec):
                                         (2, 5, W.POISSON, 3)])
 def test_rows_fp32_are_exact_sums_of_the_fused_contributions(F, d, n, form, q):
     """FP32 row-owner assembly computes the same FP32 contributions as ffc_tabulate /
-    ffc_assemble (same G_K, same contraction order) and sums them in 42-bit fixed point:
-    the unit of a chunk is 2^(eb - 41) with 2^(eb - 2) < B <= 2^(eb - 1), B the chunk's
-    bound (largest a0max[i1] * sum|G_K| of its pairs times the most pairs of a row), so
-    each contribution is off by less than 2^-40 B and each entry is within
-    m * 2^-40 * B of the exact sum (math.fsum) of its m contributions, plus the final
-    rounding to FP64. G_K is recovered from the FP32 element tensors by least squares
-    against the reference tensor, which also checks the tensor representation A = A0 : G."""
+    ffc_assemble (same G_K, same contraction order) and sums them in 31-bit fixed point:
+    the unit of a chunk is u = 2^(eb - 31) with 2^(eb - 2) < B <= 2^(eb - 1), B the
+    chunk's bound (largest a0max[i1] * sum|G_K| of its pairs times the most pairs of a
+    row), and each contribution is rounded to the nearest multiple of u, off by at most
+    u / 2 < 2^-30 B, so each entry is within m * 2^-30 * B of the exact sum (math.fsum) of
+    its m contributions, plus the final rounding to FP64. G_K is recovered from the FP32
+    element tensors by least squares against the reference tensor, which also checks the
+    tensor representation A = A0 : G."""
     import torch
 
     p = _case(d, n, form, q)
@@ -119,10 +120,13 @@ def test_rows_fp32_are_exact_sums_of_the_fused_contributions(F, d, n, form, q):
     assert np.abs(A0 @ G - contrib.T).max() <= 1e-5 * np.abs(contrib).max()
     a0max = np.abs(A0).reshape(p.n_local, -1).max(axis=1)
     incidence = np.bincount(p.dofmap.reshape(-1), minlength=p.n_dof).max()
-    B = a0max.max() * np.abs(G).sum(axis=0).max() * incidence * (1 + 1e-4)
-    tol = np.spacing(np.abs(exact)) + m * 2.0 ** -40 * B
+    # the kernel bounds Poisson contributions with the symmetric reference tensor (the
+    # off-diagonal columns summed, entries up to twice those of the 9-column A0) and the
+    # six |G| entries (each off-diagonal once): at most twice this product
+    sym = 2.0 if form == W.POISSON else 1.0
+    B = sym * a0max.max() * np.abs(G).sum(axis=0).max() * incidence * (1 + 1e-4)
+    tol = np.spacing(np.abs(exact)) + m * 2.0 ** -30 * B
     assert np.all(np.abs(got - exact) <= tol)
-    assert np.mean(got == exact) > 0.5  # most entries are the correctly rounded sum itself
 
 
 def test_rows_are_deterministic_and_overwrite(F):
@@ -154,9 +158,10 @@ def test_rows_agree_with_the_atomic_assembly(F, prec):
                _dev(slot, torch.int32), val, precision=prec)
     assert F.status_poll() == 0
     # the same contributions summed two ways: FP64 atomics against fixed point with 63
-    # bits (FP64 path; rounding apart) or 42 bits (FP32 path; each contribution rounded
-    # to 2^-40 of its chunk's bound)
-    tol = 1e-13 if prec == "fp64" else 1e-9
+    # bits (FP64 path; rounding apart) or 31 bits (FP32 path; each contribution rounded
+    # to 2^-30 of its chunk's bound, the per-entry bound checked exactly by
+    # test_rows_fp32_are_exact_sums_of_the_fused_contributions)
+    tol = 1e-13 if prec == "fp64" else 1e-5
     assert (got - val).abs().max().item() <= tol * val.abs().max().item()
 
 
@@ -296,9 +301,9 @@ def test_full_size_rows_sampled_against_the_oracle(F, form, q):
     ref_val = torch.zeros_like(val)
     F.assemble(fm, cells, verts, _dev(slot, torch.int32), ref_val, precision="fp32")
     assert F.status_poll() == 0
-    # FP64 atomics against 42-bit fixed point (each contribution rounded to 2^-40 of its
+    # FP64 atomics against 31-bit fixed point (each contribution rounded to 2^-30 of its
     # chunk's bound)
-    assert (val - ref_val).abs().max().item() <= 1e-9 * ref_val.abs().max().item()
+    assert (val - ref_val).abs().max().item() <= 1e-5 * ref_val.abs().max().item()
 
 
 @pytest.mark.parametrize("d,n,q", [(3, 3, 1), (3, 3, 2), (3, 2, 3), (3, 2, 4), (2, 5, 2), (2, 4, 4)])
