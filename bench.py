@@ -295,7 +295,10 @@ def alg_bytes_tabulate(ctx, n_local, out_bytes):
 # DRAM bytes (read + write) per launch, from one `ncu` capture of the kernel on a smaller
 # mesh scaled by the cell count (positions, pairs, values and cells all grow with it); only
 # valid for the kernels as captured, other launches report null.
-CAPTURED_TRAFFIC_GB = {("rows_mass+poisson_p4", "fp32"): 1.237 * 8}  # captured at 24^3 x 6 = 82,944 cells
+# DRAM bytes per launch of the dominant kernel from an ncu capture of the current kernel
+# (scaled from a smaller mesh by the cell count); none is held for the one-digit row-owner
+# kernel, whose last capture (1.237 GB at 24^3 x 6, two-digit sums) predates it
+CAPTURED_TRAFFIC_GB = {}
 
 _PEAKS = {}
 
