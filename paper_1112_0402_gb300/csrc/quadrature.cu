@@ -414,9 +414,16 @@ int launch_quad_prec(const QParams& prm, int precision, bool assemble, cudaStrea
 namespace tq {
 using namespace ffc::tc;
 
+// The same contraction on the tensor cores (FFC_TF32 / FFC_TF32X3 / FFC_BF16X3): D[i][c] =
+// sum_j A~0[i][j] (G~_c[j] - G~_c(centroid)) with M = 128 element-tensor entries per M tile
+// (up to four), N = 128 cells, K = points x n_g in 48-column chunks; the operands split
+// into TF32 or BF16 parts as for the tensor representation, A~0 on the host, G~ on the
+// device. The drainers add the centroid term (sum_j A~0[i][j]) : G~_c in FP32, so the
+// tensor cores' FP32 accumulation only carries the deviations from the centroid value.
 // Warp roles: 0-7 produce the G~ chunks (two lanes per cell, each half of a chunk's
-// columns), 8-11 drain TMEM into A_K, 12 issues the MMAs, 13 streams the A~0 chunks,
-// 14-15 gather the cells' nodes and form the per-cell Jacobian coefficients one tile ahead.
+// columns), 8-11 drain TMEM into A_K (or add into CSR values), 12 issues the MMAs, 13
+// streams the A~0 chunks, 14-15 gather the cells' nodes and form the per-cell Jacobian
+// coefficients one tile ahead.
 constexpr int QKCH = 48;  // K columns per chunk (a multiple of both MMA K steps)
 constexpr int TQ_PRODUCER_WARPS = 8;
 constexpr int TQ_DRAIN_WARP0 = 8, TQ_MMA_WARP = 12, TQ_TMA_WARP = 13, TQ_GEO_WARP0 = 14;
