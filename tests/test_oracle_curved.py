@@ -69,7 +69,7 @@ def _mapped_reference_cell(d, c):
 
 
 @pytest.mark.parametrize("d", [2, 3])
-@pytest.mark.parametrize("q", [1, 2])
+@pytest.mark.parametrize("q", [1, 2, 3])
 def test_mass_sum_is_the_exact_measure_of_a_mapped_cell(d, q):
     c = 0.7
     nodes = _mapped_reference_cell(d, c)[None]
@@ -112,3 +112,24 @@ def test_a_transposed_inverse_breaks_the_energy_identity():
     u = X[:, :, 0]
     energy = np.einsum("ei,eij,ej->e", u, bad, u)
     assert np.abs(energy - Mm).max() > 1e-6
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_curved_p3_energy_identity(d):
+    """P3 on quadratic-geometry cells: the coordinate x_a is a quadratic function of X, so
+    it lies in the P3 space and its nodal interpolant (values of the map at the P3
+    lattice points) is exact; u^T A u is then the rule's measure of the cell, the sum of
+    the P3 mass matrix (which sums the P3 basis, a partition of unity)."""
+    cm = curved_mesh(d, 2 if d == 3 else 3, eps=0.12)
+    X = gather_nodes(cm)  # [E, n_g, d], P2 geometry nodes
+    p = 9
+    A = OC.element_tensors_curved(OC.POISSON, X, 3, 2, p)
+    Mm = OC.element_tensors_curved(OC.MASS, X, 3, 2, p)
+    lat3 = np.array(basis.lattice(d, 3), dtype=float) / 3  # barycentric P3 lattice [n3, d+1]
+    psi2 = basis.values(d, 2, lat3)  # the geometry basis at the P3 lattice points [n3, n_g]
+    x3 = np.einsum("sn,ena->esa", psi2, X)  # the map at the P3 nodes [E, n3, d]
+    assert np.abs(A.sum(axis=2)).max() <= 1e-13 * np.abs(A).max()
+    for a in range(d):
+        u = x3[:, :, a]
+        energy = np.einsum("ei,eij,ej->e", u, A, u)
+        assert np.abs(energy - Mm.sum(axis=(1, 2))).max() <= 1e-13
