@@ -76,14 +76,15 @@ typedef enum { FFC_TRIANGLE = 2, FFC_TETRAHEDRON = 3 } ffc_cell; /* value = spat
  * in FP64), the block algorithm takes an FP64 K. FP64 is the CSR accumulation type of
  * ffc_assemble. Tensor-core precisions are built for tetrahedra: convection P2,
  * elasticity P1-P3, Poisson P2-P4, mass P3-P4 (others, and every linear form, return
- * FFC_EUNSUPPORTED). */
+ * FFC_EUNSUPPORTED); for the quadrature representation see ffc_tabulate_quadrature. */
 typedef enum {
   FFC_FP64 = 0,   /* FP64 contraction, A_K stored as double */
   FFC_FP32 = 1,   /* FP32 G and A0, FP32 accumulation on CUDA cores, A_K stored as float */
   FFC_TF32 = 2,   /* tcgen05 kind::tf32, one product, FP32 accumulation in TMEM, float out */
   FFC_TF32X3 = 3, /* tcgen05 kind::tf32 with hi/lo splits of G and A0 (three products), float out */
   FFC_BF16X3 = 4, /* tcgen05 kind::f16 (BF16) with three-part splits of G and A0 (six products), float out */
-  FFC_FP64_OZAKI = 5 /* FP64 by exact products of 7-bit digits on tcgen05, double out (ffc_tabulate_quadrature) */
+  FFC_FP64_OZAKI = 5 /* FP64 by exact products of 7-bit digits on tcgen05, double out (the quadrature calls only;
+                        FFC_EINVAL elsewhere) */
 } ffc_precision;
 
 /* How the CUDA-core precisions (FFC_FP64, FFC_FP32) evaluate the vector forms.
