@@ -1230,8 +1230,9 @@ extern "C" int ffc_assemble_quadrature(const ffc_qform* f, int64_t n_elem, const
                                        int precision, void* stream) {
   int rc = check_args(f, n_elem, cells, nodes, n_nodes, precision, "ffc_assemble_quadrature", true);
   if (rc != FFC_OK || n_elem == 0) return rc;
-  if (!slot || !csr_val || nnz <= 0) {
-    set_error("ffc_assemble_quadrature: slot / csr_val");
+  if (!slot || !csr_val || nnz <= 0 || (reinterpret_cast<uintptr_t>(slot) & 3) ||
+      (reinterpret_cast<uintptr_t>(csr_val) & 7)) {
+    set_error("ffc_assemble_quadrature: slot / csr_val null, misaligned, or nnz <= 0");
     return FFC_EINVAL;
   }
   if (precision != FFC_FP64 && precision != FFC_FP32) {  // the tensor-core kernels, atomics in their drain

@@ -140,3 +140,20 @@ def test_digit_split_fp64_is_checked_before_device_work():
     # the tensor representation's entry points refuse it
     f = F.Form(F.POISSON, F.TETRAHEDRON, 2)
     assert L.ffc_tabulate(f.handle, 4, None, None, 10, None, None, F.FP64_OZAKI, None) == -1
+
+
+def test_assembly_pointers_are_checked_before_device_work():
+    """ffc_assemble_quadrature refuses null or misaligned slot / CSR pointers and a
+    non-positive nnz with FFC_EINVAL, for every precision, before touching the device
+    (the cell and node pointers below are never dereferenced)."""
+    F = _F()
+    from paper_1112_0402_gb300 import _capi
+
+    L = _capi.lib()
+    qf = F.QForm(F.POISSON, F.TETRAHEDRON, 2, 2)
+    cells, nodes = 4096, 8192  # aligned stand-ins, never read: the checks fail first
+    for prec in (F.FP64, F.FP32, F.TF32X3, F.FP64_OZAKI):
+        assert L.ffc_assemble_quadrature(qf.handle, 4, cells, nodes, 10, None, 16384, 5, prec, None) == -1
+        assert L.ffc_assemble_quadrature(qf.handle, 4, cells, nodes, 10, 4098, 16384, 5, prec, None) == -1
+        assert L.ffc_assemble_quadrature(qf.handle, 4, cells, nodes, 10, 4096, 16388, 5, prec, None) == -1
+        assert L.ffc_assemble_quadrature(qf.handle, 4, cells, nodes, 10, 4096, 16384, 0, prec, None) == -1
