@@ -418,8 +418,10 @@ void ffc_qform_destroy(ffc_qform* f);
  *   csr_val[slot[e][i1][i2]] += A_K[e][i1][i2]   (FP64 atomic adds)
  * with slot from ffc_csr_pattern of the P_degree dof map (the geometry nodes are only an
  * input of the map, not of the pattern); the precisions and limits of
- * ffc_tabulate_quadrature (the tensor-core kernels add in their drain). A slot outside
- * [0, nnz) is skipped and sets FFC_FLAG_BOUNDS.
+ * ffc_tabulate_quadrature (the tensor-core kernels add in their drain). slot (device
+ * int32 [n_elem][n][n]) and csr_val (device double [nnz]) must be naturally aligned and
+ * nnz > 0 (FFC_EINVAL otherwise); a slot outside [0, nnz) is skipped and sets
+ * FFC_FLAG_BOUNDS.
  */
 int ffc_tabulate_quadrature(const ffc_qform* f, int64_t n_elem, const int32_t* cells, const double* nodes,
                             int64_t n_nodes, void* A_K, int precision, void* stream);
